@@ -1,0 +1,309 @@
+/*
+ * oracle/track_ref.c -- plain FP64 reference tracker (TEST INFRASTRUCTURE).
+ *
+ * This file is the oracle that the GPU library is checked against.  It is not
+ * part of the product path: only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load it.  It shares no code, header, table or constant
+ * generator with the CUDA library; the two meet only in the seeded input
+ * generator (which holds no tracking arithmetic).
+ *
+ * What it computes (Oeftiger 2014, "Parallelisation of PyHEADTAIL"):
+ *   - Sec. 1.1.2: each macro-particle's longitudinal coordinates (z, delta) are
+ *     integrated turn by turn with Euler-Cromer (1st order), leap-frog (2nd
+ *     order Verlet) or a 4th-order Ruth scheme; particles are independent.
+ *   - Sec. 1.1.1: the transverse coordinates are pushed by the same linear
+ *     transfer matrix every turn.
+ *   - Sec. 2.3: two nested loops, turns (sequential) outside, particles
+ *     (independent) inside.
+ * The paper prints none of the formulas.  The readings used here are the
+ * textbook single-harmonic synchrotron map:
+ *   kick  K(w):  phi = phi_s + k z;  delta <- delta + w A (sin phi - sin phi_s)
+ *   drift D(w):  z <- z - w eta C delta
+ *   EC    = K(1) then D(1)           (momentum first, then position)
+ *   LF    = D(1/2) K(1) D(1/2)       (Verlet drift-kick-drift)
+ *   RUTH4 = D(t/2) K(t) D((1-t)/2) K(1-2t) D((1-t)/2) K(t) D(t/2),
+ *           t = 1/(2 - 2^(1/3))      (Forest & Ruth 1990; Yoshida 1990)
+ *   transverse, per plane: [u; u'] <- [[cos mu, b sin mu], [-sin mu / b, cos mu]] [u; u']
+ *           mu = 2 pi frac(Q), alpha = 0, no chromaticity.
+ * Derived constants (all FP64, from the ring parameters):
+ *   beta*gamma = p0/m; gamma = sqrt(1 + (beta gamma)^2); beta = beta gamma / gamma
+ *   eta = 1/gamma_t^2 - 1/gamma^2;  k = 2 pi h / C;  A = q V / (beta p0)   [p0 in eV/c]
+ * Moments after each recorded turn: means, population rms (two-pass) and the
+ * rms emittance sqrt(<u^2><u'^2> - <u u'>^2) of the centred coordinates.
+ *
+ * Compiled with -O2 -ffp-contract=off (no fused multiply-add): every operation
+ * rounds as written.  Parity status: pinned (closed-form linear map, textbook
+ * synchrotron tune and bucket height, pendulum detuning, time-reversal
+ * symmetry, symplecticity, order scaling, high-precision brute force, exact
+ * transverse rotation); see the tests.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define REF_OK 0
+#define REF_E_INVALID (-1)
+#define REF_E_UNSTABLE (-2)
+
+enum { REF_EULER_CROMER = 0, REF_LEAPFROG = 1, REF_RUTH4 = 2 };
+
+/* Number of moment values per recorded turn, in this order:
+ *  0 mean z   1 mean delta   2 rms z   3 rms delta   4 eps_z
+ *  5 mean x   6 mean x'      7 rms x   8 rms x'      9 eps_x
+ * 10 mean y  11 mean y'     12 rms y  13 rms y'     14 eps_y            */
+#define REF_NMOM 15
+
+typedef struct {
+    double circumference_m; /* C */
+    double gamma_t;         /* transition gamma */
+    double p0_eVc;          /* reference momentum in eV/c */
+    double mass_eV;         /* rest mass in eV/c^2 */
+    double charge_e;        /* charge in units of e */
+    double harmonic;        /* RF harmonic number h */
+    double voltage_V;       /* RF voltage V */
+    double phi_s_rad;       /* synchronous phase */
+    double rf_linear;       /* nonzero: sin(phi) - sin(phi_s) -> cos(phi_s) k z */
+    double beta_x_m, beta_y_m, Qx, Qy;
+} ref_params;
+
+typedef struct {
+    double betagamma, gamma, beta, eta, k, A, etaC, phi_s, sin_phis, cos_phis;
+    double K, Qs; /* linear strength eta C A k cos(phi_s) and sqrt(K)/(2 pi) */
+    double rf_linear;
+    double mx[4], my[4]; /* transverse one-turn matrices, row-major */
+} ref_derived;
+
+static const double REF_PI = 3.14159265358979323846;
+
+int ref_derive(const ref_params* p, ref_derived* d)
+{
+    if (!p || !d) return REF_E_INVALID;
+    if (!(p->circumference_m > 0) || !(p->p0_eVc > 0) || !(p->mass_eV > 0) ||
+        !(p->gamma_t > 0) || !(p->harmonic > 0))
+        return REF_E_INVALID;
+    memset(d, 0, sizeof(*d));
+    d->betagamma = p->p0_eVc / p->mass_eV;
+    d->gamma = sqrt(1.0 + d->betagamma * d->betagamma);
+    d->beta = d->betagamma / d->gamma;
+    d->eta = 1.0 / (p->gamma_t * p->gamma_t) - 1.0 / (d->gamma * d->gamma);
+    d->k = 2.0 * REF_PI * p->harmonic / p->circumference_m;
+    d->A = p->charge_e * p->voltage_V / (d->beta * p->p0_eVc);
+    d->etaC = d->eta * p->circumference_m;
+    d->phi_s = p->phi_s_rad;
+    d->sin_phis = sin(p->phi_s_rad);
+    d->cos_phis = cos(p->phi_s_rad);
+    d->rf_linear = p->rf_linear;
+    d->K = d->etaC * d->A * d->k * d->cos_phis;
+    d->Qs = d->K > 0 ? sqrt(d->K) / (2.0 * REF_PI) : 0.0;
+
+    double mux = 2.0 * REF_PI * (p->Qx - floor(p->Qx));
+    double muy = 2.0 * REF_PI * (p->Qy - floor(p->Qy));
+    double bx = p->beta_x_m > 0 ? p->beta_x_m : 1.0;
+    double by = p->beta_y_m > 0 ? p->beta_y_m : 1.0;
+    d->mx[0] = cos(mux);       d->mx[1] = bx * sin(mux);
+    d->mx[2] = -sin(mux) / bx; d->mx[3] = cos(mux);
+    d->my[0] = cos(muy);       d->my[1] = by * sin(muy);
+    d->my[2] = -sin(muy) / by; d->my[3] = cos(muy);
+
+    /* a zero voltage is a pure drift: allowed.  Otherwise the linearised
+     * motion must oscillate: eta cos(phi_s) > 0 and 0 < K < 4. */
+    if (p->voltage_V != 0.0 && !(d->K > 0.0 && d->K < 4.0)) return REF_E_UNSTABLE;
+    return REF_OK;
+}
+
+/* ---- one stage of the longitudinal map -------------------------------- */
+
+static double ref_force(const ref_derived* d, double z)
+{
+    if (d->rf_linear != 0.0) return d->cos_phis * d->k * z;
+    return sin(d->phi_s + d->k * z) - d->sin_phis;
+}
+
+static void ref_kick(const ref_derived* d, double w, double z, double* dp)
+{
+    *dp = *dp + (w * d->A) * ref_force(d, z);
+}
+
+static void ref_drift(const ref_derived* d, double w, double* z, double dp)
+{
+    *z = *z - (w * d->etaC) * dp;
+}
+
+/* Forest-Ruth coefficient t = 1/(2 - 2^(1/3)). */
+static double ref_ruth_theta(void) { return 1.0 / (2.0 - cbrt(2.0)); }
+
+/* One turn of the chosen scheme; sign = +1 forward, -1 the exact inverse
+ * (stages in reverse order with negated weights). */
+static void ref_turn(const ref_derived* d, int scheme, double sign, double* z, double* dp)
+{
+    if (scheme == REF_EULER_CROMER) {
+        if (sign > 0) { ref_kick(d, 1.0, *z, dp); ref_drift(d, 1.0, z, *dp); }
+        else          { ref_drift(d, -1.0, z, *dp); ref_kick(d, -1.0, *z, dp); }
+    } else if (scheme == REF_LEAPFROG) {
+        /* palindromic: the inverse has the same order */
+        ref_drift(d, 0.5 * sign, z, *dp);
+        ref_kick(d, 1.0 * sign, *z, dp);
+        ref_drift(d, 0.5 * sign, z, *dp);
+    } else {
+        double t = ref_ruth_theta();
+        ref_drift(d, 0.5 * t * sign, z, *dp);
+        ref_kick(d, t * sign, *z, dp);
+        ref_drift(d, 0.5 * (1.0 - t) * sign, z, *dp);
+        ref_kick(d, (1.0 - 2.0 * t) * sign, *z, dp);
+        ref_drift(d, 0.5 * (1.0 - t) * sign, z, *dp);
+        ref_kick(d, t * sign, *z, dp);
+        ref_drift(d, 0.5 * t * sign, z, *dp);
+    }
+}
+
+static void ref_rotate(const double* m, double sign, double* u, double* up)
+{
+    /* the inverse of [[c, b s], [-s/b, c]] is [[c, -b s], [s/b, c]] */
+    double m1 = sign > 0 ? m[1] : -m[1];
+    double m2 = sign > 0 ? m[2] : -m[2];
+    double un = m[0] * *u + m1 * *up;
+    double upn = m2 * *u + m[3] * *up;
+    *u = un;
+    *up = upn;
+}
+
+/* Two-pass moments of (a, b): mean, population rms and emittance. */
+static void ref_pair_moments(const double* a, const double* b, long n, double* out5)
+{
+    double ma = 0, mb = 0, saa = 0, sbb = 0, sab = 0;
+    long i;
+    if (n <= 0) { out5[0] = out5[1] = out5[2] = out5[3] = out5[4] = 0.0; return; }
+    for (i = 0; i < n; i++) { ma += a[i]; mb += b[i]; }
+    ma /= (double)n;
+    mb /= (double)n;
+    for (i = 0; i < n; i++) {
+        double da = a[i] - ma, db = b[i] - mb;
+        saa += da * da;
+        sbb += db * db;
+        sab += da * db;
+    }
+    saa /= (double)n;
+    sbb /= (double)n;
+    sab /= (double)n;
+    double e2 = saa * sbb - sab * sab;
+    out5[0] = ma;
+    out5[1] = mb;
+    out5[2] = sqrt(saa);
+    out5[3] = sqrt(sbb);
+    out5[4] = e2 > 0 ? sqrt(e2) : 0.0;
+}
+
+void ref_moments(const double* z, const double* dp, const double* x, const double* xp,
+                 const double* y, const double* yp, long n, double* out)
+{
+    int j;
+    for (j = 0; j < REF_NMOM; j++) out[j] = 0.0;
+    ref_pair_moments(z, dp, n, out);
+    if (x && xp) ref_pair_moments(x, xp, n, out + 5);
+    if (y && yp) ref_pair_moments(y, yp, n, out + 10);
+}
+
+/*
+ * Track n particles for `turns` turns.  Any of x..yp may be NULL (plane off).
+ * moments: NULL, or an array of (turns/stride + 1) * REF_NMOM doubles; row r
+ * holds the moments after turn r*stride (row 0 = the initial state).
+ * sign = +1 tracks forward, -1 applies the inverse map.
+ */
+int ref_track_signed(const ref_derived* d, int scheme, double sign, double* z, double* dp,
+                     double* x, double* xp, double* y, double* yp, long n, long turns,
+                     double* moments, long stride)
+{
+    long t, i;
+    if (!d || n < 0 || turns < 0 || scheme < 0 || scheme > 2) return REF_E_INVALID;
+    if (n > 0 && (!z || !dp)) return REF_E_INVALID;
+    if (moments && stride <= 0) return REF_E_INVALID;
+    int dox = x && xp, doy = y && yp;
+    if (moments) ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n, moments);
+    for (t = 1; t <= turns; t++) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (i = 0; i < n; i++) {
+            ref_turn(d, scheme, sign, &z[i], &dp[i]);
+            if (dox) ref_rotate(d->mx, sign, &x[i], &xp[i]);
+            if (doy) ref_rotate(d->my, sign, &y[i], &yp[i]);
+        }
+        if (moments && t % stride == 0)
+            ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n,
+                        moments + (t / stride) * REF_NMOM);
+    }
+    return REF_OK;
+}
+
+int ref_track(const ref_derived* d, int scheme, double* z, double* dp, double* x, double* xp,
+              double* y, double* yp, long n, long turns, double* moments, long stride)
+{
+    return ref_track_signed(d, scheme, 1.0, z, dp, x, xp, y, yp, n, turns, moments, stride);
+}
+
+/* ---- one-turn Jacobian by forward-mode dual numbers -------------------- */
+
+typedef struct { double v, dz, dd; } ref_dual; /* value and d/dz0, d/ddelta0 */
+
+static void ref_dual_turn(const ref_derived* d, int scheme, ref_dual* z, ref_dual* dp)
+{
+    /* the same stage sequence as ref_turn, carrying the tangent vectors */
+    double ws_d[4], ws_k[3];
+    int nd, nk, s;
+    if (scheme == REF_EULER_CROMER) { nk = 1; ws_k[0] = 1.0; nd = 1; ws_d[0] = 1.0; }
+    else if (scheme == REF_LEAPFROG) { nd = 2; ws_d[0] = ws_d[1] = 0.5; nk = 1; ws_k[0] = 1.0; }
+    else {
+        double t = ref_ruth_theta();
+        nd = 4; ws_d[0] = ws_d[3] = 0.5 * t; ws_d[1] = ws_d[2] = 0.5 * (1.0 - t);
+        nk = 3; ws_k[0] = ws_k[2] = t; ws_k[1] = 1.0 - 2.0 * t;
+    }
+    /* EC starts with a kick; LF and RUTH4 alternate starting with a drift */
+    int di = 0, ki = 0;
+    int nstages = nd + nk;
+    for (s = 0; s < nstages; s++) {
+        int is_kick = (scheme == REF_EULER_CROMER) ? (s == 0) : (s % 2 == 1);
+        if (is_kick) {
+            double w = ws_k[ki++] * d->A, f, fp;
+            if (d->rf_linear != 0.0) { f = d->cos_phis * d->k * z->v; fp = d->cos_phis * d->k; }
+            else { double ph = d->phi_s + d->k * z->v; f = sin(ph) - d->sin_phis; fp = d->k * cos(ph); }
+            dp->v = dp->v + w * f;
+            dp->dz = dp->dz + w * fp * z->dz;
+            dp->dd = dp->dd + w * fp * z->dd;
+        } else {
+            double w = ws_d[di++] * d->etaC;
+            z->v = z->v - w * dp->v;
+            z->dz = z->dz - w * dp->dz;
+            z->dd = z->dd - w * dp->dd;
+        }
+    }
+}
+
+/* J = d(z1, delta1)/d(z0, delta0) after `turns` turns, row-major 2x2. */
+int ref_jacobian(const ref_derived* d, int scheme, double z0, double dp0, long turns, double* J)
+{
+    if (!d || !J || scheme < 0 || scheme > 2 || turns < 0) return REF_E_INVALID;
+    ref_dual z = {z0, 1.0, 0.0}, dp = {dp0, 0.0, 1.0};
+    long t;
+    for (t = 0; t < turns; t++) ref_dual_turn(d, scheme, &z, &dp);
+    J[0] = z.dz; J[1] = z.dd; J[2] = dp.dz; J[3] = dp.dd;
+    return REF_OK;
+}
+
+int ref_num_threads(void)
+{
+#ifdef _OPENMP
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each pin takes an ``oracle.Oracle`` (the default build, or a deliberately mutated
+copy in ``test_oracle_mutants.py``) and raises AssertionError when the oracle
+disagrees with the mathematics.  The paper prints no formulas and no physics
+results (Sec. 1.1.1 and 1.1.2 only name the schemes), so every pin here is a
+closed form, an invariant, a textbook formula or a brute-force evaluation:
+
+* textbook synchrotron tune and stationary-bucket height (in terms of h, eta, V,
+  beta and E only);
+* the closed-form one-turn matrices of the linearised Euler-Cromer and leap-frog
+  maps and the Chebyshev form of their N-th power; the 4th-order tune error of
+  the Ruth scheme;
+* the pendulum's amplitude-dependent period (complete elliptic integral);
+* the separatrix found by tracking, against the textbook bucket height;
+* time-reversal symmetry of the palindromic schemes (and its absence for EC);
+* the exact inverse map; det J = 1 (dual numbers and finite differences);
+* order of the energy error under a change of RF voltage;
+* oddness of the force and the fixed point; the exact transverse rotation;
+* moments against numpy's mean / std / covariance;
+* a 40-digit mpmath evaluation of the same maps on tiny inputs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle as _oracle
+
+M_P = 938.27208816e6
+RING = dict(circumference_m=6911.5, harmonic=4620.0, p0_eVc=26e9, gamma_t=22.77, mass_eV=M_P,
+            charge_e=1.0, phi_s_rad=0.0, rf_linear=0.0, beta_x_m=50.0, beta_y_m=50.0,
+            Qx=20.13, Qy=20.18)
+
+
+def ring(**over):
+    r = dict(RING, voltage_V=2e6)
+    r.update(over)
+    return r
+
+
+def textbook(r):
+    """Textbook quantities from the ring parameters only (charge +1 e)."""
+    E = math.hypot(r["p0_eVc"], r["mass_eV"])
+    gamma = E / r["mass_eV"]
+    beta = r["p0_eVc"] / E
+    eta = 1.0 / r["gamma_t"] ** 2 - 1.0 / gamma ** 2
+    h, V, C = r["harmonic"], r["voltage_V"], r["circumference_m"]
+    cphi = math.cos(r["phi_s_rad"])
+    # small-amplitude synchrotron tune  Q_s = sqrt(h eta e V cos(phi_s) / (2 pi beta^2 E))
+    Qs = math.sqrt(h * eta * V * cphi / (2.0 * math.pi * beta ** 2 * E))
+    # stationary bucket half-height  (dp/p)_max = sqrt(2 e V / (pi beta^2 E h |eta|))
+    dhat = math.sqrt(2.0 * V / (math.pi * beta ** 2 * E * h * abs(eta)))
+    # linear one-turn quantities: eta C and the kick slope a = (e V / (beta p0 c)) (2 pi h / C) cos(phi_s)
+    etaC = eta * C
+    a = V / (beta * r["p0_eVc"]) * (2.0 * math.pi * h / C) * cphi
+    zhat = C / (2.0 * h)  # bucket half-length
+    return dict(E=E, gamma=gamma, beta=beta, eta=eta, Qs=Qs, dhat=dhat, etaC=etaC, a=a,
+                K=etaC * a, zhat=zhat, k=2.0 * math.pi * h / C)
+
+
+def _traj(O, d, scheme, z0, dp0, turns):
+    """Turn-by-turn (z, dp) of one particle, via the single-particle moments (mean = value)."""
+    *_, mom = O.track(d, scheme, [z0], [dp0], turns=turns, moments=True, stride=1)
+    return mom[:, 0].copy(), mom[:, 1].copy()
+
+
+def _tune_from_crossings(z):
+    s = np.signbit(z)
+    idx = np.nonzero(s[1:] != s[:-1])[0]
+    assert idx.size >= 4, "no oscillation"
+    tc = idx + z[idx] / (z[idx] - z[idx + 1])
+    return (idx.size - 1) / (2.0 * (tc[-1] - tc[0]))
+
+
+# --------------------------------------------------------------------------------------------
+
+
+def pin_textbook_constants(O):
+    for V in (2e6, 4.5e6):
+        r = ring(voltage_V=V)
+        tb = textbook(r)
+        d = O.derive(r)
+        assert abs(d.gamma / tb["gamma"] - 1) < 1e-14
+        assert abs(d.beta / tb["beta"] - 1) < 1e-14
+        assert abs(d.Qs / tb["Qs"] - 1) < 1e-12, (d.Qs, tb["Qs"])
+        dhat_map = 2.0 * math.sqrt(d.A / (d.k * d.etaC))
+        assert abs(dhat_map / tb["dhat"] - 1) < 1e-12, (dhat_map, tb["dhat"])
+        assert abs(math.pi / d.k / tb["zhat"] - 1) < 1e-14
+
+
+def pin_stability_rules(O):
+    assert O.derive_rc(_oracle.params(**ring())) == 0
+    # below transition (gamma < gamma_t) the stationary bucket needs phi_s = pi
+    below = ring(p0_eVc=10e9)
+    assert O.derive_rc(_oracle.params(**below)) == -2
+    assert O.derive_rc(_oracle.params(**dict(below, phi_s_rad=math.pi))) == 0
+    # zero voltage: a pure drift is allowed
+    assert O.derive_rc(_oracle.params(**ring(voltage_V=0.0))) == 0
+
+
+def _linear_matrix(O, d, scheme):
+    sz, sd = 1e-2, 1e-5
+    z1, d1, *_ = O.track(d, scheme, [sz, 0.0], [0.0, sd], turns=1)
+    return np.array([[z1[0] / sz, z1[1] / sd], [d1[0] / sz, d1[1] / sd]])
+
+
+def pin_linear_closed_form(O):
+    """rf_linear: sin(phi) - sin(phi_s) -> cos(phi_s) k z makes every scheme a constant matrix."""
+    for phis in (0.0, 0.3):
+        _linear_closed_form_at(O, phis)
+
+
+def _linear_closed_form_at(O, phis):
+    r = ring(rf_linear=1.0, phi_s_rad=phis)
+    tb = textbook(r)
+    d = O.derive(r)
+    eC, a, K = tb["etaC"], tb["a"], tb["K"]
+    closed = {
+        "euler_cromer": np.array([[1 - K, -eC], [a, 1.0]]),          # kick, then drift
+        "leapfrog": np.array([[1 - K / 2, -eC * (1 - K / 4)], [a, 1 - K / 2]]),
+    }
+    for scheme, Mc in closed.items():
+        M = _linear_matrix(O, d, scheme)
+        assert np.all(np.abs(M / Mc - 1) < 1e-12), (scheme, M, Mc)
+        # N-th power by the Chebyshev identity for det M = 1:
+        # M^N = (sin(N mu) M - sin((N-1) mu) I) / sin(mu),  cos(mu) = tr(M)/2 = 1 - K/2,
+        # i.e. mu = 2 asin(sqrt(K)/2) (the well-conditioned form near mu = 0)
+        mu = 2.0 * math.asin(math.sqrt(K) / 2.0)
+        N = 10000
+        MN = (math.sin(N * mu) * Mc - math.sin((N - 1) * mu) * np.eye(2)) / math.sin(mu)
+        z0, dp0 = 0.05, 2e-4
+        zN, dN, *_ = O.track(d, scheme, [z0], [dp0], turns=N)
+        ez, ed = MN @ np.array([z0, dp0])
+        # relative to the orbit's extent in each coordinate
+        zs = math.hypot(z0, dp0 * tb["etaC"] / (2 * math.pi * tb["Qs"]))
+        ds = zs * 2 * math.pi * tb["Qs"] / tb["etaC"]
+        assert abs(zN[0] - ez) / zs < 1e-11, (scheme, zN[0], ez)
+        assert abs(dN[0] - ed) / ds < 1e-11, (scheme, dN[0], ed)
+    # Ruth4: det 1 and a 4th-order tune: |mu - sqrt(K)| / sqrt(K) = O(K^2), i.e. ~16x smaller
+    # per K/4 (a 2nd-order scheme gives K/24, ~4x)
+    errs = []
+    for V in (2e6, 0.5e6):
+        rr = ring(rf_linear=1.0, voltage_V=V, phi_s_rad=phis)
+        tbr = textbook(rr)
+        M = _linear_matrix(O, O.derive(rr), "ruth4")
+        assert abs(np.linalg.det(M) - 1) < 1e-13
+        mu = 2.0 * math.asin(math.sqrt(max(0.0, 2.0 - np.trace(M))) / 2.0)
+        errs.append(abs(mu - math.sqrt(tbr["K"])) / math.sqrt(tbr["K"]))
+    assert errs[0] < 1e-5, errs
+    assert 13 < errs[0] / errs[1] < 19, errs
+
+
+def pin_pendulum_detuning(O):
+    """Amplitude-dependent tune of the sine kick: Q(zhat) = Qs pi / (2 K_ell(sin^2(k zhat / 2)))."""
+    from scipy.special import ellipk
+
+    r = ring()
+    tb = textbook(r)
+    d = O.derive(r)
+    for frac in (0.3, 0.6, 0.85):
+        zh = frac * tb["zhat"]
+        z, _ = _traj(O, d, "ruth4", zh, 0.0, 30000)
+        Q = _tune_from_crossings(z)
+        m = math.sin(tb["k"] * zh / 2.0) ** 2
+        Qexp = tb["Qs"] * math.pi / (2.0 * ellipk(m))
+        assert abs(Q / Qexp - 1) < 2e-5, (frac, Q, Qexp)
+
+
+def pin_separatrix(O):
+    """A particle started at z = 0 just inside the textbook bucket height stays in the bucket;
+    just outside it slips out (checked with the 4th-order scheme at low voltage)."""
+    r = ring(voltage_V=0.5e6)
+    tb = textbook(r)
+    d = O.derive(r)
+    zin, _ = _traj(O, d, "ruth4", 0.0, 0.985 * tb["dhat"], 20000)
+    zout, _ = _traj(O, d, "ruth4", 0.0, 1.015 * tb["dhat"], 20000)
+    assert np.max(np.abs(zin)) < tb["zhat"]
+    assert np.max(np.abs(zout)) > 1.5 * tb["zhat"]
+
+
+def pin_time_reversal(O):
+    """Palindromic compositions (LF, Ruth4) satisfy R M R = M^-1 with R: dp -> -dp;
+    Euler-Cromer does not."""
+    r = ring(voltage_V=4.5e6)
+    tb = textbook(r)
+    d = O.derive(r)
+    z0 = np.array([0.1, 0.4, 0.6]) * tb["zhat"]
+    d0 = np.array([0.3, -0.2, 0.1]) * tb["dhat"]
+    N = 10000
+    for scheme in ("leapfrog", "ruth4", "euler_cromer"):
+        z1, d1, *_ = O.track(d, scheme, z0, d0, turns=N)
+        z2, d2, *_ = O.track(d, scheme, z1, -d1, turns=N)
+        err = max(np.max(np.abs(z2 - z0)) / tb["zhat"], np.max(np.abs(-d2 - d0)) / tb["dhat"])
+        if scheme == "euler_cromer":
+            assert err > 1e-6, err
+        else:
+            assert err < 1e-11, (scheme, err)
+
+
+def pin_inverse_map(O):
+    r = ring(voltage_V=4.5e6)
+    tb = textbook(r)
+    d = O.derive(r)
+    z0 = np.array([0.05, 0.5, 0.85]) * tb["zhat"]
+    d0 = np.array([0.1, -0.3, 0.02]) * tb["dhat"]
+    x0, xp0 = np.array([1e-3, -2e-3, 5e-4]), np.array([2e-5, 1e-5, -3e-5])
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        z1, d1, x1, xp1, *_ = O.track(d, scheme, z0, d0, x0, xp0, turns=10000)
+        z2, d2, x2, xp2, *_ = O.track(d, scheme, z1, d1, x1, xp1, turns=10000, sign=-1.0)
+        # 1e-12 of the bucket size for orbits up to half the bucket; near the separatrix
+        # (85 %) the steep amplitude-dependence of the tune amplifies rounding: 1e-11
+        tol = np.array([1e-12, 1e-12, 1e-11])
+        assert np.all(np.abs(z2 - z0) / tb["zhat"] < tol), (scheme, z2 - z0)
+        assert np.all(np.abs(d2 - d0) / tb["dhat"] < tol), (scheme, d2 - d0)
+        assert np.max(np.abs(x2 - x0)) < 1e-12 * 3e-3
+
+
+def pin_symplectic(O):
+    r = ring(voltage_V=4.5e6)
+    tb = textbook(r)
+    d = O.derive(r)
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        for fz, fd in ((0.0, 0.0), (0.3, 0.2), (0.8, -0.1), (0.5, 0.5)):
+            z0, dp0 = fz * tb["zhat"], fd * tb["dhat"]
+            J = O.jacobian(d, scheme, z0, dp0, 1)
+            assert abs(np.linalg.det(J) - 1) < 1e-13, (scheme, J)
+            J100 = O.jacobian(d, scheme, z0, dp0, 100)
+            assert abs(np.linalg.det(J100) - 1) < 1e-10, (scheme, np.linalg.det(J100))
+            # the dual-number Jacobian is the derivative of the tracked map
+            hz, hd = 1e-6 * tb["zhat"], 1e-6 * tb["dhat"]
+            zp, dpp, *_ = O.track(d, scheme, [z0 + hz, z0 - hz, z0, z0],
+                                  [dp0, dp0, dp0 + hd, dp0 - hd], turns=1)
+            Jfd = np.array([[(zp[0] - zp[1]) / (2 * hz), (zp[2] - zp[3]) / (2 * hd)],
+                            [(dpp[0] - dpp[1]) / (2 * hz), (dpp[2] - dpp[3]) / (2 * hd)]])
+            scale = np.array([[1.0, tb["zhat"] / tb["dhat"]], [tb["dhat"] / tb["zhat"], 1.0]])
+            assert np.max(np.abs(J - Jfd) / scale) < 1e-6, (scheme, J, Jfd)
+
+
+def _energy_err(O, scheme, V, turns):
+    r = ring(voltage_V=V)
+    tb = textbook(r)
+    d = O.derive(r)
+    z, dp = _traj(O, d, scheme, 0.5 * tb["zhat"], 0.0, turns)
+    # pendulum invariant of the smooth motion (phi_s = 0)
+    H = 0.5 * d.etaC * dp ** 2 + (d.A / d.k) * (1 - np.cos(d.k * z))
+    return np.max(np.abs(H - H[0])) / H[0], np.max(np.abs(H[:1001] - H[0])) / H[0]
+
+
+def pin_energy_order(O):
+    """Symplectic schemes keep |H - H0| bounded; it scales with the step sqrt(K) to the
+    scheme's order: quartering V (halving sqrt K) divides it by ~2, ~4, ~16."""
+    expect = {"euler_cromer": (1.6, 2.6), "leapfrog": (3.2, 5.0), "ruth4": (12.0, 21.0)}
+    for scheme, (lo, hi) in expect.items():
+        e_hi, e_hi_short = _energy_err(O, scheme, 4e6, 10000)
+        e_lo, _ = _energy_err(O, scheme, 1e6, 10000)
+        assert e_hi < 1.5 * e_hi_short + 1e-13, (scheme, e_hi, e_hi_short)  # bounded, no drift
+        assert lo < e_hi / e_lo < hi, (scheme, e_hi / e_lo)
+
+
+def pin_symmetry_and_fixed_point(O):
+    r = ring(voltage_V=4.5e6)
+    tb = textbook(r)
+    d = O.derive(r)
+    z0 = np.array([0.1, 0.45, 0.7]) * tb["zhat"]
+    d0 = np.array([0.2, -0.3, 0.05]) * tb["dhat"]
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        za, da, *_ = O.track(d, scheme, z0, d0, turns=2000)
+        zb, db, *_ = O.track(d, scheme, -z0, -d0, turns=2000)
+        assert np.array_equal(za, -zb) and np.array_equal(da, -db), scheme
+        zf, df, *_ = O.track(d, scheme, [0.0], [0.0], turns=2000)
+        assert zf[0] == 0.0 and df[0] == 0.0
+    # off-zero synchronous phase (stable above transition for |phi_s| < pi/2) and
+    # phi_s = pi below transition: z = dp = 0 is still a fixed point of the map
+    for rr in (ring(phi_s_rad=0.3), ring(p0_eVc=10e9, phi_s_rad=math.pi)):
+        dd = O.derive(rr)
+        for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+            zf, df, *_ = O.track(dd, scheme, [0.0], [0.0], turns=500)
+            assert zf[0] == 0.0 and df[0] == 0.0, (scheme, zf, df)
+
+
+def pin_transverse_rotation(O):
+    r = ring(voltage_V=4.5e6)
+    d = O.derive(r)
+    N = 10000
+    for beta, Q, key in ((50.0, 20.13, "x"), (50.0, 20.18, "y")):
+        u0 = np.array([1e-3, -5e-4, 0.0])
+        up0 = np.array([0.0, 2e-5, -1e-5])
+        args = dict(x=u0, xp=up0) if key == "x" else dict(y=u0, yp=up0)
+        out = O.track(d, "leapfrog", np.zeros(3), np.zeros(3), turns=N, **args)
+        u, up = (out[2], out[3]) if key == "x" else (out[4], out[5])
+        # exact N-turn rotation (alpha = 0) by the phase N * 2 pi frac(Q), evaluated at 30
+        # digits from the double value of frac(Q) (Q - floor(Q) is exact in binary)
+        import mpmath as mp
+
+        with mp.workdps(30):
+            ph = 2 * mp.pi * N * (mp.mpf(Q) - math.floor(Q))
+            c, s = float(mp.cos(ph)), float(mp.sin(ph))
+        ue = c * u0 + beta * s * up0
+        upe = -s / beta * u0 + c * up0
+        scale = 1e-3
+        assert np.max(np.abs(u - ue)) / scale < N * 1e-15, key
+        assert np.max(np.abs(up - upe)) * beta / scale < N * 1e-15, key
+        # Courant-Snyder invariant
+        J0 = u0 ** 2 / beta + beta * up0 ** 2
+        J1 = u ** 2 / beta + beta * up ** 2
+        assert np.max(np.abs(J1 - J0)) / np.max(J0) < 1e-12
+
+
+def pin_moments(O):
+    rng = np.random.default_rng(7)
+    n = 1001
+    z, dp = rng.normal(0.01, 0.1, n), rng.normal(-1e-5, 1e-3, n) + 0.002 * rng.normal(0, 0.1, n)
+    x, xp = rng.normal(0, 1e-3, n), rng.normal(0, 2e-5, n)
+    y, yp = rng.normal(0, 2e-3, n), rng.normal(0, 1e-5, n)
+    m = O.moments(z, dp, x, xp, y, yp)
+    for off, (a, b) in zip((0, 5, 10), ((z, dp), (x, xp), (y, yp))):
+        cov = np.cov(np.vstack([a, b]), bias=True)
+        exp = [a.mean(), b.mean(), a.std(), b.std(), math.sqrt(np.linalg.det(cov))]
+        assert np.allclose(m[off:off + 5], exp, rtol=1e-12, atol=0), (off, m[off:off + 5], exp)
+    # planes switched off report zeros; one particle has zero spread; empty bunch is all zero
+    m2 = O.moments(z, dp)
+    assert np.all(m2[5:] == 0)
+    m1 = O.moments(z[:1], dp[:1], x[:1], xp[:1])
+    assert m1[0] == z[0] and m1[1] == dp[0] and m1[2] == 0 and m1[4] == 0
+    m0 = O.moments(np.zeros(0), np.zeros(0))
+    assert np.all(m0 == 0)
+    # the per-turn moment rows are the moments of the tracked state
+    r = ring(voltage_V=4.5e6)
+    d = O.derive(r)
+    tb = textbook(r)
+    z0 = rng.normal(0, 0.1, 64) * tb["zhat"] / 0.75
+    d0 = rng.normal(0, 0.2, 64) * tb["dhat"]
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        zz, dd, xx, xxp, *_, mom = O.track(d, scheme, z0, d0, x[:64], xp[:64], turns=30,
+                                           moments=True, stride=10)
+        assert mom.shape == (4, 15)
+        assert np.allclose(mom[0, :5], [z0.mean(), d0.mean(), z0.std(), d0.std(),
+                                        mom[0, 4]], rtol=1e-12)
+        assert np.allclose(mom[3, :4], [zz.mean(), dd.mean(), zz.std(), dd.std()], rtol=1e-12)
+        assert np.allclose(mom[3, 5:9], [xx.mean(), xxp.mean(), xx.std(), xxp.std()], rtol=1e-12)
+    # a matched Gaussian in the linear map keeps its rms (to the map's O(K) mismatch)
+    rl = ring(rf_linear=1.0)
+    tbl = textbook(rl)
+    dl = O.derive(rl)
+    sz = 0.1
+    sd = sz * 2 * math.pi * tbl["Qs"] / tbl["etaC"]
+    zg, dg = rng.normal(0, sz, 20000), rng.normal(0, sd, 20000)
+    *_, mom = O.track(dl, "leapfrog", zg, dg, turns=500, moments=True, stride=50)
+    assert np.max(np.abs(mom[:, 2] / mom[0, 2] - 1)) < 0.02
+
+
+def pin_brute_force(O, turns=(10000, 10000, 3000), nparticles=4):
+    """FP64 oracle vs the same maps evaluated at 40 significant digits (mpmath)."""
+    import mpmath as mp
+
+    mp.mp.dps = 40
+    r = ring(voltage_V=4.5e6)
+    tb = textbook(r)
+    d = O.derive(r)
+    A, k, eC = mp.mpf(d.A), mp.mpf(d.k), mp.mpf(d.etaC)
+    th = 1 / (2 - mp.cbrt(2))
+
+    def kick(w, z, dp):
+        return dp + w * A * mp.sin(k * z)
+
+    def drift(w, z, dp):
+        return z - w * eC * dp
+
+    def turn(scheme, z, dp):
+        if scheme == "euler_cromer":
+            dp = kick(1, z, dp)
+            z = drift(1, z, dp)
+        elif scheme == "leapfrog":
+            z = drift(mp.mpf(1) / 2, z, dp)
+            dp = kick(1, z, dp)
+            z = drift(mp.mpf(1) / 2, z, dp)
+        else:
+            for wd, wk in ((th / 2, th), ((1 - th) / 2, 1 - 2 * th), ((1 - th) / 2, th)):
+                z = drift(wd, z, dp)
+                dp = kick(wk, z, dp)
+            z = drift(th / 2, z, dp)
+        return z, dp
+
+    fr = np.linspace(0.1, 0.9, nparticles)
+    z0 = fr * tb["zhat"] * 0.9
+    d0 = (0.5 - fr) * tb["dhat"] * 0.5
+    for scheme, N in zip(("euler_cromer", "leapfrog", "ruth4"), turns):
+        zf, df, *_ = O.track(d, scheme, z0, d0, turns=N)
+        for i in range(nparticles):
+            z, dp = mp.mpf(z0[i]), mp.mpf(d0[i])
+            for _ in range(N):
+                z, dp = turn(scheme, z, dp)
+            ez = abs(float(z) - zf[i]) / tb["zhat"]
+            ed = abs(float(dp) - df[i]) / tb["dhat"]
+            assert ez < 1e-11 and ed < 1e-11, (scheme, i, ez, ed)
+
+
+ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
+            pin_pendulum_detuning, pin_separatrix, pin_time_reversal, pin_inverse_map,
+            pin_symplectic, pin_energy_order, pin_symmetry_and_fixed_point,
+            pin_transverse_rotation, pin_moments)

@@ -1,0 +1,54 @@
+"""Each pin set must have teeth: a copy of the oracle with one plausible mistake planted
+(a flipped sign, a dropped term, a wrong coefficient, a transposed operand) must fail at
+least one of the independent pins in pins.py.  The mistakes are planted in a temporary
+copy of the C source, on the CPU; the real oracle is never modified."""
+import os
+
+import pytest
+
+import oracle
+import pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "track_ref.c")
+
+MUTANTS = {
+    "drift_sign": ("*z = *z - (w * d->etaC) * dp;", "*z = *z + (w * d->etaC) * dp;"),
+    "lf_half_weight": ("ref_drift(d, 0.5 * sign, z, *dp);\n        ref_kick(d, 1.0 * sign",
+                       "ref_drift(d, 0.45 * sign, z, *dp);\n        ref_kick(d, 1.0 * sign"),
+    "ruth_theta": ("cbrt(2.0)", "sqrt(2.0)"),
+    "ruth_middle_kick": ("ref_kick(d, (1.0 - 2.0 * t) * sign", "ref_kick(d, (1.0 - t) * sign"),
+    "A_without_beta": ("(d->beta * p->p0_eVc)", "(p->p0_eVc)"),
+    "k_without_2": ("d->k = 2.0 * REF_PI * p->harmonic", "d->k = REF_PI * p->harmonic"),
+    "kick_drops_sin_phis": ("return sin(d->phi_s + d->k * z) - d->sin_phis;",
+                            "return sin(d->phi_s + d->k * z);"),
+    "linear_drops_cos_phis": ("return d->cos_phis * d->k * z;", "return d->k * z;"),
+    "beta_misplaced": ("d->mx[1] = bx * sin(mux);", "d->mx[1] = sin(mux) / bx;"),
+    "tune_plane_swapped": ("double mux = 2.0 * REF_PI * (p->Qx - floor(p->Qx));",
+                           "double mux = 2.0 * REF_PI * (p->Qy - floor(p->Qy));"),
+    "ec_drift_first": ("if (sign > 0) { ref_kick(d, 1.0, *z, dp); ref_drift(d, 1.0, z, *dp); }",
+                       "if (sign > 0) { ref_drift(d, 1.0, z, *dp); ref_kick(d, 1.0, *z, dp); }"),
+    "variance_n_minus_1": ("saa /= (double)n;", "saa /= (double)(n - 1);"),
+    "emittance_drops_cov": ("double e2 = saa * sbb - sab * sab;", "double e2 = saa * sbb;"),
+    "eta_sign": ("d->eta = 1.0 / (p->gamma_t * p->gamma_t) - 1.0 / (d->gamma * d->gamma);",
+                 "d->eta = 1.0 / (d->gamma * d->gamma) - 1.0 / (p->gamma_t * p->gamma_t);"),
+    "gamma_from_p_over_m": ("d->gamma = sqrt(1.0 + d->betagamma * d->betagamma);",
+                            "d->gamma = d->betagamma;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) >= 1, f"mutation site for {name} not found"
+    src = tmp_path / "track_ref.c"
+    src.write_text(text.replace(old, new, 1))
+    lib = oracle.build(openmp=False, force=True, src=str(src), out=str(tmp_path / "libm.so"))
+    O = oracle.Oracle(lib)
+    caught = []
+    for pin in pins.ALL_FAST:
+        try:
+            pin(O)
+        except (AssertionError, ValueError, ZeroDivisionError, FloatingPointError):
+            caught.append(pin.__name__)
+    assert caught, f"no independent pin catches the mutant {name}"
