@@ -1,0 +1,506 @@
+// Host side of the C ABI declared in include/phtl.h: argument checking, FP64
+// derivation of the map constants, launch planning and the host-buffer path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_set>
+
+#include "internal.h"
+#include "handle.h"
+
+namespace phtl {
+
+namespace {
+
+std::mutex g_registry_mu;
+std::unordered_set<const phtl_handle*> g_registry;
+
+constexpr double kPi = 3.14159265358979323846;
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+void split_df(double v, float& hi, float& lo)
+{
+    hi = static_cast<float>(v);
+    lo = static_cast<float>(v - static_cast<double>(hi));
+}
+
+// Stage coefficients of each scheme (Sec. 1.1.2 readings, see phtl.h).
+void scheme_consts(const phtl_derived& d, int scheme, MapConsts& c)
+{
+    std::memset(c.dc, 0, sizeof(c.dc));
+    std::memset(c.kw, 0, sizeof(c.kw));
+    if (scheme == PHTL_EULER_CROMER) {
+        c.kw[0] = 1.0 * d.A;
+        c.dc[0] = 1.0 * d.etaC;
+    } else if (scheme == PHTL_LEAPFROG) {
+        c.dc[0] = 0.5 * d.etaC;
+        c.kw[0] = 1.0 * d.A;
+        c.dc[1] = 0.5 * d.etaC;
+    } else {
+        // Forest-Ruth: theta = 1 / (2 - 2^(1/3))
+        const double th = 1.0 / (2.0 - std::cbrt(2.0));
+        c.dc[0] = (0.5 * th) * d.etaC;
+        c.kw[0] = th * d.A;
+        c.dc[1] = (0.5 * (1.0 - th)) * d.etaC;
+        c.kw[1] = (1.0 - 2.0 * th) * d.A;
+        c.dc[2] = (0.5 * (1.0 - th)) * d.etaC;
+        c.kw[2] = th * d.A;
+        c.dc[3] = (0.5 * th) * d.etaC;
+    }
+    for (int i = 0; i < 4; ++i) split_df(c.dc[i], c.dc_hi[i], c.dc_lo[i]);
+    for (int j = 0; j < 3; ++j) split_df(c.kw[j], c.kw_hi[j], c.kw_lo[j]);
+}
+
+int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
+{
+    if (!finite_pos(p.circumference_m) || !finite_pos(p.gamma_t) || !finite_pos(p.p0_eVc) ||
+        !finite_pos(p.mass_eV) || !finite_pos(p.beta_x_m) || !finite_pos(p.beta_y_m) ||
+        p.harmonic <= 0 || !std::isfinite(p.charge_e) || !std::isfinite(p.voltage_V) ||
+        !std::isfinite(p.phi_s_rad) || !std::isfinite(p.Qx) || !std::isfinite(p.Qy))
+        return PHTL_E_INVALID;
+    std::memset(&d, 0, sizeof(d));
+    d.betagamma = p.p0_eVc / p.mass_eV;
+    d.gamma = std::sqrt(1.0 + d.betagamma * d.betagamma);
+    d.beta = d.betagamma / d.gamma;
+    d.eta = 1.0 / (p.gamma_t * p.gamma_t) - 1.0 / (d.gamma * d.gamma);
+    d.k = 2.0 * kPi * static_cast<double>(p.harmonic) / p.circumference_m;
+    d.A = p.charge_e * p.voltage_V / (d.beta * p.p0_eVc);
+    d.etaC = d.eta * p.circumference_m;
+    d.sin_phis = std::sin(p.phi_s_rad);
+    d.cos_phis = std::cos(p.phi_s_rad);
+    d.K = d.etaC * d.A * d.k * d.cos_phis;
+    d.Qs = d.K > 0.0 ? std::sqrt(d.K) / (2.0 * kPi) : 0.0;
+    d.bucket_half_length_m = kPi / d.k;
+    const double r = d.A / (d.k * d.etaC);
+    d.bucket_half_height = r > 0.0 ? 2.0 * std::sqrt(r) : 0.0;
+    const double mux = 2.0 * kPi * (p.Qx - std::floor(p.Qx));
+    const double muy = 2.0 * kPi * (p.Qy - std::floor(p.Qy));
+    d.mx[0] = std::cos(mux);
+    d.mx[1] = p.beta_x_m * std::sin(mux);
+    d.mx[2] = -std::sin(mux) / p.beta_x_m;
+    d.mx[3] = std::cos(mux);
+    d.my[0] = std::cos(muy);
+    d.my[1] = p.beta_y_m * std::sin(muy);
+    d.my[2] = -std::sin(muy) / p.beta_y_m;
+    d.my[3] = std::cos(muy);
+    if (p.voltage_V != 0.0 && !(d.K > 0.0 && d.K < 4.0)) return PHTL_E_UNSTABLE;
+
+    for (int s = 0; s < 3; ++s) {
+        MapConsts& c = mc[s];
+        std::memset(&c, 0, sizeof(c));
+        scheme_consts(d, s, c);
+        c.k = d.k;
+        c.phis = p.phi_s_rad;
+        c.sinphis = d.sin_phis;
+        c.lin = d.cos_phis * d.k;
+        c.linear = p.rf_linear != 0;
+        for (int i = 0; i < 4; ++i) {
+            c.mx[i] = d.mx[i];
+            c.my[i] = d.my[i];
+            split_df(d.mx[i], c.mx_hi[i], c.mx_lo[i]);
+            split_df(d.my[i], c.my_hi[i], c.my_lo[i]);
+        }
+        split_df(d.k, c.k_hi, c.k_lo);
+        split_df(p.phi_s_rad, c.phis_hi, c.phis_lo);
+        c.sinphis_f = static_cast<float>(d.sin_phis);
+        c.lin_f = static_cast<float>(c.lin);
+    }
+    return PHTL_OK;
+}
+
+}  // namespace
+
+int handle_stream(phtl_handle* h, cudaStream_t* out)
+{
+    if (!h->stream) {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            h->stream = nullptr;
+            return PHTL_E_CUDA;
+        }
+    }
+    *out = h->stream;
+    return PHTL_OK;
+}
+
+void release_handle_resources(phtl_handle* h)
+{
+    if (h->stream) {
+        cudaStreamSynchronize(h->stream);
+        cudaStreamDestroy(h->stream);
+        h->stream = nullptr;
+    }
+    cudaGetLastError();
+}
+
+bool handle_valid(const phtl_handle* h)
+{
+    if (!h) return false;
+    std::lock_guard<std::mutex> g(g_registry_mu);
+    return g_registry.count(h) != 0 && h->magic == kHandleMagic;
+}
+
+int ensure_device(phtl_handle* h)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PHTL_E_NODEVICE;
+    }
+    if (h->dev_ready && h->device == dev) return PHTL_OK;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PHTL_E_NODEVICE;
+    }
+    // the library is compiled for sm_103a only
+    if (prop.major != 10 || prop.minor != 3) return PHTL_E_NODEVICE;
+    h->device = dev;
+    h->nsm = prop.multiProcessorCount;
+    h->dev_ready = true;
+    return PHTL_OK;
+}
+
+// Particle-turns per launch that keep one launch near ~50-100 ms (Sec. 2.3: bounded
+// kernel duration; the turns-per-launch trade-off of Fig. turnspercall).
+int64_t auto_turns_per_launch(int dtype, int scheme, int64_t n)
+{
+    const double budget = dtype == PHTL_F64 ? 8e8 : 8e9;
+    const double w = scheme == PHTL_RUTH4 ? 3.0 : 1.0;
+    double t = budget / (w * static_cast<double>(std::max<int64_t>(n, 1)));
+    t = std::min(t, 1048576.0);
+    return std::max<int64_t>(1, static_cast<int64_t>(t));
+}
+
+// The per-turn variant is the persistent kernel family launched with one turn per
+// launch over a grid that covers every particle once: the state makes a round trip
+// through HBM each turn (Sec. 2.3's host-side turn loop).
+cudaError_t launch_perturn(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,
+                           int dtype, cudaStream_t s)
+{
+    return dtype == PHTL_F64 ? launch_track_f64(L, c, m, s) : launch_track_f32c(L, c, m, dtype, s);
+}
+
+int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block)
+{
+    return dtype == PHTL_F64 ? occupancy_f64(scheme, trans, mon, block)
+                             : occupancy_f32c(scheme, trans, mon, dtype, block);
+}
+
+int occupancy(int dtype, int scheme, bool trans, bool mon, int block, bool perturn)
+{
+    if (perturn) return occupancy_perturn(scheme, trans, mon, dtype, block);
+    if (dtype == PHTL_F64) return occupancy_f64(scheme, trans, mon, block);
+    return occupancy_f32c(scheme, trans, mon, dtype, block);
+}
+
+int check_track_args(const phtl_handle* h, void* const* c, int64_t n, int64_t turns,
+                     int integrator, int dtype)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (integrator < PHTL_EULER_CROMER || integrator > PHTL_RUTH4) return PHTL_E_INVALID;
+    if (dtype < PHTL_F64 || dtype > PHTL_F32CD) return PHTL_E_INVALID;
+    if (n < 0 || turns < 0) return PHTL_E_INVALID;
+    if (n > 0 && (!c[0] || !c[1])) return PHTL_E_INVALID;
+    if ((c[2] == nullptr) != (c[3] == nullptr)) return PHTL_E_INVALID;
+    if ((c[4] == nullptr) != (c[5] == nullptr)) return PHTL_E_INVALID;
+    const uintptr_t es = dtype == PHTL_F64 ? 8 : 4;
+    for (int i = 0; i < 6; ++i)
+        if (c[i] && (reinterpret_cast<uintptr_t>(c[i]) % es) != 0) return PHTL_E_INVALID;
+    return PHTL_OK;
+}
+
+// Enqueue the launches of one tracking call (persistent or per-turn family).
+int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int integrator,
+                  int dtype, cudaStream_t s, bool perturn, double* mon_rows, int64_t mon_cap,
+                  int64_t mon_stride)
+{
+    int rc = ensure_device(h);
+    if (rc != PHTL_OK) return rc;
+    if (mon_rows) {
+        const int64_t nrows = turns / mon_stride + 1;
+        if (nrows > mon_cap) return PHTL_E_INVALID;
+        if (cudaMemsetAsync(mon_rows, 0, static_cast<size_t>(nrows) * PHTL_MON_FIELDS * sizeof(double),
+                            s) != cudaSuccess) {
+            cudaGetLastError();
+            return PHTL_E_CUDA;
+        }
+    }
+    if (n == 0) return PHTL_OK;
+    if (turns == 0 && !mon_rows) return PHTL_OK;
+
+    const bool trans = c[2] != nullptr || c[4] != nullptr;
+    const bool mon = mon_rows != nullptr;
+    const int block = h->block > 0 ? h->block : (perturn ? 256 : 128);
+    const int es = dtype == PHTL_F64 ? 8 : 4;
+    const int ppt = perturn ? (dtype == PHTL_F64 ? 2 : 4) : (dtype == PHTL_F64 ? 2 : 4);
+    int64_t tpl = perturn ? 1 : (h->tpl > 0 ? h->tpl : auto_turns_per_launch(dtype, integrator, n));
+    tpl = std::min<int64_t>(tpl, 1 << 30);
+
+    bool vec = true;
+    for (int i = 0; i < 6; ++i)
+        if (c[i] && (reinterpret_cast<uintptr_t>(c[i]) % 16) != 0) vec = false;
+    // FP32C buffers are [hi | comp]: the comp half is 16-byte aligned only if n % 4 == 0
+    if (dtype != PHTL_F64 && (n * es) % 16 != 0) vec = false;
+
+    const int occ = occupancy(dtype, integrator, trans, mon, block, perturn);
+    if (occ <= 0) return PHTL_E_INVALID;
+    const int64_t chunk = static_cast<int64_t>(block) * ppt;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    const int64_t resident = static_cast<int64_t>(occ) * h->nsm;
+    int64_t cap = resident;
+    if (h->max_blocks > 0) cap = std::min<int64_t>(cap, h->max_blocks);
+    const int grid = static_cast<int>(perturn ? nchunks : std::min<int64_t>(nchunks, cap));
+
+    LaunchDesc L;
+    std::memset(&L, 0, sizeof(L));
+    for (int i = 0; i < 6; ++i) L.c[i] = c[i];
+    L.n = n;
+    L.scheme = integrator;
+    L.block = block;
+    L.grid = std::max(grid, 1);
+    L.vec = vec ? 1 : 0;
+    const MapConsts& mc = h->mc[integrator];
+
+    int64_t t0 = 0;
+    bool first = true;
+    do {
+        const int64_t nt = std::min<int64_t>(tpl, turns - t0);
+        L.nturns = static_cast<int32_t>(nt);
+        MonitorArgs m;
+        std::memset(&m, 0, sizeof(m));
+        if (mon) {
+            m.rows = mon_rows;
+            m.stride = mon_stride;
+            m.until = mon_stride - (t0 % mon_stride);
+            m.row = t0 / mon_stride + 1;
+            m.initial = first ? 1 : 0;
+        }
+        cudaError_t e;
+        if (perturn)
+            e = launch_perturn(L, mc, m, dtype, s);
+        else if (dtype == PHTL_F64)
+            e = launch_track_f64(L, mc, m, s);
+        else
+            e = launch_track_f32c(L, mc, m, dtype, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return PHTL_E_CUDA;
+        }
+        t0 += nt;
+        first = false;
+        ++h->stats.launches;
+    } while (t0 < turns);
+    h->stats.particle_turns += n * turns;
+    ++h->stats.calls;
+    return PHTL_OK;
+}
+
+int track_common(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                 int64_t n, int64_t turns, int integrator, int dtype, void* stream, bool perturn)
+{
+    void* c[6] = {z, dp, x, xp, y, yp};
+    int rc = check_track_args(h, c, n, turns, integrator, dtype);
+    if (rc != PHTL_OK) return rc;
+    return enqueue_track(h, c, n, turns, integrator, dtype, static_cast<cudaStream_t>(stream),
+                         perturn, h->mon_rows, h->mon_cap, h->mon_stride);
+}
+
+}  // namespace phtl
+
+using namespace phtl;
+
+extern "C" {
+
+int phtl_create(const phtl_params* params, phtl_handle** out)
+{
+    if (!params || !out) return PHTL_E_INVALID;
+    *out = nullptr;
+    phtl_handle* h = new (std::nothrow) phtl_handle();
+    if (!h) return PHTL_E_NOMEM;
+    h->params = *params;
+    int rc = derive(*params, h->derived, h->mc);
+    if (rc != PHTL_OK) {
+        delete h;
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> g(g_registry_mu);
+        g_registry.insert(h);
+    }
+    *out = h;
+    return PHTL_OK;
+}
+
+int phtl_destroy(phtl_handle* h)
+{
+    {
+        std::lock_guard<std::mutex> g(g_registry_mu);
+        if (!h || !g_registry.count(h) || h->magic != kHandleMagic) return PHTL_E_BADHANDLE;
+        g_registry.erase(h);
+    }
+    release_handle_resources(h);
+    h->magic = 0;
+    delete h;
+    return PHTL_OK;
+}
+
+int phtl_get_derived(const phtl_handle* h, phtl_derived* out)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (!out) return PHTL_E_INVALID;
+    *out = h->derived;
+    return PHTL_OK;
+}
+
+const char* phtl_strerror(int code)
+{
+    switch (code) {
+        case PHTL_OK: return "ok";
+        case PHTL_E_INVALID: return "invalid argument";
+        case PHTL_E_UNSTABLE: return "RF parameters give no stable bucket";
+        case PHTL_E_NOMEM: return "out of memory or over the memory budget";
+        case PHTL_E_CUDA: return "CUDA runtime error";
+        case PHTL_E_TIMEOUT: return "timed out";
+        case PHTL_E_CANCELLED: return "cancelled";
+        case PHTL_E_BADHANDLE: return "bad handle or ticket";
+        case PHTL_E_NODEVICE: return "no sm_103 CUDA device";
+        default: return "unknown error code";
+    }
+}
+
+const char* phtl_version(void) { return "phtl 0.1 sm_103a"; }
+
+int phtl_set_monitor(phtl_handle* h, double* rows, int64_t capacity_rows, int64_t stride)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (rows) {
+        if (capacity_rows < 1 || stride < 1) return PHTL_E_INVALID;
+        if (reinterpret_cast<uintptr_t>(rows) % 8 != 0) return PHTL_E_INVALID;
+    }
+    h->mon_rows = rows;
+    h->mon_cap = rows ? capacity_rows : 0;
+    h->mon_stride = rows ? stride : 1;
+    return PHTL_OK;
+}
+
+int phtl_set_tuning(phtl_handle* h, int32_t block_threads, int64_t turns_per_launch,
+                    int32_t max_blocks)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))
+        return PHTL_E_INVALID;
+    if (turns_per_launch < 0 || max_blocks < 0) return PHTL_E_INVALID;
+    h->block = block_threads;
+    h->tpl = turns_per_launch;
+    h->max_blocks = max_blocks;
+    return PHTL_OK;
+}
+
+int phtl_track(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+               int64_t n, int64_t turns, int integrator, int dtype, void* cuda_stream)
+{
+    return track_common(h, z, dp, x, xp, y, yp, n, turns, integrator, dtype, cuda_stream, false);
+}
+
+int phtl_track_perturn(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                       int64_t n, int64_t turns, int integrator, int dtype, void* cuda_stream)
+{
+    return track_common(h, z, dp, x, xp, y, yp, n, turns, integrator, dtype, cuda_stream, true);
+}
+
+int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                    int64_t n, int64_t turns, int integrator, int dtype, double* mon_rows,
+                    int64_t mon_stride)
+{
+    void* hc[6] = {z, dp, x, xp, y, yp};
+    int rc = check_track_args(h, hc, n, turns, integrator, dtype);
+    if (rc != PHTL_OK) return rc;
+    if (mon_rows && mon_stride < 1) return PHTL_E_INVALID;
+    rc = ensure_device(h);
+    if (rc != PHTL_OK) return rc;
+    cudaStream_t s = nullptr;
+    rc = handle_stream(h, &s);
+    if (rc != PHTL_OK) return rc;
+    const size_t per = (dtype == PHTL_F64 ? 8u : 8u) * static_cast<size_t>(n);  // n doubles or 2n floats
+    const int64_t nrows = mon_rows ? turns / mon_stride + 1 : 0;
+    const size_t mon_bytes = static_cast<size_t>(nrows) * PHTL_MON_FIELDS * sizeof(double);
+    void* dc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* dmon = nullptr;
+    auto cleanup = [&]() {
+        for (int i = 0; i < 6; ++i)
+            if (dc[i]) cudaFreeAsync(dc[i], s);
+        if (dmon) cudaFreeAsync(dmon, s);
+        cudaStreamSynchronize(s);
+    };
+    for (int i = 0; i < 6 && n > 0; ++i) {
+        if (!hc[i]) continue;
+        if (cudaMallocAsync(&dc[i], per, s) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return PHTL_E_NOMEM;
+        }
+        if (cudaMemcpyAsync(dc[i], hc[i], per, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return PHTL_E_CUDA;
+        }
+    }
+    if (mon_rows && cudaMallocAsync(reinterpret_cast<void**>(&dmon), mon_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return PHTL_E_NOMEM;
+    }
+    rc = enqueue_track(h, dc, n, turns, integrator, dtype, s, false, dmon, nrows,
+                       mon_rows ? mon_stride : 1);
+    if (rc == PHTL_OK) {
+        for (int i = 0; i < 6 && n > 0; ++i)
+            if (hc[i] && cudaMemcpyAsync(hc[i], dc[i], per, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                rc = PHTL_E_CUDA;
+        if (mon_rows && cudaMemcpyAsync(mon_rows, dmon, mon_bytes, cudaMemcpyDeviceToHost, s) !=
+                            cudaSuccess)
+            rc = PHTL_E_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = PHTL_E_CUDA;
+    cudaGetLastError();
+    cleanup();
+    return rc;
+}
+
+int phtl_get_stats(const phtl_handle* h, phtl_stats* out)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (!out) return PHTL_E_INVALID;
+    *out = h->stats;
+    return PHTL_OK;
+}
+
+int phtl_moments_from_sums(const double* row, double* out)
+{
+    if (!row || !out) return PHTL_E_INVALID;
+    for (int j = 0; j < 15; ++j) out[j] = 0.0;
+    const double n = row[0];
+    if (!(n > 0.0)) return PHTL_OK;
+    for (int plane = 0; plane < 3; ++plane) {
+        const double* s = row + 1 + 5 * plane;
+        double* o = out + 5 * plane;
+        const double ma = s[0] / n, mb = s[1] / n;
+        const double vaa = std::max(s[2] / n - ma * ma, 0.0);
+        const double vbb = std::max(s[3] / n - mb * mb, 0.0);
+        const double vab = s[4] / n - ma * mb;
+        o[0] = ma;
+        o[1] = mb;
+        o[2] = std::sqrt(vaa);
+        o[3] = std::sqrt(vbb);
+        o[4] = std::sqrt(std::max(vaa * vbb - vab * vab, 0.0));
+    }
+    return PHTL_OK;
+}
+
+}  // extern "C"

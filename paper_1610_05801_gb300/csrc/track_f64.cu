@@ -1,0 +1,294 @@
+// FP64 persistent multi-turn tracking kernel.
+//
+// Sec. 2.3 of the paper: particles are independent, turns are sequential, and the
+// turn loop belongs inside the kernel so that each particle's state stays in
+// registers between turns.  Here every thread owns P = 2 particles (one 128-bit load
+// and store per coordinate per launch), runs `nturns` turns of the chosen scheme
+// (Sec. 1.1.2) and the transverse matrix push (Sec. 1.1.1) on them, and adds the
+// per-turn moment sums into the monitor rows.  Blocks walk over particle chunks in a
+// grid-stride loop so the grid can be sized to the resident capacity of the GPU.
+//
+// On GB300 the FP64 pipe retires 2 DFMA per clock per SM (1/64 of FP32), so this
+// kernel is FP64-pipe bound: every FP64 operation per particle-turn counts.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "monitor.cuh"
+#include "sin_f64.cuh"
+
+namespace phtl {
+namespace {
+
+constexpr int P = 2;
+
+__device__ __forceinline__ double rf_force(const MapConsts& c, double z)
+{
+    if (c.linear) return c.lin * z;
+    return sin_f64(fma(c.k, z, c.phis)) - c.sinphis;
+}
+
+__device__ __forceinline__ void drift(double (&z)[P], const double (&d)[P], double dc)
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) z[p] = fma(-dc, d[p], z[p]);
+}
+
+__device__ __forceinline__ void kick(const double (&z)[P], double (&d)[P], double kw,
+                                     const MapConsts& c)
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) d[p] = fma(kw, rf_force(c, z[p]), d[p]);
+}
+
+// One turn of the scheme; stage order as in Sec. 1.1.2's readings (see phtl.h).
+template <int SCHEME>
+__device__ __forceinline__ void long_turn(double (&z)[P], double (&d)[P], const MapConsts& c)
+{
+    if (SCHEME == PHTL_EULER_CROMER) {
+        kick(z, d, c.kw[0], c);
+        drift(z, d, c.dc[0]);
+    } else if (SCHEME == PHTL_LEAPFROG) {
+        drift(z, d, c.dc[0]);
+        kick(z, d, c.kw[0], c);
+        drift(z, d, c.dc[1]);
+    } else {
+        drift(z, d, c.dc[0]);
+        kick(z, d, c.kw[0], c);
+        drift(z, d, c.dc[1]);
+        kick(z, d, c.kw[1], c);
+        drift(z, d, c.dc[2]);
+        kick(z, d, c.kw[2], c);
+        drift(z, d, c.dc[3]);
+    }
+}
+
+__device__ __forceinline__ void rotate(double (&u)[P], double (&v)[P], const double (&m)[4])
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double un = fma(m[1], v[p], m[0] * u[p]);
+        const double vn = fma(m[3], v[p], m[2] * u[p]);
+        u[p] = un;
+        v[p] = vn;
+    }
+}
+
+__device__ __forceinline__ void pair_sums(const double (&a)[P], const double (&b)[P], double* f)
+{
+    f[0] = a[0];
+    f[1] = b[0];
+    f[2] = a[0] * a[0];
+    f[3] = b[0] * b[0];
+    f[4] = a[0] * b[0];
+#pragma unroll
+    for (int p = 1; p < P; ++p) {
+        f[0] += a[p];
+        f[1] += b[p];
+        f[2] = fma(a[p], a[p], f[2]);
+        f[3] = fma(b[p], b[p], f[3]);
+        f[4] = fma(a[p], b[p], f[4]);
+    }
+}
+
+template <bool TRANS>
+__device__ __forceinline__ void record(const double (&z)[P], const double (&d)[P],
+                                       const double (&x)[P], const double (&xp)[P],
+                                       const double (&y)[P], const double (&yp)[P],
+                                       double cnt, bool hx, bool hy, double* smem, int parity,
+                                       double* rows, int64_t row)
+{
+    constexpr int NF = TRANS ? 16 : 8;
+    double f[NF];
+    f[0] = cnt;
+    pair_sums(z, d, f + 1);
+    if (TRANS) {
+        if (hx) {
+            pair_sums(x, xp, f + 6);
+        } else {
+#pragma unroll
+            for (int j = 6; j < 11; ++j) f[j] = 0.0;
+        }
+        if (hy) {
+            pair_sums(y, yp, f + 11);
+        } else {
+#pragma unroll
+            for (int j = 11; j < 16; ++j) f[j] = 0.0;
+        }
+    } else {
+        f[6] = 0.0;
+        f[7] = 0.0;
+    }
+    block_record<NF>(f, smem, parity, rows, row, TRANS ? 16 : 6);
+}
+
+__device__ __forceinline__ void load2(const double* __restrict__ g, int64_t base, int64_t n,
+                                      bool vec, double (&v)[P])
+{
+    if (vec && base + P <= n) {
+        const double2 t = __ldcs(reinterpret_cast<const double2*>(g + base));
+        v[0] = t.x;
+        v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) v[p] = (base + p < n) ? g[base + p] : 0.0;
+    }
+}
+
+__device__ __forceinline__ void store2(double* __restrict__ g, int64_t base, int64_t n,
+                                       bool vec, const double (&v)[P])
+{
+    if (vec && base + P <= n) {
+        __stcs(reinterpret_cast<double2*>(g + base), make_double2(v[0], v[1]));
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            if (base + p < n) g[base + p] = v[p];
+    }
+}
+
+template <int SCHEME, bool TRANS, bool MON>
+__global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
+{
+    extern __shared__ double smem[];
+    double* gz = static_cast<double*>(L.c[0]);
+    double* gd = static_cast<double*>(L.c[1]);
+    double* gx = static_cast<double*>(L.c[2]);
+    double* gxp = static_cast<double*>(L.c[3]);
+    double* gy = static_cast<double*>(L.c[4]);
+    double* gyp = static_cast<double*>(L.c[5]);
+    const bool hx = TRANS && gx != nullptr;
+    const bool hy = TRANS && gy != nullptr;
+    const bool vec = L.vec != 0;
+    const int64_t chunk = static_cast<int64_t>(blockDim.x) * P;
+    const int64_t nchunks = (L.n + chunk - 1) / chunk;
+    int parity = 0;
+
+    for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+        const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
+        double z[P], d[P], x[P], xp[P], y[P], yp[P];
+        load2(gz, base, L.n, vec, z);
+        load2(gd, base, L.n, vec, d);
+#pragma unroll
+        for (int p = 0; p < P; ++p) x[p] = xp[p] = y[p] = yp[p] = 0.0;
+        if (hx) {
+            load2(gx, base, L.n, vec, x);
+            load2(gxp, base, L.n, vec, xp);
+        }
+        if (hy) {
+            load2(gy, base, L.n, vec, y);
+            load2(gyp, base, L.n, vec, yp);
+        }
+        const int64_t left = L.n - base;
+        const double cnt = left >= P ? static_cast<double>(P) : (left > 0 ? static_cast<double>(left) : 0.0);
+
+        int64_t until = m.until, row = m.row;
+        if (MON && m.initial) {
+            record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, 0);
+            parity ^= 1;
+        }
+        for (int t = 0; t < L.nturns; ++t) {
+            long_turn<SCHEME>(z, d, c);
+            if (TRANS) {
+                if (hx) rotate(x, xp, c.mx);
+                if (hy) rotate(y, yp, c.my);
+            }
+            if (MON) {
+                if (--until == 0) {
+                    record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
+                    parity ^= 1;
+                    ++row;
+                    until = m.stride;
+                }
+            }
+        }
+        store2(gz, base, L.n, vec, z);
+        store2(gd, base, L.n, vec, d);
+        if (hx) {
+            store2(gx, base, L.n, vec, x);
+            store2(gxp, base, L.n, vec, xp);
+        }
+        if (hy) {
+            store2(gy, base, L.n, vec, y);
+            store2(gyp, base, L.n, vec, yp);
+        }
+    }
+}
+
+template <int S, bool T, bool M>
+const void* kernel_ptr()
+{
+    return reinterpret_cast<const void*>(&k_track_f64<S, T, M>);
+}
+
+const void* select_kernel(int scheme, bool trans, bool mon)
+{
+#define PHTL_SEL(S)                                                              \
+    if (scheme == S) {                                                           \
+        if (trans) return mon ? kernel_ptr<S, true, true>() : kernel_ptr<S, true, false>(); \
+        return mon ? kernel_ptr<S, false, true>() : kernel_ptr<S, false, false>();         \
+    }
+    PHTL_SEL(PHTL_EULER_CROMER)
+    PHTL_SEL(PHTL_LEAPFROG)
+    PHTL_SEL(PHTL_RUTH4)
+#undef PHTL_SEL
+    return nullptr;
+}
+
+}  // namespace
+
+int occupancy_f64(int scheme, bool trans, bool mon, int block)
+{
+    const void* k = select_kernel(scheme, trans, mon);
+    if (!k) return 0;
+    int nb = 0;
+    const size_t smem = mon ? 2u * (block / 32) * 16 * sizeof(double) : 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_track_f64(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,
+                             cudaStream_t s)
+{
+    const bool trans = L.c[2] != nullptr || L.c[4] != nullptr;
+    const bool mon = m.rows != nullptr;
+    const void* k = select_kernel(L.scheme, trans, mon);
+    if (!k) return cudaErrorInvalidValue;
+    const size_t smem = mon ? 2u * (L.block / 32) * 16 * sizeof(double) : 0;
+    LaunchDesc Lc = L;
+    MapConsts cc = c;
+    MonitorArgs mm = m;
+    void* args[] = {&Lc, &cc, &mm};
+    return cudaLaunchKernel(k, dim3(L.grid), dim3(L.block), args, smem, s);
+}
+
+namespace {
+
+__global__ void k_eval_sin(const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                           int which)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        y[i] = which == 0 ? sin_f64(x[i]) : sin(x[i]);
+}
+
+}  // namespace
+
+}  // namespace phtl
+
+extern "C" int phtl_eval_sin(const double* x, double* y, int64_t n, int which, void* stream)
+{
+    if (n < 0 || (which != 0 && which != 1)) return PHTL_E_INVALID;
+    if (n > 0 && (!x || !y)) return PHTL_E_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PHTL_E_NODEVICE;
+    }
+    if (n == 0) return PHTL_OK;
+    const int block = 256;
+    const int64_t want = (n + block - 1) / block;
+    const int grid = static_cast<int>(want < 152 * 16 ? want : 152 * 16);
+    phtl::k_eval_sin<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n, which);
+    if (cudaGetLastError() != cudaSuccess) return PHTL_E_CUDA;
+    return PHTL_OK;
+}

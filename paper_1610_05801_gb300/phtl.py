@@ -1,0 +1,293 @@
+"""Thin ctypes binding of libphtl.so (C ABI in include/phtl.h).
+
+Argument marshalling only: every step of the tracking runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams; tensors are passed as raw
+device pointers.  There is no CPU fallback: if the library is missing or the GPU
+is not an sm_103 device, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphtl.so")
+
+OK = 0
+E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_TIMEOUT, E_CANCELLED, E_BADHANDLE, E_NODEVICE = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
+EULER_CROMER, LEAPFROG, RUTH4 = 0, 1, 2
+F64, F32C, F32CD = 0, 1, 2
+MON_FIELDS = 16
+INTEGRATORS = {"euler_cromer": EULER_CROMER, "ec": EULER_CROMER, "leapfrog": LEAPFROG,
+               "lf": LEAPFROG, "ruth4": RUTH4}
+DTYPES = {"f64": F64, "f32c": F32C, "f32cd": F32CD}
+MOMENT_NAMES = (
+    "mean_z", "mean_dp", "rms_z", "rms_dp", "eps_z",
+    "mean_x", "mean_xp", "rms_x", "rms_xp", "eps_x",
+    "mean_y", "mean_yp", "rms_y", "rms_yp", "eps_y",
+)
+
+
+class PhtlError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+class Params(C.Structure):
+    _fields_ = [("circumference_m", C.c_double), ("gamma_t", C.c_double), ("p0_eVc", C.c_double),
+                ("mass_eV", C.c_double), ("charge_e", C.c_double), ("voltage_V", C.c_double),
+                ("phi_s_rad", C.c_double), ("beta_x_m", C.c_double), ("beta_y_m", C.c_double),
+                ("Qx", C.c_double), ("Qy", C.c_double), ("harmonic", C.c_int32),
+                ("rf_linear", C.c_int32)]
+
+
+class Derived(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "betagamma", "gamma", "beta", "eta", "k", "A", "etaC", "sin_phis", "cos_phis", "K", "Qs",
+        "bucket_half_length_m", "bucket_half_height")] + [("mx", C.c_double * 4),
+                                                          ("my", C.c_double * 4)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("particle_turns", C.c_int64), ("calls", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _int = C.c_void_p, C.c_int64, C.c_int
+
+# name -> (restype, argtypes); every symbol include/phtl.h declares
+SIGNATURES = {
+    "phtl_create": (_int, [C.POINTER(Params), C.POINTER(_vp)]),
+    "phtl_destroy": (_int, [_vp]),
+    "phtl_get_derived": (_int, [_vp, C.POINTER(Derived)]),
+    "phtl_strerror": (C.c_char_p, [_int]),
+    "phtl_version": (C.c_char_p, []),
+    "phtl_set_monitor": (_int, [_vp, _vp, _i64, _i64]),
+    "phtl_set_tuning": (_int, [_vp, C.c_int32, _i64, C.c_int32]),
+    "phtl_track": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _int, _int, _vp]),
+    "phtl_track_perturn": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _int, _int, _vp]),
+    "phtl_track_host": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _int, _int, _vp, _i64]),
+    "phtl_moments_from_sums": (_int, [_vp, _vp]),
+    "phtl_get_stats": (_int, [_vp, C.POINTER(Stats)]),
+    "phtl_eval_sin": (_int, [_vp, _vp, _i64, _int, _vp]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libphtl.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"{path} not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().phtl_strerror(int(code)).decode()
+    except ImportError:
+        return f"error {code}"
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise PhtlError(rc, what)
+
+
+def make_params(**kw) -> Params:
+    p = Params()
+    defaults = dict(mass_eV=938.27208816e6, charge_e=1.0, phi_s_rad=0.0, beta_x_m=1.0,
+                    beta_y_m=1.0, Qx=0.0, Qy=0.0, rf_linear=0, voltage_V=0.0)
+    defaults.update(kw)
+    for k, v in defaults.items():
+        setattr(p, k, int(v) if k in ("harmonic", "rf_linear") else float(v))
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(t)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _integrator(i):
+    return INTEGRATORS[i] if isinstance(i, str) else int(i)
+
+
+def _dtype(d):
+    return DTYPES[d] if isinstance(d, str) else int(d)
+
+
+class Ring:
+    """A phtl handle: ring/RF parameters plus derived FP64 constants (phtl_create)."""
+
+    def __init__(self, **params):
+        self._lib = load()
+        self.params = make_params(**params)
+        h = _vp()
+        _check(self._lib.phtl_create(C.byref(self.params), C.byref(h)), "phtl_create")
+        self._h = h
+        self._monitor = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.phtl_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def derived(self) -> Derived:
+        d = Derived()
+        _check(self._lib.phtl_get_derived(self._h, C.byref(d)), "phtl_get_derived")
+        return d
+
+    def stats(self) -> Stats:
+        st = Stats()
+        _check(self._lib.phtl_get_stats(self._h, C.byref(st)), "phtl_get_stats")
+        return st
+
+    def set_tuning(self, block_threads: int = 0, turns_per_launch: int = 0, max_blocks: int = 0):
+        _check(self._lib.phtl_set_tuning(self._h, int(block_threads), int(turns_per_launch),
+                                         int(max_blocks)), "phtl_set_tuning")
+
+    def set_monitor(self, rows=None, stride: int = 1):
+        """rows: a CUDA float64 tensor of shape (capacity, 16), or None to detach."""
+        if rows is None:
+            _check(self._lib.phtl_set_monitor(self._h, None, 0, 1), "phtl_set_monitor")
+            self._monitor = None
+            return
+        _check_tensor(rows, "float64", "monitor")
+        assert rows.dim() == 2 and rows.shape[1] == MON_FIELDS
+        _check(self._lib.phtl_set_monitor(self._h, rows.data_ptr(), rows.shape[0], int(stride)),
+               "phtl_set_monitor")
+        self._monitor = rows  # keep it alive while attached
+
+    def _track(self, fn, z, dp, x, xp, y, yp, turns, integrator, dtype, stream):
+        dt = _dtype(dtype)
+        want = "float64" if dt == F64 else "float32"
+        bufs = (z, dp, x, xp, y, yp)
+        for name, b in zip(("z", "dp", "x", "xp", "y", "yp"), bufs):
+            if b is not None:
+                _check_tensor(b, want, name)
+        n = z.numel() if dt == F64 else z.numel() // 2
+        for b in bufs:
+            if b is not None and b.numel() != z.numel():
+                raise ValueError("all coordinate buffers must have the same length")
+        rc = fn(self._h, *[_ptr(b) for b in bufs], n, int(turns), _integrator(integrator), dt,
+                _stream_ptr(stream))
+        _check(rc, fn.__name__)
+
+    def track(self, z, dp, x=None, xp=None, y=None, yp=None, turns=1, integrator="leapfrog",
+              dtype="f64", stream=None):
+        """Persistent multi-turn tracking in place (phtl_track); stream-ordered."""
+        self._track(self._lib.phtl_track, z, dp, x, xp, y, yp, turns, integrator, dtype, stream)
+
+    def track_perturn(self, z, dp, x=None, xp=None, y=None, yp=None, turns=1,
+                      integrator="leapfrog", dtype="f64", stream=None):
+        """One launch per turn (phtl_track_perturn); stream-ordered."""
+        self._track(self._lib.phtl_track_perturn, z, dp, x, xp, y, yp, turns, integrator, dtype,
+                    stream)
+
+    def track_host(self, z, dp, x=None, xp=None, y=None, yp=None, turns=1,
+                   integrator="leapfrog", dtype="f64", mon_rows=None, mon_stride=1):
+        """End-to-end call on host buffers (numpy arrays or CPU tensors, ideally pinned):
+        allocate, copy in, track, copy out, free (phtl_track_host); synchronous."""
+        dt = _dtype(dtype)
+        bufs = (z, dp, x, xp, y, yp)
+        n = _numel(z) if dt == F64 else _numel(z) // 2
+        rc = self._lib.phtl_track_host(self._h, *[_ptr(b) for b in bufs], n, int(turns),
+                                       _integrator(integrator), dt, _ptr(mon_rows),
+                                       int(mon_stride))
+        _check(rc, "phtl_track_host")
+
+
+def _numel(b):
+    return b.numel() if hasattr(b, "numel") and callable(b.numel) else b.size
+
+
+def _check_tensor(t, dtype: str, name: str):
+    if not hasattr(t, "is_cuda") or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype}":
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def moments_from_sums(rows) -> np.ndarray:
+    """Moments (mean, rms, emittance per plane; see MOMENT_NAMES) of monitor rows
+    (array-like (..., 16) of raw sums) via phtl_moments_from_sums."""
+    lib = load()
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.float64)).reshape(-1, MON_FIELDS)
+    out = np.zeros((r.shape[0], 15))
+    for i in range(r.shape[0]):
+        _check(lib.phtl_moments_from_sums(r[i].ctypes.data, out[i].ctypes.data),
+               "phtl_moments_from_sums")
+    return out.reshape(np.asarray(rows).shape[:-1] + (15,))
+
+
+def split_f32c(a: np.ndarray) -> np.ndarray:
+    """FP64 values -> the FP32C layout [hi(n) | comp(n)] (hi = nearest float, comp = rest)."""
+    a = np.asarray(a, dtype=np.float64)
+    hi = a.astype(np.float32)
+    lo = (a - hi.astype(np.float64)).astype(np.float32)
+    return np.concatenate([hi, lo])
+
+
+def join_f32c(b) -> np.ndarray:
+    """FP32C layout [hi | comp] -> FP64 values hi + comp."""
+    b = np.asarray(b, dtype=np.float32)
+    n = b.shape[0] // 2
+    return b[:n].astype(np.float64) + b[n:].astype(np.float64)
+
+
+def eval_sin(x, which: int = 0, stream=None):
+    """Device sine of a CUDA float64 tensor: which=0 the library's FP64 sine, 1 CUDA's."""
+    import torch
+
+    _check_tensor(x, "float64", "x")
+    y = torch.empty_like(x)
+    _check(load().phtl_eval_sin(x.data_ptr(), y.data_ptr(), x.numel(), int(which),
+                                _stream_ptr(stream)), "phtl_eval_sin")
+    return y

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances (written here, derived in the design doc):
+  FP64 path  : per-particle relative error <= 1e-10 after up to 1e4 turns for particles
+               inside 90 % of the separatrix (error relative to the particle's own
+               amplitude, see helpers.py); monitor moments <= 1e-9 relative.
+  FP32C path : moments (rms z, rms delta, emittance; means relative to the rms) within
+               1e-5 of the FP64 oracle after 1e4 turns, and per-particle errors <= 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import helpers
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1610_05801_gb300 import phtl  # noqa: E402
+
+SCHEMES = ("euler_cromer", "leapfrog", "ruth4")
+DEV = "cuda:0"
+
+
+def _dev(a, dtype="f64"):
+    if a is None:
+        return None
+    if dtype == "f64":
+        return torch.tensor(a, dtype=torch.float64, device=DEV)
+    return torch.tensor(phtl.split_f32c(a), dtype=torch.float32, device=DEV)
+
+
+def _host(t, dtype="f64"):
+    if t is None:
+        return None
+    a = t.cpu().numpy()
+    return a if dtype == "f64" else phtl.join_f32c(a)
+
+
+def run_gpu(inp, scheme, turns, dtype="f64", transverse=True, stride=None, tuning=None,
+            perturn=False, offset=0):
+    """Track inp's particles on the GPU; returns (coords, moments or None)."""
+    keys = ("z", "dp", "x", "xp", "y", "yp") if transverse else ("z", "dp")
+    R = phtl.Ring(**inp["ring"])
+    if tuning:
+        R.set_tuning(**tuning)
+    bufs = []
+    for k in keys:
+        a = inp[k]
+        if offset:
+            # place the data at an element offset inside a larger allocation (misaligned)
+            base = _dev(np.concatenate([np.zeros(offset), a]), dtype) if dtype == "f64" else None
+            if base is None:
+                raise ValueError("offset only for f64")
+            bufs.append(base[offset:])
+        else:
+            bufs.append(_dev(a, dtype))
+    while len(bufs) < 6:
+        bufs.append(None)
+    mon = None
+    if stride:
+        mon = torch.full((turns // stride + 1, phtl.MON_FIELDS), float("nan"),
+                         dtype=torch.float64, device=DEV)
+        R.set_monitor(mon, stride=stride)
+    fn = R.track_perturn if perturn else R.track
+    fn(*bufs, turns=turns, integrator=scheme, dtype=dtype)
+    torch.cuda.synchronize()
+    out = [_host(b, dtype) for b in bufs]
+    moms = phtl.moments_from_sums(mon.cpu().numpy()) if stride else None
+    R.close()
+    return out, moms
+
+
+def run_ref(inp, scheme, turns, transverse=True, stride=None):
+    args = [inp["z"], inp["dp"]]
+    if transverse:
+        args += [inp["x"], inp["xp"], inp["y"], inp["yp"]]
+    r = oracle.track(inp["d"], scheme, *args, turns=turns, moments=bool(stride),
+                     stride=stride or 1)
+    return list(r[:6]), r[6]
+
+
+def moment_errors(d, mg, mr):
+    """Relative moment errors: means relative to the corresponding rms, rms relative to
+    itself, emittance relative to rms_u * rms_u' (its natural scale; the emittance of a
+    two-particle bunch is exactly zero)."""
+    e = []
+    for off in (0, 5, 10):
+        if mr[0, off + 2] == 0:
+            continue
+        for j, ref_scale in ((0, 2), (1, 3)):
+            e.append(np.abs(mg[:, off + j] - mr[:, off + j]) / mr[:, off + ref_scale])
+        for j in (2, 3):
+            e.append(np.abs(mg[:, off + j] - mr[:, off + j]) / mr[:, off + j])
+        e.append(np.abs(mg[:, off + 4] - mr[:, off + 4]) / (mr[:, off + 2] * mr[:, off + 3]))
+    return float(np.max(np.vstack(e)))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("transverse", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 1001, 4099])
+def test_f64_small_sizes(scheme, transverse, n):
+    inp = helpers.inputs(n, seed=n, transverse=transverse)
+    turns = 1000
+    got, mg = run_gpu(inp, scheme, turns, transverse=transverse, stride=7,
+                      tuning=dict(block_threads=32, turns_per_launch=333))
+    ref, mr = run_ref(inp, scheme, turns, transverse=transverse, stride=7)
+    err = helpers.rel_errors(inp["d"], ref, got, inp["z"], inp["dp"])
+    assert np.max(err) < 1e-10, np.max(err)
+    assert mg.shape == mr.shape
+    d = inp["d"]
+    zb, db = math.pi / d.k, 2 * math.sqrt(d.A / (d.k * d.etaC))
+    assert np.allclose(mg[:, 0], mr[:, 0], rtol=0, atol=1e-10 * zb)
+    assert np.allclose(mg[:, 1], mr[:, 1], rtol=0, atol=1e-10 * db)
+    if n > 1:
+        assert moment_errors(inp["d"], mg, mr) < 1e-9
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_f64_1e4_turns_inside_90pct(scheme):
+    """The stated tolerance: <= 1e-10 per particle after 1e4 turns, 90 % separatrix."""
+    inp = helpers.inputs(3000, seed=11, transverse=True, sep_frac=0.9, sigma_z=0.25)
+    turns = 10000
+    got, mg = run_gpu(inp, scheme, turns, stride=100)
+    ref, mr = run_ref(inp, scheme, turns, stride=100)
+    err = helpers.rel_errors(inp["d"], ref, got, inp["z"], inp["dp"])
+    assert np.max(err) < 1e-10, (np.max(err), np.argmax(err))
+    assert moment_errors(inp["d"], mg, mr) < 1e-9
+
+
+def test_f64_grid_stride_and_launch_chunking_are_invisible():
+    """Different grids, block sizes and turns-per-launch give bitwise identical particles."""
+    inp = helpers.inputs(5000, seed=3)
+    a, _ = run_gpu(inp, "ruth4", 500, tuning=dict(block_threads=64, turns_per_launch=37,
+                                                  max_blocks=3))
+    b, _ = run_gpu(inp, "ruth4", 500, tuning=dict(block_threads=256, turns_per_launch=500))
+    c, _ = run_gpu(inp, "ruth4", 500)
+    for u, v, w in zip(a, b, c):
+        assert np.array_equal(u, v) and np.array_equal(u, w)
+
+
+def test_f64_perturn_variant_equals_persistent():
+    inp = helpers.inputs(2049, seed=5)
+    for scheme in SCHEMES:
+        a, ma = run_gpu(inp, scheme, 200, perturn=True, stride=10)
+        b, mb = run_gpu(inp, scheme, 200, stride=10)
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v)
+        assert np.allclose(ma, mb, rtol=1e-12, atol=0)
+
+
+def test_f64_misaligned_pointers_take_the_scalar_path():
+    inp = helpers.inputs(1003, seed=9)
+    got, _ = run_gpu(inp, "leapfrog", 300, offset=1)
+    ref, _ = run_ref(inp, "leapfrog", 300)
+    err = helpers.rel_errors(inp["d"], ref, got, inp["z"], inp["dp"])
+    assert np.max(err) < 1e-10
+
+
+def test_zero_turns_and_empty_bunch():
+    inp = helpers.inputs(64, seed=1)
+    got, mg = run_gpu(inp, "leapfrog", 0, stride=1)
+    assert np.array_equal(got[0], inp["z"]) and np.array_equal(got[1], inp["dp"])
+    assert mg.shape == (1, 15)
+    mr = oracle.moments(inp["z"], inp["dp"], inp["x"], inp["xp"], inp["y"], inp["yp"])
+    assert np.allclose(mg[0], mr, rtol=1e-12, atol=1e-18)
+    R = phtl.Ring(**inp["ring"])
+    mon = torch.full((11, 16), float("nan"), dtype=torch.float64, device=DEV)
+    R.set_monitor(mon, stride=1)
+    e = torch.zeros(0, dtype=torch.float64, device=DEV)
+    R.track(e, e, turns=10)
+    torch.cuda.synchronize()
+    assert torch.all(mon == 0)
+    R.close()
+
+
+def test_linear_mode_matches_closed_form():
+    """rf_linear: the GPU leap-frog map equals the closed-form matrix power."""
+    import pins
+
+    r = pins.ring(rf_linear=1.0, voltage_V=4.5e6)
+    tb = pins.textbook(r)
+    K, eC, a = tb["K"], tb["etaC"], tb["a"]
+    M = np.array([[1 - K / 2, -eC * (1 - K / 4)], [a, 1 - K / 2]])
+    mu = 2.0 * math.asin(math.sqrt(K) / 2.0)
+    N = 5000
+    MN = (math.sin(N * mu) * M - math.sin((N - 1) * mu) * np.eye(2)) / math.sin(mu)
+    ring = dict(r, harmonic=int(r["harmonic"]), rf_linear=1)
+    R = phtl.Ring(**ring)
+    z = torch.tensor([0.05, -0.1], dtype=torch.float64, device=DEV)
+    d = torch.tensor([2e-4, 1e-4], dtype=torch.float64, device=DEV)
+    R.track(z, d, turns=N, integrator="leapfrog")
+    torch.cuda.synchronize()
+    for i, (z0, d0) in enumerate(((0.05, 2e-4), (-0.1, 1e-4))):
+        ez, ed = MN @ np.array([z0, d0])
+        assert abs(z[i].item() - ez) < 1e-11 * 0.2
+        assert abs(d[i].item() - ed) < 1e-11 * 2e-3
+    R.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32c", "f32cd"])
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_f32c_moments_and_particles(dtype, scheme):
+    inp = helpers.inputs(4096 + 7, seed=21)
+    turns = 10000
+    got, mg = run_gpu(inp, scheme, turns, dtype=dtype, stride=100)
+    ref, mr = run_ref(inp, scheme, turns, stride=100)
+    assert moment_errors(inp["d"], mg, mr) < 1e-5
+    # per particle: the SFU sine's absolute error (~2^-21 on [-pi, pi]) acts as a small
+    # perturbation of the potential, i.e. a tune shift, so phases drift apart slowly
+    err = helpers.rel_errors(inp["d"], ref, got, inp["z"], inp["dp"])
+    assert np.max(err) < 1e-2, np.max(err)
+    assert np.median(err) < 1e-4, np.median(err)
