@@ -183,6 +183,166 @@ int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* 
                     int64_t n, int64_t turns, int integrator, int dtype, double* mon_rows,
                     int64_t mon_stride);
 
+/* ---- batched launch (many independent bunches in one graph-captured launch) ------------ */
+
+/* One bunch of a batch.  Particles are independent and turns sequential (Sec. 2.3), so
+ * bunches of different sizes, turn counts, RF voltages, integrators and arithmetic can
+ * share launches.  The ring (C, h, p0, gamma_t, phi_s, transverse optics) is the handle's;
+ * voltage_V is this bunch's own RF voltage.                                            */
+typedef struct phtl_job {
+    void* c[6];           /* z, dp, x, xp, y, yp: device pointers, layout as phtl_track;
+                             x/xp and y/yp pairs may be NULL                              */
+    double* mon_rows;     /* device monitor rows of this bunch, or NULL                   */
+    int64_t mon_capacity; /* rows at mon_rows (>= turns / mon_stride + 1)                  */
+    int64_t mon_stride;   /* >= 1 when mon_rows is set                                     */
+    int64_t n;            /* macro-particles                                               */
+    int64_t turns;        /* turns tracked by each run of the batch                        */
+    double voltage_V;     /* RF voltage of this bunch                                      */
+    int32_t integrator;   /* PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4                 */
+    int32_t dtype;        /* PHTL_F64 | PHTL_F32C | PHTL_F32CD                              */
+} phtl_job;
+
+typedef struct phtl_batch phtl_batch; /* opaque, library-owned */
+
+/* Launch shape chosen by the autotuner (or set with phtl_set_tuning). */
+typedef struct phtl_tuning {
+    int32_t block_threads;
+    int32_t pad_;
+    int64_t turns_per_launch;
+    double particle_turns_per_s; /* the probe's measured throughput                        */
+} phtl_tuning;
+
+typedef struct phtl_batch_info {
+    int32_t njobs;
+    int32_t graph;                       /* 1: runs replay a captured CUDA graph          */
+    int32_t block_threads[3];            /* per arithmetic (PHTL_F64, F32C, F32CD); 0 = none */
+    int32_t pad_;
+    int64_t turns_per_launch[3];
+    double probe_particle_turns_per_s[3];
+    int64_t launches_per_run;            /* kernel launches in one run (known after a run) */
+    int64_t tiles_first_launch;          /* blocks of the first chunk launch, all groups   */
+    int64_t particle_turns_per_run;      /* sum of n * turns                              */
+} phtl_batch_info;
+
+/* Project-written autotuner: times the batched kernel of `dtype`/`integrator` at block
+ * sizes 64, 128 and 256 on scratch particles that fill the GPU once (the library
+ * allocates and frees them; the call synchronises), keeps the fastest block, and picks
+ * the turns per launch that make a launch over `active_particles` particles last about
+ * target_launch_ms.  Errors: PHTL_E_BADHANDLE, PHTL_E_INVALID, PHTL_E_NODEVICE,
+ * PHTL_E_CUDA.                                                                          */
+int phtl_autotune(phtl_handle* h, int dtype, int integrator, int64_t active_particles,
+                  double target_launch_ms, phtl_tuning* out);
+
+/* Build a batch: validates every job (as phtl_track, plus a stability check of each
+ * bunch's voltage -> PHTL_E_UNSTABLE), groups the jobs by arithmetic, sorts each group by
+ * turns (longest first), uploads a device job table, and fixes the launch shape (the
+ * handle's tuning if both block and turns per launch are set, else phtl_autotune with a
+ * 20 ms target).  use_graph != 0: the first run captures its launches into a CUDA graph
+ * that later runs replay.  The caller's buffers must stay valid until
+ * phtl_batch_destroy.  Synchronous set-up.                                             */
+int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32_t use_graph,
+                      phtl_batch** out);
+
+/* Enqueue one run on cuda_stream: every job advances by its `turns`, its monitor (if
+ * any) rewritten from row 0.  A job's particles come out bitwise as phtl_track would give
+ * them.  Stream-ordered.  Errors: PHTL_E_BADHANDLE, PHTL_E_CUDA.                         */
+int phtl_batch_run(phtl_batch* b, void* cuda_stream);
+
+int phtl_batch_info_get(const phtl_batch* b, phtl_batch_info* out);
+
+/* Synchronise the device, free the job tables and graph.  Errors: PHTL_E_BADHANDLE.     */
+int phtl_batch_destroy(phtl_batch* b);
+
+/* ---- serving loop (continuous batching) ------------------------------------------------- */
+
+/* Job states reported by phtl_poll / phtl_wait. */
+enum { PHTL_QUEUED = 0, PHTL_RUNNING = 1, PHTL_DONE = 2, PHTL_FAILED = 3, PHTL_CANCELLED = 4 };
+
+typedef struct phtl_server_config {
+    int64_t memory_budget_bytes; /* device bytes admitted jobs may hold (state + monitor),
+                                    resident states included; 0 = 150e9                  */
+    int32_t max_active;          /* jobs tracked concurrently (slots); 0 = 64              */
+    int32_t block_threads;       /* 0 = autotuned per arithmetic                          */
+    int64_t chunk_turns_f64;     /* turns per scheduling round for FP64 jobs; 0 = chosen
+                                    every round for a ~target_round_ms round               */
+    int64_t chunk_turns_f32;     /* the same for PHTL_F32C / PHTL_F32CD jobs               */
+    double target_round_ms;      /* 0 = 20 ms                                              */
+} phtl_server_config;
+
+/* One tracking request: host buffers in, host buffers out. */
+typedef struct phtl_request {
+    const void* in[6];      /* host inputs z, dp, x, xp, y, yp (layout as phtl_track;
+                               x/xp and y/yp pairs may be NULL).  Ignored on resume.       */
+    void* out[6];           /* host outputs, same planes as in[] (may alias in[]), written
+                               before the job turns PHTL_DONE                              */
+    double* mon_rows;       /* host rows for turns/mon_stride + 1 monitor rows, or NULL    */
+    int64_t mon_stride;
+    int64_t n;              /* macro-particles                                            */
+    int64_t turns;
+    double voltage_V;       /* this job's RF voltage (the ring is the handle's)           */
+    int32_t integrator;
+    int32_t dtype;
+    uint64_t resume_ticket; /* nonzero: continue from that PHTL_DONE job's resident device
+                               state (same n, dtype and planes; given by out[])            */
+    int32_t keep_resident;  /* nonzero: keep the device state after DONE for a resume;
+                               it counts against the budget until phtl_release           */
+    int32_t pad_;
+} phtl_request;
+
+typedef struct phtl_status {
+    int32_t state;          /* PHTL_QUEUED .. PHTL_CANCELLED                              */
+    int32_t error;          /* PHTL_OK, or the error of a FAILED / CANCELLED job           */
+    int64_t turns_done;
+    int64_t t_submit_ns, t_admit_ns, t_done_ns; /* steady clock                          */
+} phtl_status;
+
+typedef struct phtl_server_stats {
+    int64_t submitted, completed, failed, cancelled, queued, active;
+    int64_t bytes_in_use, bytes_peak;
+    int64_t rounds, launches;
+    double particle_turns;  /* completed work                                            */
+    double busy_s;          /* time spent in scheduling rounds                            */
+    double p50_latency_s, p99_latency_s, mean_latency_s; /* submit -> done, DONE jobs     */
+    double throughput_pts;  /* particle_turns / (last done - first submit)               */
+} phtl_server_stats;
+
+/* Start the serving loop of a handle: a worker thread that admits queued requests in
+ * arrival order while a slot is free and their device bytes fit the budget, tracks all
+ * admitted jobs together in scheduling rounds of batched launches (every job advances by
+ * up to one chunk of turns per round), and retires finished jobs between rounds (results
+ * copied to the request's host buffers, device memory freed unless kept resident).  A
+ * job's particles are bitwise the same as phtl_track would give; its monitor sums agree
+ * to FP64 rounding.  cfg NULL = defaults.  Synchronous set-up (runs the autotuner).
+ * Errors: PHTL_E_BADHANDLE, PHTL_E_INVALID (bad config or already started),
+ * PHTL_E_NODEVICE, PHTL_E_CUDA, PHTL_E_NOMEM.                                        */
+int phtl_server_start(phtl_handle* h, const phtl_server_config* cfg);
+
+/* Queue a request; *ticket identifies it.  Host buffers must stay valid until the job is
+ * final.  Errors: PHTL_E_BADHANDLE (no server / unknown resume ticket), PHTL_E_INVALID,
+ * PHTL_E_UNSTABLE (voltage), PHTL_E_NOMEM (larger than the whole budget).            */
+int phtl_submit(phtl_handle* h, const phtl_request* req, uint64_t* ticket);
+
+/* Current status of a ticket.  Errors: PHTL_E_BADHANDLE.                               */
+int phtl_poll(phtl_handle* h, uint64_t ticket, phtl_status* out);
+
+/* Wait until the ticket is final or timeout_ms passes (0 = do not wait): PHTL_OK, or
+ * PHTL_E_TIMEOUT with *out the current status.                                         */
+int phtl_wait(phtl_handle* h, uint64_t ticket, int64_t timeout_ms, phtl_status* out);
+
+/* Cancel a queued or running job; it leaves at the next round boundary with state
+ * PHTL_CANCELLED and turns_done at that boundary.  Errors: PHTL_E_BADHANDLE,
+ * PHTL_E_INVALID (already final).                                                      */
+int phtl_cancel(phtl_handle* h, uint64_t ticket);
+
+/* Free the resident device state of a PHTL_DONE job kept with keep_resident.           */
+int phtl_release(phtl_handle* h, uint64_t ticket);
+
+int phtl_server_get_stats(phtl_handle* h, phtl_server_stats* out);
+
+/* Stop the loop: the running round completes, jobs not yet DONE end CANCELLED, resident
+ * states are freed.  phtl_destroy does this too.                                       */
+int phtl_server_stop(phtl_handle* h);
+
 /* ---- host helpers -------------------------------------------------------------------- */
 
 /* Cumulative counters of a handle since phtl_create (host only). */

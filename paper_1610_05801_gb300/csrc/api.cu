@@ -30,29 +30,9 @@ void split_df(double v, float& hi, float& lo)
     lo = static_cast<float>(v - static_cast<double>(hi));
 }
 
-// Stage coefficients of each scheme (Sec. 1.1.2 readings, see phtl.h).
 void scheme_consts(const phtl_derived& d, int scheme, MapConsts& c)
 {
-    std::memset(c.dc, 0, sizeof(c.dc));
-    std::memset(c.kw, 0, sizeof(c.kw));
-    if (scheme == PHTL_EULER_CROMER) {
-        c.kw[0] = 1.0 * d.A;
-        c.dc[0] = 1.0 * d.etaC;
-    } else if (scheme == PHTL_LEAPFROG) {
-        c.dc[0] = 0.5 * d.etaC;
-        c.kw[0] = 1.0 * d.A;
-        c.dc[1] = 0.5 * d.etaC;
-    } else {
-        // Forest-Ruth: theta = 1 / (2 - 2^(1/3))
-        const double th = 1.0 / (2.0 - std::cbrt(2.0));
-        c.dc[0] = (0.5 * th) * d.etaC;
-        c.kw[0] = th * d.A;
-        c.dc[1] = (0.5 * (1.0 - th)) * d.etaC;
-        c.kw[1] = (1.0 - 2.0 * th) * d.A;
-        c.dc[2] = (0.5 * (1.0 - th)) * d.etaC;
-        c.kw[2] = th * d.A;
-        c.dc[3] = (0.5 * th) * d.etaC;
-    }
+    scheme_weights(scheme, d.A, d.etaC, c.dc, c.kw);
     for (int i = 0; i < 4; ++i) split_df(c.dc[i], c.dc_hi[i], c.dc_lo[i]);
     for (int j = 0; j < 3; ++j) split_df(c.kw[j], c.kw_hi[j], c.kw_lo[j]);
 }
@@ -70,7 +50,7 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
     d.beta = d.betagamma / d.gamma;
     d.eta = 1.0 / (p.gamma_t * p.gamma_t) - 1.0 / (d.gamma * d.gamma);
     d.k = 2.0 * kPi * static_cast<double>(p.harmonic) / p.circumference_m;
-    d.A = p.charge_e * p.voltage_V / (d.beta * p.p0_eVc);
+    d.A = kick_amplitude(p, d, p.voltage_V);
     d.etaC = d.eta * p.circumference_m;
     d.sin_phis = std::sin(p.phi_s_rad);
     d.cos_phis = std::cos(p.phi_s_rad);
@@ -116,6 +96,37 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
 
 }  // namespace
 
+// Stage coefficients of each scheme (Sec. 1.1.2 readings, see phtl.h):
+// dc[i] = w_i * eta C for the drifts, kw[j] = w_j * A for the kicks.
+void scheme_weights(int scheme, double A, double etaC, double (&dc)[4], double (&kw)[3])
+{
+    for (int i = 0; i < 4; ++i) dc[i] = 0.0;
+    for (int j = 0; j < 3; ++j) kw[j] = 0.0;
+    if (scheme == PHTL_EULER_CROMER) {
+        kw[0] = 1.0 * A;
+        dc[0] = 1.0 * etaC;
+    } else if (scheme == PHTL_LEAPFROG) {
+        dc[0] = 0.5 * etaC;
+        kw[0] = 1.0 * A;
+        dc[1] = 0.5 * etaC;
+    } else {
+        // Forest-Ruth: theta = 1 / (2 - 2^(1/3))
+        const double th = 1.0 / (2.0 - std::cbrt(2.0));
+        dc[0] = (0.5 * th) * etaC;
+        kw[0] = th * A;
+        dc[1] = (0.5 * (1.0 - th)) * etaC;
+        kw[1] = (1.0 - 2.0 * th) * A;
+        dc[2] = (0.5 * (1.0 - th)) * etaC;
+        kw[2] = th * A;
+        dc[3] = (0.5 * th) * etaC;
+    }
+}
+
+double kick_amplitude(const phtl_params& p, const phtl_derived& d, double voltage_V)
+{
+    return p.charge_e * voltage_V / (d.beta * p.p0_eVc);
+}
+
 int handle_stream(phtl_handle* h, cudaStream_t* out)
 {
     if (!h->stream) {
@@ -131,6 +142,7 @@ int handle_stream(phtl_handle* h, cudaStream_t* out)
 
 void release_handle_resources(phtl_handle* h)
 {
+    stop_server(h);
     if (h->stream) {
         cudaStreamSynchronize(h->stream);
         cudaStreamDestroy(h->stream);

@@ -41,6 +41,7 @@ struct phtl_handle {
 namespace phtl {
 
 bool handle_valid(const phtl_handle* h);
+void stop_server(phtl_handle* h);
 int ensure_device(phtl_handle* h);
 int handle_stream(phtl_handle* h, cudaStream_t* out);
 void release_handle_resources(phtl_handle* h);
@@ -50,5 +51,7 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
                   int dtype, cudaStream_t s, bool perturn, double* mon_rows, int64_t mon_cap,
                   int64_t mon_stride);
 int64_t auto_turns_per_launch(int dtype, int scheme, int64_t n);
+void scheme_weights(int scheme, double A, double etaC, double (&dc)[4], double (&kw)[3]);
+double kick_amplitude(const phtl_params& p, const phtl_derived& d, double voltage_V);
 
 }  // namespace phtl

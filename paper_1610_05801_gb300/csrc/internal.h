@@ -55,6 +55,28 @@ struct LaunchDesc {
     int32_t pad_;
 };
 
+// One bunch of a batched launch, as the batched kernels read it from the device job
+// table.  Jobs are sorted by turns (descending), so the jobs still running at any turn
+// chunk form a prefix of the table; tile_begin is the first block index of the job's
+// particle tiles (blockDim.x * P particles each).
+struct JobDesc {
+    void* c[6];          // z, dp, x, xp, y, yp (x..yp pairs may be nullptr)
+    double* mon;         // monitor rows or nullptr
+    int64_t stride;      // monitor stride (>= 1)
+    int64_t n;           // particles
+    int64_t turns;       // turns per run of the batch
+    int64_t tile_begin;  // first tile (block) of this job
+    int64_t turn_offset; // turns this job had done before the launch sequence (monitor rows
+                         // continue from there; the initial row is written when it is 0)
+    double dc[4];        // drift weights w_i * eta C of the job's scheme
+    double kw[3];        // kick weights w_j * A_job of the job's scheme
+    float dc_hi[4];      // the same rounded to FP32
+    float kw_hi[3];
+    int32_t scheme;      // integrator
+    int32_t vec;         // nonzero: 16-byte aligned buffers (128-bit loads)
+    int32_t pad_;
+};
+
 // Launchers (one per kernel family); return cudaGetLastError() of the launch.
 cudaError_t launch_track_f64(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,
                              cudaStream_t s);
@@ -62,6 +84,13 @@ cudaError_t launch_track_f32c(const LaunchDesc& L, const MapConsts& c, const Mon
                               int dtype, cudaStream_t s);
 cudaError_t launch_perturn(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,
                            int dtype, cudaStream_t s);
+
+// Batched launch over a job table: turns [t0, t0 + T) of every job with turns > t0
+// (grid = the tiles of those jobs), or row-0 records only when T == 0.
+cudaError_t launch_batched(const JobDesc* jobs, int32_t njobs, const MapConsts& c, int dtype,
+                           bool mon, int64_t t0, int32_t T, int grid, int block, cudaStream_t s);
+int occupancy_batched(int dtype, bool mon, int block);
+int particles_per_thread(int dtype);
 
 // Resident blocks per SM of a kernel variant at a block size (0 = cannot launch).
 int occupancy_f64(int scheme, bool trans, bool mon, int block);

@@ -57,6 +57,24 @@ class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("particle_turns", C.c_int64), ("calls", C.c_int64)]
 
 
+class Job(C.Structure):
+    _fields_ = [("c", C.c_void_p * 6), ("mon_rows", C.c_void_p), ("mon_capacity", C.c_int64),
+                ("mon_stride", C.c_int64), ("n", C.c_int64), ("turns", C.c_int64),
+                ("voltage_V", C.c_double), ("integrator", C.c_int32), ("dtype", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("pad_", C.c_int32), ("turns_per_launch", C.c_int64),
+                ("particle_turns_per_s", C.c_double)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("njobs", C.c_int32), ("graph", C.c_int32), ("block_threads", C.c_int32 * 3),
+                ("pad_", C.c_int32), ("turns_per_launch", C.c_int64 * 3),
+                ("probe_particle_turns_per_s", C.c_double * 3), ("launches_per_run", C.c_int64),
+                ("tiles_first_launch", C.c_int64), ("particle_turns_per_run", C.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp, _i64, _int = C.c_void_p, C.c_int64, C.c_int
@@ -76,6 +94,11 @@ SIGNATURES = {
     "phtl_moments_from_sums": (_int, [_vp, _vp]),
     "phtl_get_stats": (_int, [_vp, C.POINTER(Stats)]),
     "phtl_eval_sin": (_int, [_vp, _vp, _i64, _int, _vp]),
+    "phtl_autotune": (_int, [_vp, _int, _int, _i64, C.c_double, C.POINTER(Tuning)]),
+    "phtl_batch_create": (_int, [_vp, C.POINTER(Job), C.c_int32, C.c_int32, C.POINTER(_vp)]),
+    "phtl_batch_run": (_int, [_vp, _vp]),
+    "phtl_batch_info_get": (_int, [_vp, C.POINTER(BatchInfo)]),
+    "phtl_batch_destroy": (_int, [_vp]),
 }
 
 
@@ -187,6 +210,14 @@ class Ring:
         _check(self._lib.phtl_get_stats(self._h, C.byref(st)), "phtl_get_stats")
         return st
 
+    def autotune(self, dtype="f32c", integrator="leapfrog", active_particles=1_000_000,
+                 target_launch_ms=20.0) -> Tuning:
+        t = Tuning()
+        _check(self._lib.phtl_autotune(self._h, _dtype(dtype), _integrator(integrator),
+                                       int(active_particles), float(target_launch_ms),
+                                       C.byref(t)), "phtl_autotune")
+        return t
+
     def set_tuning(self, block_threads: int = 0, turns_per_launch: int = 0, max_blocks: int = 0):
         _check(self._lib.phtl_set_tuning(self._h, int(block_threads), int(turns_per_launch),
                                          int(max_blocks)), "phtl_set_tuning")
@@ -291,3 +322,71 @@ def eval_sin(x, which: int = 0, stream=None):
     _check(load().phtl_eval_sin(x.data_ptr(), y.data_ptr(), x.numel(), int(which),
                                 _stream_ptr(stream)), "phtl_eval_sin")
     return y
+
+
+def make_job(z, dp, x=None, xp=None, y=None, yp=None, turns=1, voltage_V=None,
+             integrator="leapfrog", dtype="f32c", monitor=None, stride=1) -> dict:
+    """A batch job description (buffers are CUDA tensors; monitor a (rows, 16) float64
+    tensor or None)."""
+    return dict(c=[z, dp, x, xp, y, yp], turns=int(turns), voltage_V=voltage_V,
+                integrator=integrator, dtype=dtype, monitor=monitor, stride=int(stride))
+
+
+class Batch:
+    """Many independent bunches tracked by shared, graph-captured launches
+    (phtl_batch_create / phtl_batch_run)."""
+
+    def __init__(self, ring: Ring, jobs, use_graph: bool = True):
+        self._lib = load()
+        self._ring = ring
+        self._keep = []
+        arr = (Job * max(1, len(jobs)))()
+        for i, j in enumerate(jobs):
+            dt = _dtype(j["dtype"])
+            want = "float64" if dt == F64 else "float32"
+            for b in j["c"]:
+                if b is not None:
+                    _check_tensor(b, want, "job buffer")
+                    self._keep.append(b)
+            z = j["c"][0]
+            n = z.numel() if dt == F64 else z.numel() // 2
+            for k in range(6):
+                arr[i].c[k] = _ptr(j["c"][k])
+            mon = j.get("monitor")
+            if mon is not None:
+                _check_tensor(mon, "float64", "monitor")
+                self._keep.append(mon)
+                arr[i].mon_rows = mon.data_ptr()
+                arr[i].mon_capacity = mon.shape[0]
+                arr[i].mon_stride = int(j.get("stride", 1))
+            arr[i].n = n
+            arr[i].turns = int(j["turns"])
+            v = j.get("voltage_V")
+            arr[i].voltage_V = float(ring.params.voltage_V if v is None else v)
+            arr[i].integrator = _integrator(j["integrator"])
+            arr[i].dtype = dt
+        self._jobs = arr
+        h = _vp()
+        _check(self._lib.phtl_batch_create(ring.handle, arr, len(jobs), 1 if use_graph else 0,
+                                           C.byref(h)), "phtl_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(self._lib.phtl_batch_run(self._h, _stream_ptr(stream)), "phtl_batch_run")
+
+    def info(self) -> BatchInfo:
+        b = BatchInfo()
+        _check(self._lib.phtl_batch_info_get(self._h, C.byref(b)), "phtl_batch_info_get")
+        return b
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.phtl_batch_destroy(self._h)
+            self._h = _vp()
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -166,3 +166,39 @@ def test_f32c_split_roundtrip():
     b = phtl.split_f32c(a)
     assert b.dtype == np.float32 and b.shape == (2002,)
     assert np.max(np.abs(phtl.join_f32c(b) - a) / np.abs(a)) < 1e-14
+
+
+def test_batch_validation_needs_no_gpu():
+    """Job errors are reported before any device work."""
+    R = phtl.Ring(**synth.ring(2e6))
+    lib = phtl.load()
+    z = np.zeros(8)
+    p = z.ctypes.data
+
+    def create(**over):
+        J = (phtl.Job * 1)()
+        J[0].c[0] = p
+        J[0].c[1] = p
+        J[0].n = 8
+        J[0].turns = 10
+        J[0].voltage_V = 2e6
+        J[0].integrator = 1
+        J[0].dtype = 0
+        for k, v in over.items():
+            setattr(J[0], k, v)
+        h = C.c_void_p()
+        return lib.phtl_batch_create(R.handle, J, 1, 1, C.byref(h))
+
+    assert create(integrator=5) == phtl.E_INVALID
+    assert create(dtype=9) == phtl.E_INVALID
+    assert create(n=-1) == phtl.E_INVALID
+    assert create(voltage_V=float("inf")) == phtl.E_INVALID
+    assert create(voltage_V=1e10) == phtl.E_UNSTABLE      # K >= 4
+    assert create(voltage_V=-2e6) == phtl.E_UNSTABLE      # wrong-sign bucket
+    assert create(mon_rows=p, mon_capacity=2, mon_stride=1) == phtl.E_INVALID  # too few rows
+    h = C.c_void_p()
+    assert lib.phtl_batch_create(None, None, 0, 1, C.byref(h)) == phtl.E_BADHANDLE
+    assert lib.phtl_batch_create(R.handle, None, 1, 1, C.byref(h)) == phtl.E_INVALID
+    assert lib.phtl_batch_run(None, None) == phtl.E_BADHANDLE
+    assert lib.phtl_batch_destroy(None) == phtl.E_BADHANDLE
+    R.close()

@@ -83,10 +83,11 @@ def run_ref(inp, scheme, turns, transverse=True, stride=None):
     return list(r[:6]), r[6]
 
 
-def moment_errors(d, mg, mr):
+def moment_errors(d, mg, mr, with_emittance=True):
     """Relative moment errors: means relative to the corresponding rms, rms relative to
-    itself, emittance relative to rms_u * rms_u' (its natural scale; the emittance of a
-    two-particle bunch is exactly zero)."""
+    itself, emittance relative to rms_u * rms_u' (its natural scale).  The emittance of a
+    one- or two-particle bunch is zero, where the raw-sum formula
+    sqrt(<u^2><u'^2> - <uu'>^2) only resolves ~sqrt(rounding): skip it there."""
     e = []
     for off in (0, 5, 10):
         if mr[0, off + 2] == 0:
@@ -95,7 +96,8 @@ def moment_errors(d, mg, mr):
             e.append(np.abs(mg[:, off + j] - mr[:, off + j]) / mr[:, off + ref_scale])
         for j in (2, 3):
             e.append(np.abs(mg[:, off + j] - mr[:, off + j]) / mr[:, off + j])
-        e.append(np.abs(mg[:, off + 4] - mr[:, off + 4]) / (mr[:, off + 2] * mr[:, off + 3]))
+        if with_emittance:
+            e.append(np.abs(mg[:, off + 4] - mr[:, off + 4]) / (mr[:, off + 2] * mr[:, off + 3]))
     return float(np.max(np.vstack(e)))
 
 
@@ -116,7 +118,7 @@ def test_f64_small_sizes(scheme, transverse, n):
     assert np.allclose(mg[:, 0], mr[:, 0], rtol=0, atol=1e-10 * zb)
     assert np.allclose(mg[:, 1], mr[:, 1], rtol=0, atol=1e-10 * db)
     if n > 1:
-        assert moment_errors(inp["d"], mg, mr) < 1e-9
+        assert moment_errors(inp["d"], mg, mr, with_emittance=n > 2) < 1e-9
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
