@@ -44,6 +44,22 @@ WORKLOADS = {
     # small case for quick checks (not a bench line)
     "tiny": dict(n=20_000, turns=200, schemes=("euler_cromer", "leapfrog", "ruth4"),
                  dtype="f64", voltage=4.5e6, transverse=True, stride=1),
+    # 64 uneven bunches (log-uniform 1e3-4e6 particles, ~6e7 in total; V ~ U(1, 6) MV;
+    # turns ~ U(1e3, 1e5)), leap-frog FP32-compensated, per-bunch turn-by-turn monitors,
+    # one graph-captured batch per step
+    "batched_64_bunches_f32c_lf": dict(kind="batched", nbunch=64, total=6e7, dtype="f32c",
+                                       scheme="leapfrog", stride=1),
+    # the same batch in FP64 (per-job FP64 reference point; turns scaled down by 100)
+    "batched_64_bunches_f64_lf": dict(kind="batched", nbunch=64, total=6e7, dtype="f64",
+                                      scheme="leapfrog", stride=1, turn_scale=0.01),
+    # serving: Poisson arrivals at 200 jobs/s (first `count` of the trace), sizes
+    # log-uniform 1e4-8e6, turns log-uniform 1e2-1e5, integrator uniform over three,
+    # FP64 or FP32C 50/50, 150 GB admission budget; then the same jobs at ~70 % load
+    "serving_poisson_200hz": dict(kind="serving", count=48, rate_hz=200.0, budget=150e9),
+    # precision sweep: 4e6 particles x 1e6 turns leap-frog FP32C (60 % core, 40 % halo to
+    # 98 % of the separatrix) against FP64 on a 1e4-particle subsample
+    "precision_sweep_4e6x1e6_lf": dict(kind="precision", n=4_000_000, turns=1_000_000,
+                                       subsample=10_000, voltage=2e6, stride=10_000),
 }
 DEFAULT_WORKLOAD = "single_bunch_1e6x1e4_ec_lf_ruth4_f64"
 
@@ -363,6 +379,253 @@ def run_ours(args, wl_name, wl):
     return 0
 
 
+def _clocked(fn):
+    """Run fn() with the clock sampler on; returns (fn's value, clocks)."""
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    try:
+        v = fn()
+    finally:
+        clk = clocks.stop()
+    return v, clk
+
+
+def run_batched(args, wl_name, wl):
+    """Config 3: one graph-captured batch of uneven bunches per step."""
+    import numpy as np
+    import torch
+
+    from paper_1610_05801_gb300 import build as _build
+    from paper_1610_05801_gb300 import phtl, synth
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = synth.batched_jobs(seed=3, nbunch=wl["nbunch"], total=wl["total"])
+    scale = wl.get("turn_scale", 1.0)
+    ring = synth.ring(2e6)
+    R = phtl.Ring(**ring)
+    dt = wl["dtype"]
+    jobs, keep = [], []
+    for sp in specs:
+        der = phtl.Ring(**dict(ring, voltage_V=sp["voltage_V"])).derived()
+        b = synth.Bucket(k=der.k, A=der.A, etaC=der.etaC, Qs=der.Qs, betagamma=der.betagamma)
+        z, d, _ = synth.matched_bunch(sp["seed"], sp["n"], b)
+        turns = max(1, int(sp["turns"] * scale))
+        if dt == "f64":
+            bz = torch.tensor(z, dtype=torch.float64, device=dev)
+            bd = torch.tensor(d, dtype=torch.float64, device=dev)
+        else:
+            bz = torch.tensor(phtl.split_f32c(z), dtype=torch.float32, device=dev)
+            bd = torch.tensor(phtl.split_f32c(d), dtype=torch.float32, device=dev)
+        mon = torch.zeros((turns // wl["stride"] + 1, 16), dtype=torch.float64, device=dev)
+        jobs.append(phtl.make_job(bz, bd, turns=turns, voltage_V=sp["voltage_V"],
+                                  integrator=wl["scheme"], dtype=dt, monitor=mon,
+                                  stride=wl["stride"]))
+        keep += [bz, bd, mon]
+    t_create = time.perf_counter()
+    B = phtl.Batch(R, jobs, use_graph=True)
+    t_create = time.perf_counter() - t_create
+    info = B.info()
+    pt = info.particle_turns_per_run
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        B.run(stream)
+    torch.cuda.synchronize()
+
+    def timed():
+        evs = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.run(stream)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    st0 = R.stats()
+    ms, clk = _clocked(timed)
+    launches = R.stats().launches - st0.launches
+    t = sum(ms) / 1e3
+    slot = phtl.DTYPES[dt]
+    line = {
+        "metric": METRIC, "value": pt * args.steps / t, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
+        "data": "synthetic (seeded uneven bunches)",
+        "config": {"workload": wl_name, "bunches": len(specs),
+                   "particles_total": int(sum(s["n"] for s in specs)),
+                   "particle_turns_per_step": pt, "integrator": wl["scheme"],
+                   "monitor_stride": wl["stride"], "turn_scale": scale,
+                   "block_threads": info.block_threads[slot],
+                   "turns_per_launch": info.turns_per_launch[slot],
+                   "launches_per_step": info.launches_per_run, "graph": bool(info.graph),
+                   "autotune_probe_pts": info.probe_particle_turns_per_s[slot],
+                   "create_s": t_create,
+                   "l2": "state ~1 GB (> L2) resident in HBM"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    B.close()
+    R.close()
+    return 0
+
+
+def run_serving(args, wl_name, wl):
+    """Config 4: continuous batching of a Poisson trace; p50/p99 latency."""
+    import numpy as np
+
+    from paper_1610_05801_gb300 import build as _build
+    from paper_1610_05801_gb300 import phtl, synth
+
+    _build.build()
+    trace = synth.serving_trace(seed=4, count=wl["count"], rate_hz=wl["rate_hz"])
+    ring = synth.ring(2e6)
+    R = phtl.Ring(**ring)
+    der = R.derived()
+    b = synth.Bucket(k=der.k, A=der.A, etaC=der.etaC, Qs=der.Qs, betagamma=der.betagamma)
+    hosts = []
+    for j in trace:
+        z, d, _ = synth.matched_bunch(j["seed"], j["n"], b)
+        if j["dtype"] == 0:
+            hosts.append((np.ascontiguousarray(z), np.ascontiguousarray(d)))
+        else:
+            hosts.append((phtl.split_f32c(z), phtl.split_f32c(d)))
+
+    def play(S, times):
+        t0 = time.perf_counter()
+        tickets = []
+        for j, (z, d), ta in zip(trace, hosts, times):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(S.submit(z, d, turns=j["turns"], integrator=j["integrator"],
+                                    dtype=j["dtype"], out=[z, d, None, None, None, None]))
+        for t in tickets:
+            rc, st = S.wait(t, 3_600_000)
+            assert rc == phtl.OK and st.state == phtl.DONE, (rc, st.state, st.error)
+        return time.perf_counter() - t0
+
+    S = phtl.Server(R, memory_budget_bytes=int(wl["budget"]), max_active=64)
+    (mk1, clk) = _clocked(lambda: play(S, [j["t_arrive_s"] for j in trace]))
+    s1 = S.stats()
+    S.stop()
+    cap = s1.throughput_pts
+    work = sum(j["n"] * j["turns"] for j in trace)
+    # the same jobs at ~70 % of the measured capacity: mean gap = mean work / (0.7 cap)
+    gaps = np.array([j["t_arrive_s"] for j in trace])
+    gaps = np.diff(np.concatenate([[0.0], gaps]))
+    scale = (work / len(trace)) / (0.7 * cap) / max(gaps.mean(), 1e-12)
+    S2 = phtl.Server(R, memory_budget_bytes=int(wl["budget"]), max_active=64)
+    mk2 = play(S2, list(np.cumsum(gaps * scale)))
+    s2 = S2.stats()
+    S2.stop()
+    line = {
+        "metric": METRIC, "value": s1.throughput_pts, "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": mk1 * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed f64/f32c", "data": "synthetic Poisson trace",
+        "config": {"workload": wl_name, "jobs": len(trace), "offered_rate_hz": wl["rate_hz"],
+                   "particle_turns": work, "budget_bytes": wl["budget"], "max_active": 64,
+                   "f64_jobs": sum(1 for j in trace if j["dtype"] == 0)},
+        "latency": {"p50_s": s1.p50_latency_s, "p99_s": s1.p99_latency_s,
+                    "mean_s": s1.mean_latency_s, "makespan_s": mk1, "rounds": s1.rounds,
+                    "bytes_peak": s1.bytes_peak},
+        "at_70pct_load": {"rate_hz": len(trace) / float(np.sum(gaps * scale)),
+                          "throughput_pts": s2.throughput_pts, "p50_s": s2.p50_latency_s,
+                          "p99_s": s2.p99_latency_s, "makespan_s": mk2},
+        "gpu_launches": s1.launches, "clocks": clk,
+        "e2e": {"value": s1.throughput_pts, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(z.nbytes + d.nbytes for z, d in hosts)),
+                "d2h_bytes_per_step": int(sum(z.nbytes + d.nbytes for z, d in hosts)),
+                "api": "phtl_submit / phtl_wait on host buffers"},
+    }
+    print(json.dumps(line), flush=True)
+    R.close()
+    return 0
+
+
+def run_precision(args, wl_name, wl):
+    """Config 2: FP32C vs FP64 moments after 1e6 turns (halo bunch), on the GPU; the FP64
+    oracle re-tracks the 1e4-particle subsample (with --oracle)."""
+    import numpy as np
+    import torch
+
+    from paper_1610_05801_gb300 import build as _build
+    from paper_1610_05801_gb300 import phtl, synth
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    ring = synth.ring(wl["voltage"])
+    R = phtl.Ring(**ring)
+    der = R.derived()
+    b = synth.Bucket(k=der.k, A=der.A, etaC=der.etaC, Qs=der.Qs, betagamma=der.betagamma)
+    z, d = synth.halo_bunch(2, wl["n"], b)
+    turns, sub, stride = wl["turns"], wl["subsample"], wl["stride"]
+    rows = turns // stride + 1
+    res = {}
+    for dt in ("f32c", "f32cd"):
+        bz = torch.tensor(phtl.split_f32c(z), dtype=torch.float32, device=dev)
+        bd = torch.tensor(phtl.split_f32c(d), dtype=torch.float32, device=dev)
+        mon = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
+        R.set_monitor(mon, stride=stride)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.track(bz, bd, turns=turns, integrator="leapfrog", dtype=dt)
+        e.record()
+        torch.cuda.synchronize()
+        R.set_monitor(None)
+        zf = phtl.join_f32c(bz.cpu().numpy())
+        df = phtl.join_f32c(bd.cpu().numpy())
+        res[dt] = dict(ms=a.elapsed_time(e), z=zf[:sub], d=df[:sub],
+                       mom_full=phtl.moments_from_sums(mon.cpu().numpy()))
+    # FP64 on the subsample (GPU), with per-row monitors of the subsample
+    bz = torch.tensor(z[:sub], dtype=torch.float64, device=dev)
+    bd = torch.tensor(d[:sub], dtype=torch.float64, device=dev)
+    mon = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
+    R.set_monitor(mon, stride=stride)
+    R.track(bz, bd, turns=turns, integrator="leapfrog", dtype="f64")
+    torch.cuda.synchronize()
+    R.set_monitor(None)
+    m64 = phtl.moments_from_sums(mon.cpu().numpy())
+    out = {"metric": "moment relative error FP32C vs FP64 after 1e6 turns", "workload": wl_name,
+           "n": wl["n"], "turns": turns, "subsample": sub}
+    for dt in ("f32c", "f32cd"):
+        # the FP32 path's subsample, tracked separately so its moments can be compared row by row
+        sz = torch.tensor(phtl.split_f32c(z[:sub]), dtype=torch.float32, device=dev)
+        sd = torch.tensor(phtl.split_f32c(d[:sub]), dtype=torch.float32, device=dev)
+        ms = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
+        R.set_monitor(ms, stride=stride)
+        R.track(sz, sd, turns=turns, integrator="leapfrog", dtype=dt)
+        torch.cuda.synchronize()
+        R.set_monitor(None)
+        m32 = phtl.moments_from_sums(ms.cpu().numpy())
+        assert np.array_equal(phtl.join_f32c(sz.cpu().numpy()), res[dt]["z"])  # same bits
+        rel = {}
+        for name, j, sc in (("mean_z", 0, 2), ("mean_dp", 1, 3), ("rms_z", 2, 2),
+                            ("rms_dp", 3, 3), ("eps_z", 4, 4)):
+            rel[name] = float(np.max(np.abs(m32[:, j] - m64[:, j]) / np.abs(m64[:, sc])))
+        H = lambda zz, dd: 0.5 * der.etaC * dd * dd + (der.A / der.k) * (1 - np.cos(der.k * zz))
+        h0, h1 = H(z[:sub], d[:sub]), H(res[dt]["z"], res[dt]["d"])
+        out[dt] = {"pts_full": wl["n"] * turns / (res[dt]["ms"] / 1e3), "kernel_ms": res[dt]["ms"],
+                   "max_rel_moment_err": rel,
+                   "hamiltonian_drift_rel_median": float(np.median(np.abs(h1 - h0) / h0)),
+                   "hamiltonian_drift_rel_max": float(np.max(np.abs(h1 - h0) / h0))}
+    if args.oracle:
+        import oracle
+
+        O = oracle.load()
+        t0 = time.perf_counter()
+        ref = O.track(O.derive(ring), "leapfrog", z[:sub], d[:sub], turns=turns, moments=True,
+                      stride=stride)
+        out["oracle_s"] = time.perf_counter() - t0
+        mo = ref[6]
+        out["f64_gpu_vs_oracle_max_rel_rms"] = float(np.max(np.abs(m64[:, 2:4] - mo[:, 2:4]) / mo[:, 2:4]))
+    print(json.dumps(out), flush=True)
+    R.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,10 +636,23 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=20_000,
                     help="particles in the oracle's bounded CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle", action="store_true",
+                    help="precision sweep: also re-track the subsample with the FP64 oracle")
     args = ap.parse_args(argv)
     wl = WORKLOADS[args.workload]
+    kind = wl.get("kind", "single")
     if args.impl == "reference":
+        if kind != "single":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle reference arm covers the single-bunch workload only"}))
+            return 0
         return run_reference(args, args.workload, wl)
+    if kind == "batched":
+        return run_batched(args, args.workload, wl)
+    if kind == "serving":
+        return run_serving(args, args.workload, wl)
+    if kind == "precision":
+        return run_precision(args, args.workload, wl)
     return run_ours(args, args.workload, wl)
 
 

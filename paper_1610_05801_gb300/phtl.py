@@ -75,6 +75,34 @@ class BatchInfo(C.Structure):
                 ("tiles_first_launch", C.c_int64), ("particle_turns_per_run", C.c_int64)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_int64), ("max_active", C.c_int32),
+                ("block_threads", C.c_int32), ("chunk_turns_f64", C.c_int64),
+                ("chunk_turns_f32", C.c_int64), ("target_round_ms", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("in_", C.c_void_p * 6), ("out", C.c_void_p * 6), ("mon_rows", C.c_void_p),
+                ("mon_stride", C.c_int64), ("n", C.c_int64), ("turns", C.c_int64),
+                ("voltage_V", C.c_double), ("integrator", C.c_int32), ("dtype", C.c_int32),
+                ("resume_ticket", C.c_uint64), ("keep_resident", C.c_int32), ("pad_", C.c_int32)]
+
+
+class Status(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("turns_done", C.c_int64),
+                ("t_submit_ns", C.c_int64), ("t_admit_ns", C.c_int64), ("t_done_ns", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "cancelled", "queued",
+                                         "active", "bytes_in_use", "bytes_peak", "rounds",
+                                         "launches")] + \
+               [(n, C.c_double) for n in ("particle_turns", "busy_s", "p50_latency_s",
+                                          "p99_latency_s", "mean_latency_s", "throughput_pts")]
+
+
+QUEUED, RUNNING, DONE, FAILED, CANCELLED = 0, 1, 2, 3, 4
+
 _lib = None
 _lock = threading.Lock()
 _vp, _i64, _int = C.c_void_p, C.c_int64, C.c_int
@@ -99,6 +127,14 @@ SIGNATURES = {
     "phtl_batch_run": (_int, [_vp, _vp]),
     "phtl_batch_info_get": (_int, [_vp, C.POINTER(BatchInfo)]),
     "phtl_batch_destroy": (_int, [_vp]),
+    "phtl_server_start": (_int, [_vp, C.POINTER(ServerConfig)]),
+    "phtl_submit": (_int, [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "phtl_poll": (_int, [_vp, C.c_uint64, C.POINTER(Status)]),
+    "phtl_wait": (_int, [_vp, C.c_uint64, _i64, C.POINTER(Status)]),
+    "phtl_cancel": (_int, [_vp, C.c_uint64]),
+    "phtl_release": (_int, [_vp, C.c_uint64]),
+    "phtl_server_get_stats": (_int, [_vp, C.POINTER(ServerStats)]),
+    "phtl_server_stop": (_int, [_vp]),
 }
 
 
@@ -390,3 +426,81 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """The continuous-batching serving loop of a Ring (phtl_server_start ...).
+
+    Requests carry host arrays (numpy, C-contiguous; float64 for "f64", float32 with the
+    [hi | comp] layout for the FP32C types); results are written to `out` arrays (by
+    default the inputs, in place) before the job turns DONE."""
+
+    def __init__(self, ring: Ring, memory_budget_bytes=0, max_active=0, block_threads=0,
+                 chunk_turns_f64=0, chunk_turns_f32=0, target_round_ms=0.0):
+        self._lib = load()
+        self._ring = ring
+        cfg = ServerConfig(int(memory_budget_bytes), int(max_active), int(block_threads),
+                           int(chunk_turns_f64), int(chunk_turns_f32), float(target_round_ms))
+        _check(self._lib.phtl_server_start(ring.handle, C.byref(cfg)), "phtl_server_start")
+        self._keep = {}
+        self._running = True
+
+    def submit(self, z=None, dp=None, x=None, xp=None, y=None, yp=None, turns=1, voltage_V=None,
+               integrator="leapfrog", dtype="f64", out=None, monitor=None, stride=1, n=None,
+               resume=0, keep_resident=False) -> int:
+        dt = _dtype(dtype)
+        ins = [z, dp, x, xp, y, yp]
+        outs = list(out) if out is not None else ins
+        r = Request()
+        for k in range(6):
+            r.in_[k] = _ptr(ins[k]) if not resume else None
+            r.out[k] = _ptr(outs[k])
+        if n is None:
+            ref = outs[0] if outs[0] is not None else ins[0]
+            n = _numel(ref) if dt == F64 else _numel(ref) // 2
+        r.n = int(n)
+        r.turns = int(turns)
+        r.voltage_V = float(self._ring.params.voltage_V if voltage_V is None else voltage_V)
+        r.integrator = _integrator(integrator)
+        r.dtype = dt
+        if monitor is not None:
+            r.mon_rows = _ptr(monitor)
+            r.mon_stride = int(stride)
+        r.resume_ticket = int(resume)
+        r.keep_resident = 1 if keep_resident else 0
+        t = C.c_uint64()
+        _check(self._lib.phtl_submit(self._ring.handle, C.byref(r), C.byref(t)), "phtl_submit")
+        self._keep[t.value] = (ins, outs, monitor)
+        return t.value
+
+    def poll(self, ticket) -> Status:
+        st = Status()
+        _check(self._lib.phtl_poll(self._ring.handle, int(ticket), C.byref(st)), "phtl_poll")
+        return st
+
+    def wait(self, ticket, timeout_ms=60000):
+        """Returns (rc, Status): rc == OK when final, E_TIMEOUT otherwise."""
+        st = Status()
+        rc = self._lib.phtl_wait(self._ring.handle, int(ticket), int(timeout_ms), C.byref(st))
+        if rc not in (OK, E_TIMEOUT):
+            raise PhtlError(rc, "phtl_wait")
+        if rc == OK and st.state != RUNNING:
+            self._keep.pop(int(ticket), None)
+        return rc, st
+
+    def cancel(self, ticket):
+        return self._lib.phtl_cancel(self._ring.handle, int(ticket))
+
+    def release(self, ticket):
+        _check(self._lib.phtl_release(self._ring.handle, int(ticket)), "phtl_release")
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        _check(self._lib.phtl_server_get_stats(self._ring.handle, C.byref(s)), "phtl_server_get_stats")
+        return s
+
+    def stop(self):
+        if self._running:
+            self._lib.phtl_server_stop(self._ring.handle)
+            self._running = False
+            self._keep = {}
