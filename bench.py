@@ -254,7 +254,10 @@ def run_ours(args, wl_name, wl):
     der = R.derived()
     host = make_inputs(wl, der, seed=1 + rank)
     n, turns, dt = wl["n"], wl["turns"], wl["dtype"]
-    bufs = [torch.tensor(a, dtype=torch.float64, device=dev) for a in host]
+    if dt == "f64":
+        bufs = [torch.tensor(a, dtype=torch.float64, device=dev) for a in host]
+    else:
+        bufs = [torch.tensor(phtl.split_f32c(a), dtype=torch.float32, device=dev) for a in host]
     while len(bufs) < 6:
         bufs.append(None)
     nrows = turns // max(1, wl["stride"]) + 1
@@ -265,6 +268,7 @@ def run_ours(args, wl_name, wl):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
     ev = {s: [] for s in wl["schemes"]}
+    track = R.track_perturn if wl.get("perturn") else R.track
 
     def step(record=False):
         for s in wl["schemes"]:
@@ -272,7 +276,7 @@ def run_ours(args, wl_name, wl):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            R.track(*bufs, turns=turns, integrator=s, dtype=dt, stream=stream)
+            track(*bufs, turns=turns, integrator=s, dtype=dt, stream=stream)
             if record:
                 e1.record(stream)
                 ev[s].append((e0, e1))
@@ -319,10 +323,85 @@ def run_ours(args, wl_name, wl):
     flops = alg_flops(dom, wl["transverse"], wl["stride"] > 0) * n * tpl
     achieved = flops / dur_s / 1e12
 
-    # end-to-end through the C ABI on pinned host buffers (copies inside the timed region)
-    hbufs = [torch.tensor(a, dtype=torch.float64).pin_memory() for a in host]
+    if args.no_e2e or wl.get("perturn"):
+        e2e_value, h2d, d2h, e2e_steps = None, 0, 0, 0
+    else:
+        e2e_value, h2d, d2h, e2e_steps = e2e_host(R, host, wl, args, dist, dev, ws)
+    roof = per_turn_roofline(wl, per_scheme_ms, n, turns, dt) if wl.get("perturn") else None
+    kname = (f"k_track_{'f64' if dt == 'f64' else 'f32c'}<{dom}"
+             f"{', transverse' if wl['transverse'] else ''}{', monitor' if wl['stride'] else ''}>")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
+        "data": "synthetic (seeded matched bunch + transverse Gaussians; no dataset)",
+        "config": {"workload": wl_name, "n_particles": n, "turns": turns,
+                   "integrators": list(wl["schemes"]), "transverse": wl["transverse"],
+                   "monitor_stride": wl["stride"], "ring": "C=6911.5 m h=4620 p0=26 GeV/c "
+                   "gamma_t=22.77 V=4.5 MV phi_s=0",
+                   "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
+                   "parallelism": f"replica per GPU x{ws}",
+                   "launch": "per-turn" if wl.get("perturn") else "persistent"},
+        "roofline": roof or {
+            "bound": "alu", "kernel": kname,
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
+                           "counts and max clock); DFMA rate confirmed by a microbenchmark",
+            "alg_flops_per_particle_turn": alg_flops(dom, wl["transverse"], wl["stride"] > 0),
+            "launch_ms": dur_s * 1e3, "turns_per_launch": tpl},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "api": "phtl_track_host (pinned host buffers; alloc, H2D, kernels, D2H, free)"},
+        "clocks": clk,
+        "per_scheme_ms": per_scheme_ms,
+        "wall_s_timed_region": wall,
+    }
+    return finish_line(line, args, wl, rank, R, dist)
+
+
+def per_turn_roofline(wl, per_scheme_ms, n, turns, dt):
+    """HBM roofline of the per-turn variant: the state is read and written every turn."""
+    import json as _j  # noqa: F401
+
+    peaks = measured_peaks()
+    coords = 6 if wl["transverse"] else 2
+    bytes_pt = coords * 2 * 8  # FP64: 8 B per coordinate; FP32C: hi + comp = 8 B; read + write
+    dom = max(per_scheme_ms, key=per_scheme_ms.get)
+    achieved = bytes_pt * n * turns / (per_scheme_ms[dom] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": f"per-turn launches, {dom}, {dt}", "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": None, "peak_source": peaks["source"],
+            "alg_bytes_per_particle_turn": bytes_pt}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json copy)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def e2e_host(R, host, wl, args, dist, dev, ws):
+    """The same metric through phtl_track_host on pinned host buffers (H2D, kernels, D2H
+    inside the timed region)."""
+    import torch
+
+    from paper_1610_05801_gb300 import phtl
+
+    n, turns, dt = wl["n"], wl["turns"], wl["dtype"]
+    if dt == "f64":
+        hbufs = [torch.tensor(a, dtype=torch.float64).pin_memory() for a in host]
+    else:
+        hbufs = [torch.tensor(phtl.split_f32c(a), dtype=torch.float32).pin_memory() for a in host]
     while len(hbufs) < 6:
         hbufs.append(None)
+    nrows = turns // max(1, wl["stride"]) + 1
     hmon = torch.zeros((nrows, phtl.MON_FIELDS), dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     R.track_host(*hbufs, turns=turns, integrator=wl["schemes"][0], dtype=dt,
@@ -335,37 +414,13 @@ def run_ours(args, wl_name, wl):
             R.track_host(*hbufs, turns=turns, integrator=s, dtype=dt,
                          mon_rows=hmon if wl["stride"] else None, mon_stride=max(1, wl["stride"]))
     e2e_t = max_over_ranks(time.perf_counter() - t0, dist, dev)
-    nb = sum(h.numel() * 8 for h in hbufs if h is not None)
+    nb = sum(h.numel() * h.element_size() for h in hbufs if h is not None)
     h2d = nb * len(wl["schemes"])
     d2h = (nb + (hmon.numel() * 8 if wl["stride"] else 0)) * len(wl["schemes"])
-    e2e_value = n * turns * len(wl["schemes"]) * e2e_steps * ws / e2e_t
+    return n * turns * len(wl["schemes"]) * e2e_steps * ws / e2e_t, h2d, d2h, e2e_steps
 
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
-        "data": "synthetic (seeded matched bunch + transverse Gaussians; no dataset)",
-        "config": {"workload": wl_name, "n_particles": n, "turns": turns,
-                   "integrators": list(wl["schemes"]), "transverse": wl["transverse"],
-                   "monitor_stride": wl["stride"], "ring": "C=6911.5 m h=4620 p0=26 GeV/c "
-                   "gamma_t=22.77 V=4.5 MV phi_s=0",
-                   "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
-                   "parallelism": f"replica per GPU x{ws}"},
-        "roofline": {"bound": "alu", "kernel": f"k_track_f64<{dom}, transverse, monitor>",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
-                                    "counts and max clock); DFMA rate confirmed by a microbenchmark",
-                     "alg_flops_per_particle_turn": alg_flops(dom, wl["transverse"], wl["stride"] > 0),
-                     "launch_ms": dur_s * 1e3, "turns_per_launch": tpl},
-        "gpu_launches": launches,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "api": "phtl_track_host (pinned host buffers; alloc, H2D, kernels, D2H, free)"},
-        "clocks": clk,
-        "per_scheme_ms": per_scheme_ms,
-        "wall_s_timed_region": wall,
-    }
+
+def finish_line(line, args, wl, rank, R, dist):
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, sample, _ = cpu_baseline(wl, n_sample=args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -638,9 +693,28 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle", action="store_true",
                     help="precision sweep: also re-track the subsample with the FP64 oracle")
+    # overrides of the single-bunch workload (profiling captures and sweeps; the headline
+    # line uses the workload as defined)
+    ap.add_argument("--n", type=int)
+    ap.add_argument("--turns", type=int)
+    ap.add_argument("--schemes", help="comma-separated integrators")
+    ap.add_argument("--dtype", choices=("f64", "f32c", "f32cd"))
+    ap.add_argument("--stride", type=int, help="monitor stride (0 = no monitor)")
+    ap.add_argument("--no-transverse", action="store_true")
+    ap.add_argument("--perturn", action="store_true", help="one launch per turn (HBM-bound variant)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
     kind = wl.get("kind", "single")
+    if kind == "single":
+        for key in ("n", "turns", "dtype", "stride"):
+            if getattr(args, key) is not None:
+                wl[key] = getattr(args, key)
+        if args.schemes:
+            wl["schemes"] = tuple(args.schemes.split(","))
+        if args.no_transverse:
+            wl["transverse"] = False
+        wl["perturn"] = args.perturn
     if args.impl == "reference":
         if kind != "single":
             print(json.dumps({"impl": "reference", "unavailable":
