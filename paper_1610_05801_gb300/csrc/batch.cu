@@ -45,6 +45,8 @@ double probe_rate(phtl_handle* h, int dtype, int scheme, int block, int64_t m, i
                   cudaStream_t s)
 {
     const size_t es = dtype == PHTL_F64 ? sizeof(double) : 2 * sizeof(float);
+    // a multiple of 16 particles keeps z, dp and the FP32C comp halves 16-byte aligned
+    m = (m + 15) / 16 * 16;
     void* zd = nullptr;
     JobDesc* dj = nullptr;
     double rate = 0.0;
@@ -61,7 +63,10 @@ double probe_rate(phtl_handle* h, int dtype, int scheme, int block, int64_t m, i
         J.turns = turns;
         J.stride = 1;
         J.scheme = scheme;
-        J.vec = 1;
+        const bool aligned = reinterpret_cast<uintptr_t>(J.c[0]) % 16 == 0 &&
+                             reinterpret_cast<uintptr_t>(J.c[1]) % 16 == 0 &&
+                             (dtype == PHTL_F64 || (m * 4) % 16 == 0);
+        J.vec = aligned ? 1 : 0;
         scheme_weights(scheme, h->derived.A, h->derived.etaC, J.dc, J.kw);
         for (int i = 0; i < 4; ++i) J.dc_hi[i] = static_cast<float>(J.dc[i]);
         for (int j = 0; j < 3; ++j) J.kw_hi[j] = static_cast<float>(J.kw[j]);

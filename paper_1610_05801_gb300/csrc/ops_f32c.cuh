@@ -222,10 +222,17 @@ __device__ __forceinline__ void record(const DF (&z)[P], const DF (&d)[P], const
     }
 }
 
+// 128-bit accesses only where the host allowed them (vec) AND both the hi and the comp
+// addresses really are 16-byte aligned; anything else takes the scalar path.
+__device__ __forceinline__ bool aligned16_pair(const float* a, const float* b)
+{
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
 __device__ __forceinline__ void load4(const float* __restrict__ g, int64_t base, int64_t n,
                                       bool vec, DF (&v)[P])
 {
-    if (vec && base + P <= n) {
+    if (vec && base + P <= n && aligned16_pair(g + base, g + n + base)) {
         const float4 h = __ldcs(reinterpret_cast<const float4*>(g + base));
         const float4 c = __ldcs(reinterpret_cast<const float4*>(g + n + base));
         v[0] = {h.x, c.x};
@@ -245,7 +252,7 @@ __device__ __forceinline__ void load4(const float* __restrict__ g, int64_t base,
 __device__ __forceinline__ void store4(float* __restrict__ g, int64_t base, int64_t n, bool vec,
                                        const DF (&v)[P])
 {
-    if (vec && base + P <= n) {
+    if (vec && base + P <= n && aligned16_pair(g + base, g + n + base)) {
         __stcs(reinterpret_cast<float4*>(g + base), make_float4(v[0].hi, v[1].hi, v[2].hi, v[3].hi));
         __stcs(reinterpret_cast<float4*>(g + n + base), make_float4(v[0].c, v[1].c, v[2].c, v[3].c));
     } else {

@@ -118,10 +118,17 @@ __device__ __forceinline__ void record(const double (&z)[P], const double (&d)[P
     block_record<NF>(f, smem, parity, rows, row, TRANS ? 16 : 6);
 }
 
+// 128-bit accesses only where the host allowed them (vec) AND the address really is
+// 16-byte aligned; anything else takes the scalar path.
+__device__ __forceinline__ bool aligned16(const void* p)
+{
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
 __device__ __forceinline__ void load2(const double* __restrict__ g, int64_t base, int64_t n,
                                       bool vec, double (&v)[P])
 {
-    if (vec && base + P <= n) {
+    if (vec && base + P <= n && aligned16(g + base)) {
         const double2 t = __ldcs(reinterpret_cast<const double2*>(g + base));
         v[0] = t.x;
         v[1] = t.y;
@@ -134,7 +141,7 @@ __device__ __forceinline__ void load2(const double* __restrict__ g, int64_t base
 __device__ __forceinline__ void store2(double* __restrict__ g, int64_t base, int64_t n,
                                        bool vec, const double (&v)[P])
 {
-    if (vec && base + P <= n) {
+    if (vec && base + P <= n && aligned16(g + base)) {
         __stcs(reinterpret_cast<double2*>(g + base), make_double2(v[0], v[1]));
     } else {
 #pragma unroll

@@ -146,3 +146,34 @@ def test_autotuner_picks_a_valid_shape():
         est_ms = 2e6 * t.turns_per_launch / t.particle_turns_per_s * 1e3
         assert 5.0 < est_ms < 80.0 or t.turns_per_launch == 8
     R.close()
+
+
+def test_autotuned_batch_with_odd_sizes():
+    """Regression: the autotuner's probe must keep its scratch buffers 16-byte aligned for
+    the 128-bit loads even when the batch has an odd particle count (513 here)."""
+    ring = synth.ring(2e6, transverse=True)
+    R = phtl.Ring(**ring)  # no tuning set: phtl_batch_create runs the autotuner per group
+    specs = [(513, 250, 6.0e6, "euler_cromer", "f32cd", 0, True),
+             (1001, 300, 2.0e6, "leapfrog", "f32c", 3, False),
+             (7, 400, 1.0e6, "ruth4", "f64", 0, False)]
+    jobs, refs = [], []
+    for i, (n, turns, V, integ, dt, stride, tr) in enumerate(specs):
+        b = _bufs(n, 500 + i, dt, tr, V)
+        jobs.append(phtl.make_job(*b, turns=turns, voltage_V=V, integrator=integ, dtype=dt,
+                                  monitor=_mon(turns, stride), stride=stride or 1))
+        refs.append((V, integ, dt, turns, [None if t is None else t.clone() for t in b]))
+    B = phtl.Batch(R, jobs)
+    info = B.info()
+    assert all(b in (0, 64, 128, 256) for b in info.block_threads)
+    B.run()
+    torch.cuda.synchronize()
+    for j, (V, integ, dt, turns, b) in zip(jobs, refs):
+        Rs = phtl.Ring(**dict(ring, voltage_V=V))
+        Rs.track(*b, turns=turns, integrator=integ, dtype=dt)
+        torch.cuda.synchronize()
+        for u, v in zip(j["c"], b):
+            if u is not None:
+                assert torch.equal(u, v)
+        Rs.close()
+    B.close()
+    R.close()
