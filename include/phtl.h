@@ -58,6 +58,7 @@ extern "C" {
 #define PHTL_E_CANCELLED (-6) /* the job was cancelled                                */
 #define PHTL_E_BADHANDLE (-7) /* null, destroyed or foreign handle / unknown ticket   */
 #define PHTL_E_NODEVICE (-8)  /* no CUDA device, or not an sm_103 device              */
+#define PHTL_E_TOOBIG (-9)    /* more jobs than phtl_batch_run_noalloc's fixed table   */
 
 /* ---- enums ------------------------------------------------------------------------- */
 enum { PHTL_EULER_CROMER = 0, PHTL_LEAPFROG = 1, PHTL_RUTH4 = 2 };
@@ -252,6 +253,31 @@ int phtl_batch_info_get(const phtl_batch* b, phtl_batch_info* out);
 
 /* Synchronise the device, free the job tables and graph.  Errors: PHTL_E_BADHANDLE.     */
 int phtl_batch_destroy(phtl_batch* b);
+
+/* Capacity of the fixed job table used by phtl_batch_run_noalloc. */
+#define PHTL_NOALLOC_MAX_JOBS 256
+
+/* One run of a batch that allocates nothing.  No counterpart in the paper: this entry
+ * point exists for callers that cannot let the library allocate device memory -- an
+ * application whose device memory is owned and budgeted by its own allocator or pool,
+ * or a loop that must never pay for cudaMalloc / cudaFree, which can block the host and
+ * synchronise the device.  It tracks the same jobs with the same kernels and gives the
+ * same particles as phtl_batch_create + phtl_batch_run (monitor sums equal to FP64
+ * rounding), but it calls no cudaMalloc, cudaFree or other allocating routine: the job
+ * table is written into a fixed device array of PHTL_NOALLOC_MAX_JOBS entries that lives
+ * in the library for as long as the process runs, on every GPU that loads it.  The
+ * launch shape is the handle's tuning (phtl_set_tuning), else 128 threads per block and
+ * the library's default turns per launch; no autotuner probe and no CUDA graph.
+ * jobs: as for phtl_batch_create (caller-owned device buffers, updated in place).
+ * The call is stream-ordered on cuda_stream.  The first call on a device looks up the
+ * array's device address (one-time set-up); make that first call before any stream
+ * capture.  Every call shares the array and it keeps the last call's contents; each call
+ * rewrites all entries it uses.  Calls that can overlap on the GPU (for example on two
+ * streams with no ordering between them) race on the array: order them on one stream.
+ * Errors: PHTL_E_TOOBIG (njobs > PHTL_NOALLOC_MAX_JOBS), PHTL_E_BADHANDLE,
+ * PHTL_E_INVALID, PHTL_E_UNSTABLE, PHTL_E_NODEVICE, PHTL_E_CUDA.                        */
+int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int32_t njobs,
+                           void* cuda_stream);
 
 /* ---- serving loop (continuous batching) ------------------------------------------------- */
 

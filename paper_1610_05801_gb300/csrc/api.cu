@@ -383,6 +383,7 @@ const char* phtl_strerror(int code)
         case PHTL_E_CANCELLED: return "cancelled";
         case PHTL_E_BADHANDLE: return "bad handle or ticket";
         case PHTL_E_NODEVICE: return "no sm_103 CUDA device";
+        case PHTL_E_TOOBIG: return "more jobs than the fixed table of the no-allocation batch run";
         default: return "unknown error code";
     }
 }

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libphtl.so")
 OK = 0
 E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_TIMEOUT, E_CANCELLED, E_BADHANDLE, E_NODEVICE = (
     -1, -2, -3, -4, -5, -6, -7, -8)
+E_TOOBIG = -9
+NOALLOC_MAX_JOBS = 256
 EULER_CROMER, LEAPFROG, RUTH4 = 0, 1, 2
 F64, F32C, F32CD = 0, 1, 2
 MON_FIELDS = 16
@@ -127,6 +129,7 @@ SIGNATURES = {
     "phtl_batch_run": (_int, [_vp, _vp]),
     "phtl_batch_info_get": (_int, [_vp, C.POINTER(BatchInfo)]),
     "phtl_batch_destroy": (_int, [_vp]),
+    "phtl_batch_run_noalloc": (_int, [_vp, C.POINTER(Job), C.c_int32, _vp]),
     "phtl_server_start": (_int, [_vp, C.POINTER(ServerConfig)]),
     "phtl_submit": (_int, [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
     "phtl_poll": (_int, [_vp, C.c_uint64, C.POINTER(Status)]),
@@ -368,6 +371,45 @@ def make_job(z, dp, x=None, xp=None, y=None, yp=None, turns=1, voltage_V=None,
                 integrator=integrator, dtype=dtype, monitor=monitor, stride=int(stride))
 
 
+def job_array(ring: Ring, jobs):
+    """phtl_job array for a list of make_job() dicts; returns (array, tensors to keep alive)."""
+    keep = []
+    arr = (Job * max(1, len(jobs)))()
+    for i, j in enumerate(jobs):
+        dt = _dtype(j["dtype"])
+        want = "float64" if dt == F64 else "float32"
+        for b in j["c"]:
+            if b is not None:
+                _check_tensor(b, want, "job buffer")
+                keep.append(b)
+        z = j["c"][0]
+        n = z.numel() if dt == F64 else z.numel() // 2
+        for k in range(6):
+            arr[i].c[k] = _ptr(j["c"][k])
+        mon = j.get("monitor")
+        if mon is not None:
+            _check_tensor(mon, "float64", "monitor")
+            keep.append(mon)
+            arr[i].mon_rows = mon.data_ptr()
+            arr[i].mon_capacity = mon.shape[0]
+            arr[i].mon_stride = int(j.get("stride", 1))
+        arr[i].n = n
+        arr[i].turns = int(j["turns"])
+        v = j.get("voltage_V")
+        arr[i].voltage_V = float(ring.params.voltage_V if v is None else v)
+        arr[i].integrator = _integrator(j["integrator"])
+        arr[i].dtype = dt
+    return arr, keep
+
+
+def batch_run_noalloc(ring: Ring, jobs, stream=None):
+    """One run of `jobs` through phtl_batch_run_noalloc (no device allocation; the job
+    table goes into the library's fixed device array).  Stream-ordered."""
+    arr, _keep = job_array(ring, jobs)
+    _check(load().phtl_batch_run_noalloc(ring.handle, arr, len(jobs), _stream_ptr(stream)),
+           "phtl_batch_run_noalloc")
+
+
 class Batch:
     """Many independent bunches tracked by shared, graph-captured launches
     (phtl_batch_create / phtl_batch_run)."""
@@ -375,32 +417,7 @@ class Batch:
     def __init__(self, ring: Ring, jobs, use_graph: bool = True):
         self._lib = load()
         self._ring = ring
-        self._keep = []
-        arr = (Job * max(1, len(jobs)))()
-        for i, j in enumerate(jobs):
-            dt = _dtype(j["dtype"])
-            want = "float64" if dt == F64 else "float32"
-            for b in j["c"]:
-                if b is not None:
-                    _check_tensor(b, want, "job buffer")
-                    self._keep.append(b)
-            z = j["c"][0]
-            n = z.numel() if dt == F64 else z.numel() // 2
-            for k in range(6):
-                arr[i].c[k] = _ptr(j["c"][k])
-            mon = j.get("monitor")
-            if mon is not None:
-                _check_tensor(mon, "float64", "monitor")
-                self._keep.append(mon)
-                arr[i].mon_rows = mon.data_ptr()
-                arr[i].mon_capacity = mon.shape[0]
-                arr[i].mon_stride = int(j.get("stride", 1))
-            arr[i].n = n
-            arr[i].turns = int(j["turns"])
-            v = j.get("voltage_V")
-            arr[i].voltage_V = float(ring.params.voltage_V if v is None else v)
-            arr[i].integrator = _integrator(j["integrator"])
-            arr[i].dtype = dt
+        arr, self._keep = job_array(ring, jobs)
         self._jobs = arr
         h = _vp()
         _check(self._lib.phtl_batch_create(ring.handle, arr, len(jobs), 1 if use_graph else 0,
