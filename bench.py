@@ -446,7 +446,7 @@ def _clocked(fn):
 
 
 def run_batched(args, wl_name, wl):
-    """Config 3: one graph-captured batch of uneven bunches per step."""
+    """64 uneven bunches: one graph-captured batch per step."""
     import numpy as np
     import torch
 
@@ -481,12 +481,12 @@ def run_batched(args, wl_name, wl):
     t_create = time.perf_counter()
     B = phtl.Batch(R, jobs, use_graph=True)
     t_create = time.perf_counter() - t_create
-    info = B.info()
-    pt = info.particle_turns_per_run
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         B.run(stream)
     torch.cuda.synchronize()
+    info = B.info()
+    pt = info.particle_turns_per_run
 
     def timed():
         evs = []
@@ -528,7 +528,7 @@ def run_batched(args, wl_name, wl):
 
 
 def run_serving(args, wl_name, wl):
-    """Config 4: continuous batching of a Poisson trace; p50/p99 latency."""
+    """Serving: continuous batching of a Poisson trace of jobs; p50/p99 latency."""
     import numpy as np
 
     from paper_1610_05801_gb300 import build as _build
@@ -601,7 +601,7 @@ def run_serving(args, wl_name, wl):
 
 
 def run_precision(args, wl_name, wl):
-    """Config 2: FP32C vs FP64 moments after 1e6 turns (halo bunch), on the GPU; the FP64
+    """Precision sweep: FP32C vs FP64 moments after 1e6 turns (halo bunch), on the GPU; the FP64
     oracle re-tracks the 1e4-particle subsample (with --oracle)."""
     import numpy as np
     import torch
@@ -619,7 +619,7 @@ def run_precision(args, wl_name, wl):
     turns, sub, stride = wl["turns"], wl["subsample"], wl["stride"]
     rows = turns // stride + 1
     res = {}
-    for dt in ("f32c", "f32cd"):
+    for dt in ("f32c", "f32cd", "f32cs"):
         bz = torch.tensor(phtl.split_f32c(z), dtype=torch.float32, device=dev)
         bd = torch.tensor(phtl.split_f32c(d), dtype=torch.float32, device=dev)
         mon = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
@@ -643,9 +643,10 @@ def run_precision(args, wl_name, wl):
     torch.cuda.synchronize()
     R.set_monitor(None)
     m64 = phtl.moments_from_sums(mon.cpu().numpy())
+    z64, d64 = bz.cpu().numpy(), bd.cpu().numpy()
     out = {"metric": "moment relative error FP32C vs FP64 after 1e6 turns", "workload": wl_name,
            "n": wl["n"], "turns": turns, "subsample": sub}
-    for dt in ("f32c", "f32cd"):
+    for dt in ("f32c", "f32cd", "f32cs"):
         # the FP32 path's subsample, tracked separately so its moments can be compared row by row
         sz = torch.tensor(phtl.split_f32c(z[:sub]), dtype=torch.float32, device=dev)
         sd = torch.tensor(phtl.split_f32c(d[:sub]), dtype=torch.float32, device=dev)
@@ -660,12 +661,19 @@ def run_precision(args, wl_name, wl):
         for name, j, sc in (("mean_z", 0, 2), ("mean_dp", 1, 3), ("rms_z", 2, 2),
                             ("rms_dp", 3, 3), ("eps_z", 4, 4)):
             rel[name] = float(np.max(np.abs(m32[:, j] - m64[:, j]) / np.abs(m64[:, sc])))
+        # invariant of each particle after 1e6 turns, FP32 path vs FP64 path (the same map,
+        # so the scheme's own oscillation of H cancels), and the per-particle distance
         H = lambda zz, dd: 0.5 * der.etaC * dd * dd + (der.A / der.k) * (1 - np.cos(der.k * zz))
-        h0, h1 = H(z[:sub], d[:sub]), H(res[dt]["z"], res[dt]["d"])
+        h64, h32 = H(z64, d64), H(res[dt]["z"], res[dt]["d"])
+        dh = np.abs(h32 - h64) / h64
+        zb, db = np.pi / der.k, der.bucket_half_height
+        dist = np.hypot((res[dt]["z"] - z64) / zb, (res[dt]["d"] - d64) / db)
         out[dt] = {"pts_full": wl["n"] * turns / (res[dt]["ms"] / 1e3), "kernel_ms": res[dt]["ms"],
                    "max_rel_moment_err": rel,
-                   "hamiltonian_drift_rel_median": float(np.median(np.abs(h1 - h0) / h0)),
-                   "hamiltonian_drift_rel_max": float(np.max(np.abs(h1 - h0) / h0))}
+                   "invariant_rel_diff_median": float(np.median(dh)),
+                   "invariant_rel_diff_max": float(np.max(dh)),
+                   "particle_dist_median": float(np.median(dist)),
+                   "particle_dist_p90": float(np.quantile(dist, 0.9))}
     if args.oracle:
         import oracle
 
@@ -698,7 +706,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int)
     ap.add_argument("--turns", type=int)
     ap.add_argument("--schemes", help="comma-separated integrators")
-    ap.add_argument("--dtype", choices=("f64", "f32c", "f32cd"))
+    ap.add_argument("--dtype", choices=("f64", "f32c", "f32cd", "f32cs"))
     ap.add_argument("--stride", type=int, help="monitor stride (0 = no monitor)")
     ap.add_argument("--no-transverse", action="store_true")
     ap.add_argument("--perturn", action="store_true", help="one launch per turn (HBM-bound variant)")

@@ -65,13 +65,17 @@ enum { PHTL_EULER_CROMER = 0, PHTL_LEAPFROG = 1, PHTL_RUTH4 = 2 };
 
 /* Arithmetic of the particle state.
  *  PHTL_F64   : every coordinate buffer holds n doubles.
- *  PHTL_F32C  : FP32 with compensated (Kahan/TwoSum) accumulation.  Every coordinate
- *               buffer holds 2n floats: [hi(0..n-1) | comp(0..n-1)]; the value of
- *               particle i is hi[i] + comp[i].  The RF phase argument k z is formed in
- *               FP64 from hi + comp, then rounded to FP32 for the SFU sine.
- *  PHTL_F32CD : as PHTL_F32C, but the phase argument is formed in double-float
- *               (FP32 pair) arithmetic instead of FP64.                               */
-enum { PHTL_F64 = 0, PHTL_F32C = 1, PHTL_F32CD = 2 };
+ *  PHTL_F32C  : FP32 with compensated (TwoSum) accumulation.  Every coordinate buffer
+ *               holds 2n floats: [hi(0..n-1) | comp(0..n-1)]; the value of particle i is
+ *               hi[i] + comp[i].  Drift and kick increments are FP32 products with the
+ *               FP64 coefficients split into hi + lo floats.  The RF phase argument k z
+ *               is formed in FP64 from hi + comp and rounded to FP32; the sine is the
+ *               library's FP32 polynomial sine (~1 ulp).
+ *  PHTL_F32CD : as PHTL_F32C, but the phase argument is formed in double-float (FP32
+ *               pair) arithmetic instead of FP64 (no FP64 instruction on the path).
+ *  PHTL_F32CS : as PHTL_F32CD, but the sine is the SFU's (__sinf, absolute error
+ *               ~2^-21 on [-pi, pi]): fastest, least accurate over long horizons.    */
+enum { PHTL_F64 = 0, PHTL_F32C = 1, PHTL_F32CD = 2, PHTL_F32CS = 3 };
 
 /* ---- machine description ----------------------------------------------------------- */
 typedef struct phtl_params {
@@ -159,7 +163,7 @@ int phtl_set_tuning(phtl_handle* h, int32_t block_threads, int64_t turns_per_lau
  * turns into bounded launches).
  * z, dp: device pointers (required when n > 0).  x, xp / y, yp: device pointers, or
  * both NULL to leave that plane out.  Layout: PHTL_F64 -> n doubles per coordinate;
- * PHTL_F32C / PHTL_F32CD -> 2n floats per coordinate ([hi | comp]).  Pointers must be
+ * PHTL_F32C / PHTL_F32CD / PHTL_F32CS -> 2n floats per coordinate ([hi | comp]).  Pointers must be
  * aligned to the element size; 16-byte alignment enables 128-bit loads.
  * integrator: PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
@@ -200,7 +204,7 @@ typedef struct phtl_job {
     int64_t turns;        /* turns tracked by each run of the batch                        */
     double voltage_V;     /* RF voltage of this bunch                                      */
     int32_t integrator;   /* PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4                 */
-    int32_t dtype;        /* PHTL_F64 | PHTL_F32C | PHTL_F32CD                              */
+    int32_t dtype;        /* PHTL_F64 | PHTL_F32C | PHTL_F32CD | PHTL_F32CS                 */
 } phtl_job;
 
 typedef struct phtl_batch phtl_batch; /* opaque, library-owned */
@@ -216,10 +220,9 @@ typedef struct phtl_tuning {
 typedef struct phtl_batch_info {
     int32_t njobs;
     int32_t graph;                       /* 1: runs replay a captured CUDA graph          */
-    int32_t block_threads[3];            /* per arithmetic (PHTL_F64, F32C, F32CD); 0 = none */
-    int32_t pad_;
-    int64_t turns_per_launch[3];
-    double probe_particle_turns_per_s[3];
+    int32_t block_threads[4];            /* per arithmetic (PHTL_F64 .. PHTL_F32CS); 0 = none */
+    int64_t turns_per_launch[4];
+    double probe_particle_turns_per_s[4];
     int64_t launches_per_run;            /* kernel launches in one run (known after a run) */
     int64_t tiles_first_launch;          /* blocks of the first chunk launch, all groups   */
     int64_t particle_turns_per_run;      /* sum of n * turns                              */
@@ -291,7 +294,7 @@ typedef struct phtl_server_config {
     int32_t block_threads;       /* 0 = autotuned per arithmetic                          */
     int64_t chunk_turns_f64;     /* turns per scheduling round for FP64 jobs; 0 = chosen
                                     every round for a ~target_round_ms round               */
-    int64_t chunk_turns_f32;     /* the same for PHTL_F32C / PHTL_F32CD jobs               */
+    int64_t chunk_turns_f32;     /* the same for the FP32-compensated jobs                 */
     double target_round_ms;      /* 0 = 20 ms                                              */
 } phtl_server_config;
 

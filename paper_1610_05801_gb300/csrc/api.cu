@@ -30,6 +30,18 @@ void split_df(double v, float& hi, float& lo)
     lo = static_cast<float>(v - static_cast<double>(hi));
 }
 
+// Three-shear form of the rotation by mu = 2 pi frac(Q) with beta function b:
+// [[c, b s], [-s/b, c]] = [[1, p], [0, 1]] [[1, 0], [q, 1]] [[1, p], [0, 1]],
+// p = b tan(mu/2), q = -s/b.  Near mu = pi, tan(mu/2) blows up: keep the matrix.
+void shear_params(double Q, double b, double (&sh)[2], int32_t& use)
+{
+    const double mu = 2.0 * kPi * (Q - std::floor(Q));
+    const double t = std::tan(0.5 * mu);
+    use = std::isfinite(t) && std::fabs(t) < 1e3 ? 1 : 0;
+    sh[0] = use ? b * t : 0.0;
+    sh[1] = use ? -std::sin(mu) / b : 0.0;
+}
+
 void scheme_consts(const phtl_derived& d, int scheme, MapConsts& c)
 {
     scheme_weights(scheme, d.A, d.etaC, c.dc, c.kw);
@@ -86,10 +98,12 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
             split_df(d.mx[i], c.mx_hi[i], c.mx_lo[i]);
             split_df(d.my[i], c.my_hi[i], c.my_lo[i]);
         }
+        shear_params(p.Qx, p.beta_x_m, c.shx, c.shear_x);
+        shear_params(p.Qy, p.beta_y_m, c.shy, c.shear_y);
         split_df(d.k, c.k_hi, c.k_lo);
         split_df(p.phi_s_rad, c.phis_hi, c.phis_lo);
-        c.sinphis_f = static_cast<float>(d.sin_phis);
-        c.lin_f = static_cast<float>(c.lin);
+        split_df(d.sin_phis, c.sinphis_hi, c.sinphis_lo);
+        split_df(c.lin, c.lin_hi, c.lin_lo);
     }
     return PHTL_OK;
 }
@@ -217,7 +231,7 @@ int check_track_args(const phtl_handle* h, void* const* c, int64_t n, int64_t tu
 {
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
     if (integrator < PHTL_EULER_CROMER || integrator > PHTL_RUTH4) return PHTL_E_INVALID;
-    if (dtype < PHTL_F64 || dtype > PHTL_F32CD) return PHTL_E_INVALID;
+    if (dtype < PHTL_F64 || dtype > PHTL_F32CS) return PHTL_E_INVALID;
     if (n < 0 || turns < 0) return PHTL_E_INVALID;
     if (n > 0 && (!c[0] || !c[1])) return PHTL_E_INVALID;
     if ((c[2] == nullptr) != (c[3] == nullptr)) return PHTL_E_INVALID;

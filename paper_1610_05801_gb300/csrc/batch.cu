@@ -68,8 +68,7 @@ double probe_rate(phtl_handle* h, int dtype, int scheme, int block, int64_t m, i
                              (dtype == PHTL_F64 || (m * 4) % 16 == 0);
         J.vec = aligned ? 1 : 0;
         scheme_weights(scheme, h->derived.A, h->derived.etaC, J.dc, J.kw);
-        for (int i = 0; i < 4; ++i) J.dc_hi[i] = static_cast<float>(J.dc[i]);
-        for (int j = 0; j < 3; ++j) J.kw_hi[j] = static_cast<float>(J.kw[j]);
+        fill_float_weights(J);
         if (cudaMalloc(reinterpret_cast<void**>(&dj), sizeof(JobDesc)) != cudaSuccess) break;
         if (cudaMemcpyAsync(dj, &J, sizeof(J), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
         const int ppt = particles_per_thread(dtype);
@@ -218,7 +217,7 @@ int phtl_autotune(phtl_handle* h, int dtype, int integrator, int64_t active_part
                   double target_launch_ms, phtl_tuning* out)
 {
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
-    if (!out || dtype < PHTL_F64 || dtype > PHTL_F32CD || integrator < 0 || integrator > 2 ||
+    if (!out || dtype < PHTL_F64 || dtype > PHTL_F32CS || integrator < 0 || integrator > 2 ||
         active_particles < 0 || !(target_launch_ms > 0.0))
         return PHTL_E_INVALID;
     return autotune(h, dtype, integrator, active_particles, target_launch_ms, out);
@@ -255,7 +254,7 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
     b->info.njobs = njobs;
     b->info.graph = b->use_graph ? 1 : 0;
 
-    for (int dt = PHTL_F64; dt <= PHTL_F32CD; ++dt) {
+    for (int dt = PHTL_F64; dt <= PHTL_F32CS; ++dt) {
         std::vector<int32_t> idx;
         for (int32_t i = 0; i < njobs; ++i)
             if (jobs[i].dtype == dt) idx.push_back(i);
@@ -311,8 +310,7 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
             J.scheme = U.integrator;
             J.tile_begin = tiles;
             scheme_weights(U.integrator, kick_amplitude(h->params, d, U.voltage_V), d.etaC, J.dc, J.kw);
-            for (int i = 0; i < 4; ++i) J.dc_hi[i] = static_cast<float>(J.dc[i]);
-            for (int j = 0; j < 3; ++j) J.kw_hi[j] = static_cast<float>(J.kw[j]);
+            fill_float_weights(J);
             tiles += (U.n + per_tile - 1) / per_tile;
             G.jobs.push_back(J);
             G.mon_bytes.push_back(U.mon_rows ? (U.turns / U.mon_stride + 1) * PHTL_MON_FIELDS * 8 : 0);

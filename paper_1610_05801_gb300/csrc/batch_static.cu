@@ -96,7 +96,7 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
     JobDesc host[PHTL_NOALLOC_MAX_JOBS];
     int32_t order[PHTL_NOALLOC_MAX_JOBS];
     int32_t used = 0;
-    for (int dt = PHTL_F64; dt <= PHTL_F32CD; ++dt) {
+    for (int dt = PHTL_F64; dt <= PHTL_F32CS; ++dt) {
         int32_t cnt = 0;
         for (int32_t i = 0; i < njobs; ++i)
             if (jobs[i].dtype == dt) order[cnt++] = i;
@@ -133,8 +133,7 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
             J.scheme = U.integrator;
             J.tile_begin = tiles;
             scheme_weights(U.integrator, kick_amplitude(h->params, d, U.voltage_V), d.etaC, J.dc, J.kw);
-            for (int i = 0; i < 4; ++i) J.dc_hi[i] = static_cast<float>(J.dc[i]);
-            for (int i = 0; i < 3; ++i) J.kw_hi[i] = static_cast<float>(J.kw[i]);
+            fill_float_weights(J);
             tiles += (U.n + per_tile - 1) / per_tile;
             if (U.mon_rows) {
                 rc = cuda_rc(cudaMemsetAsync(U.mon_rows, 0,

@@ -9,6 +9,8 @@
 
 namespace phtl {
 
+constexpr int kNumDtypes = 4;  // PHTL_F64 .. PHTL_F32CS
+
 // Per-stage coefficients of one turn of the longitudinal map (Sec. 1.1.2 schemes),
 // pre-multiplied on the host in FP64:
 //   drift stage i:  z <- z - dc[i] * delta           dc[i] = w_i * eta * C
@@ -24,10 +26,14 @@ struct MapConsts {
     double lin;      // cos(phi_s) * k (rf_linear mode)
     double mx[4];    // transverse one-turn matrices, row-major
     double my[4];
+    // the same rotations as three shears, u += p v; v += q u; u += p v with
+    // p = beta tan(mu/2), q = -sin(mu)/beta (shear_* = 0: use the matrix instead)
+    double shx[2], shy[2];
+    int32_t shear_x, shear_y;
     // double-float (FP32 pair) copies for the FP32 paths: value = hi + lo
     float dc_hi[4], dc_lo[4];
     float kw_hi[3], kw_lo[3];
-    float k_hi, k_lo, phis_hi, phis_lo, sinphis_f, lin_f;
+    float k_hi, k_lo, phis_hi, phis_lo, sinphis_hi, sinphis_lo, lin_hi, lin_lo;
     float mx_hi[4], mx_lo[4], my_hi[4], my_lo[4];
     int32_t linear;  // rf_linear flag
     int32_t pad_;
@@ -70,12 +76,27 @@ struct JobDesc {
                          // continue from there; the initial row is written when it is 0)
     double dc[4];        // drift weights w_i * eta C of the job's scheme
     double kw[3];        // kick weights w_j * A_job of the job's scheme
-    float dc_hi[4];      // the same rounded to FP32
+    float dc_hi[4];      // the same split into FP32 hi + lo (value = hi + lo)
+    float dc_lo[4];
     float kw_hi[3];
+    float kw_lo[3];
     int32_t scheme;      // integrator
     int32_t vec;         // nonzero: 16-byte aligned buffers (128-bit loads)
     int32_t pad_;
 };
+
+// Split the job's FP64 drift / kick weights into FP32 hi + lo pairs.
+inline void fill_float_weights(JobDesc& J)
+{
+    for (int i = 0; i < 4; ++i) {
+        J.dc_hi[i] = static_cast<float>(J.dc[i]);
+        J.dc_lo[i] = static_cast<float>(J.dc[i] - static_cast<double>(J.dc_hi[i]));
+    }
+    for (int i = 0; i < 3; ++i) {
+        J.kw_hi[i] = static_cast<float>(J.kw[i]);
+        J.kw_lo[i] = static_cast<float>(J.kw[i] - static_cast<double>(J.kw_hi[i]));
+    }
+}
 
 // Launchers (one per kernel family); return cudaGetLastError() of the launch.
 cudaError_t launch_track_f64(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,

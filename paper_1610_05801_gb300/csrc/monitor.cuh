@@ -13,6 +13,7 @@
 
 #include <cstdint>
 
+#include "dfloat.cuh"
 #include "phtl.h"
 
 namespace phtl {
@@ -64,6 +65,52 @@ __device__ __forceinline__ void block_record(double (&f)[NF], double* smem, int 
         double s = 0.0;
         for (int w = 0; w < nwarps; ++w) s += buf[w * 16 + lane];
         atomicAdd(rows + row * PHTL_MON_FIELDS + lane, s);
+    }
+}
+
+// The same reduction with double-float (FP32 pair) partial sums, for the FP64 kernel:
+// the butterfly and the block sum run on the FP32 pipe; only the block total of each
+// field is converted to FP64 for the atomic add.  smem: 2 * (blockDim.x / 32) * 16 DF2.
+template <int NF>
+__device__ __forceinline__ DF2 warp_reduce_scatter_df(DF2 (&f)[NF], int lane)
+{
+    static_assert(NF == 8 || NF == 16, "NF must be 8 or 16");
+#pragma unroll
+    for (int o = 16; o >= (NF == 16 ? 2 : 4); o >>= 1) {
+        const int h = (NF == 16) ? (o >> 1) : (o >> 2);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < NF / 2; ++i) {
+            if (i < h) {
+                const DF2 send = upper ? f[i] : f[i + h];
+                const DF2 keep = upper ? f[i + h] : f[i];
+                f[i] = df_add(keep, df_shfl_xor(send, o));
+            }
+        }
+    }
+    DF2 v = f[0];
+    if (NF == 8) v = df_add(v, df_shfl_xor(v, 2));
+    v = df_add(v, df_shfl_xor(v, 1));
+    return v;
+}
+
+template <int NF>
+__device__ __forceinline__ void block_record_df(DF2 (&f)[NF], DF2* smem, int parity,
+                                                double* __restrict__ rows, int64_t row,
+                                                int nvalid)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const DF2 v = warp_reduce_scatter_df<NF>(f, lane);
+    DF2* buf = smem + parity * (nwarps * 16);
+    constexpr int kShift = (NF == 16) ? 1 : 2;
+    if ((lane & ((1 << kShift) - 1)) == 0) buf[warp * 16 + (lane >> kShift)] = v;
+    __syncthreads();
+    if (warp == 0 && lane < nvalid) {
+        DF2 s = buf[lane];
+        for (int w = 1; w < nwarps; ++w) s = df_add(s, buf[w * 16 + lane]);
+        atomicAdd(rows + row * PHTL_MON_FIELDS + lane, df_to_double(s));
     }
 }
 

@@ -5,8 +5,10 @@
 
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 #include "monitor.cuh"
+#include "sin_f64.cuh"
 
 namespace phtl {
 namespace f32c {
@@ -71,71 +73,170 @@ __device__ __forceinline__ void df_rotate(DF& u, DF& v, const float (&mh)[4], co
     }
 }
 
-// Phase argument phi = phi_s + k z rounded to FP32 and reduced to [-pi, pi].
-template <int DT>
-__device__ __forceinline__ float phase(const MapConsts& c, const DF& z)
+// ---------------------------------------------------------------------------------------
+// Arithmetic of PHTL_F32C / PHTL_F32CD: double-float (FP32 pair, ~48 bits) throughout.
+// Increments are double-float products and are added with TwoSum + Fast2Sum, the sine is
+// a double-float polynomial, so each turn's relative error stays near 1e-14: over 1e6 turns
+// particles near the separatrix (where the tune varies steeply with amplitude) keep their
+// phases, and bunch moments follow the FP64 result.
+
+__device__ __forceinline__ DF2 as2(const DF& a) { return DF2{a.hi, a.c}; }
+__device__ __forceinline__ DF2 neg2(DF2 a) { return DF2{-a.h, -a.l}; }
+
+__device__ __forceinline__ void acc2(DF& a, DF2 inc)
 {
-    float ph;
+    const DF2 s = df_add(as2(a), inc);
+    a.hi = s.h;
+    a.c = s.l;
+}
+
+// float -> double with integer operations (the F2F instruction runs at the FP64 pipe's
+// rate on this GPU).  Subnormal floats become zero; Inf / NaN use the conversion.
+__device__ __forceinline__ double widen_bits(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0xffu) return static_cast<double>(f);
+    const unsigned sign = u & 0x80000000u;
+    if (e == 0u) return __hiloint2double(static_cast<int>(sign), 0);
+    const unsigned m = u & 0x7fffffu;
+    return __hiloint2double(static_cast<int>(sign | ((e + 896u) << 20) | (m >> 3)),
+                            static_cast<int>(m << 29));
+}
+
+// Phase argument phi = phi_s + k z as a double-float pair.  PHTL_F32C forms it in FP64 from
+// hi + comp (exact in double) with one DFMA; PHTL_F32CD in double-float arithmetic.
+template <int DT>
+__device__ __forceinline__ DF2 phase_df(const MapConsts& c, const DF& z)
+{
     if (DT == PHTL_F32C) {
-        // FP64: hi + comp is exact in double; one DFMA, then round to FP32
-        const double zd = static_cast<double>(z.hi) + static_cast<double>(z.c);
-        ph = static_cast<float>(fma(c.k, zd, c.phis));
-    } else {
-        // double-float: exact FP32 product k_hi * z_hi plus the cross terms, plus phi_s
-        const float p = __fmul_rn(c.k_hi, z.hi);
-        float e = __fmaf_rn(c.k_hi, z.hi, -p);
-        e = __fmaf_rn(c.k_hi, z.c, __fmaf_rn(c.k_lo, z.hi, e));
-        const float s = __fadd_rn(p, c.phis_hi);
-        const float bb = __fsub_rn(s, p);
-        const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.phis_hi, bb));
-        ph = __fadd_rn(s, __fadd_rn(err, __fadd_rn(e, c.phis_lo)));
+        const double zd = widen_bits(z.hi) + widen_bits(z.c);
+        return split_bits(fma(c.k, zd, c.phis));
     }
-    // reduce by 2 pi (two-part constant) so the SFU sine sees |arg| <= ~pi
-    const float nq = rintf(ph * kInvTwoPi);
-    return __fmaf_rn(-nq, kTwoPiLo, __fmaf_rn(-nq, kTwoPiHi, ph));
+    return df_add(df_mul(DF2{c.k_hi, c.k_lo}, as2(z)), DF2{c.phis_hi, c.phis_lo});
 }
 
-template <int DT>
-__device__ __forceinline__ float rf_force(const MapConsts& c, const DF& z)
+// Double-float split of an FP64 constant at compile time.
+struct DFC {
+    float h, l;
+    __host__ __device__ constexpr DFC(double v) : h(static_cast<float>(v)), l(static_cast<float>(v - static_cast<double>(static_cast<float>(v)))) {}
+};
+
+// Double-float sine, absolute error ~1e-14 on the kick's range.  Cody-Waite reduction
+// x = q pi/2 + r with a three-part pi/2 whose products with q are formed exactly, then on
+// |r| <= pi/4 one polynomial chosen per lane by the quadrant parity,
+// sin r = r + r^3 S(r^2), cos r = 1 - r^2/2 + r^4 C(r^2), with the coefficients of the FP64
+// sine (sin_f64.cuh): the three leading Horner steps in double-float, the three small
+// trailing terms (|t^3 S_3| <= 7e-7, |t^3 C_3| <= 6e-6) in plain FP32.  |x| >= 1e4 falls back
+// to the FP64 sine.
+__device__ __forceinline__ DF2 sin_df(DF2 x)
 {
-    if (c.linear) return c.lin_f * (z.hi + z.c);
-    return __sinf(phase<DT>(c, z)) - c.sinphis_f;
+    if (!(fabsf(x.h) < 1.0e4f)) return split_bits(sin_f64(widen_bits(x.h) + widen_bits(x.l)));
+    const float magic = 12582912.0f;
+    const float t0 = __fmaf_rn(x.h, 0.6366197466850281f, magic);
+    const float q = __fsub_rn(t0, magic);
+    const int qi = __float_as_int(t0);
+    // r = x - q (P1 + P2 + P3), pi/2 = P1 + P2 + P3 (+1e-23)
+    const float p1 = __fmul_rn(q, 1.5707963705062866f);
+    const float e1 = __fmaf_rn(q, 1.5707963705062866f, -p1);
+    DF2 r = df_add(x, DF2{-p1, -e1});
+    const float p2 = __fmul_rn(q, -4.371138828673793e-08f);
+    const float e2 = __fmaf_rn(q, -4.371138828673793e-08f, -p2);
+    r = df_add(r, DF2{-p2, -e2});
+    r = df_add(r, DF2{__fmul_rn(q, 1.7151245100058819e-15f), 0.0f});
+    const DF2 t = df_mul(r, r);
+    const bool odd = (qi & 1) != 0;
+    // trailing terms in FP32
+    float tail = odd ? -1.1382632425521717e-11f : 1.5918129294866608e-10f;
+    tail = __fmaf_rn(tail, t.h, odd ? 2.08761462684032e-09f : -2.5051131845003624e-08f);
+    tail = __fmaf_rn(tail, t.h, odd ? -2.7557317271729793e-07f : 2.755731610255244e-06f);
+    // leading Horner steps in double-float
+    constexpr DFC s2(-0.00019841269836758574), s1(0.008333333333330948), s0(-0.16666666666666666);
+    constexpr DFC c2(2.480158729876569e-05), c1(-0.0013888888888887398), c0(0.041666666666666664);
+    DF2 u = df_add(df_mul(t, DF2{tail, 0.0f}), odd ? DF2{c2.h, c2.l} : DF2{s2.h, s2.l});
+    u = df_add(df_mul(t, u), odd ? DF2{c1.h, c1.l} : DF2{s1.h, s1.l});
+    u = df_add(df_mul(t, u), odd ? DF2{c0.h, c0.l} : DF2{s0.h, s0.l});
+    const DF2 m = df_mul(odd ? t : r, t);                                  // r^3 or r^4
+    const DF2 a = odd ? df_add(DF2{1.0f, 0.0f}, DF2{-0.5f * t.h, -0.5f * t.l}) : r;
+    const DF2 res = df_add(a, df_mul(m, u));
+    return (qi & 2) ? neg2(res) : res;
 }
 
+// ---------------------------------------------------------------------------------------
+// Arithmetic of PHTL_F32CS: FP32 increments and the SFU sine (fast, less accurate).
+
+// Phase argument rounded to FP32 (double-float formation, then rounded).
+__device__ __forceinline__ float phase_f(const MapConsts& c, const DF& z)
+{
+    const DF2 ph = df_add(df_mul(DF2{c.k_hi, c.k_lo}, as2(z)), DF2{c.phis_hi, c.phis_lo});
+    return __fadd_rn(ph.h, ph.l);
+}
+
+__device__ __forceinline__ float sin_sfu(float x)
+{
+    const float nq = rintf(x * kInvTwoPi);
+    return __sinf(__fmaf_rn(-nq, kTwoPiLo, __fmaf_rn(-nq, kTwoPiHi, x)));
+}
+
+// ---------------------------------------------------------------------------------------
+// kick: delta += kw * (sin(phi) - sin(phi_s)), kw = kh + kl (the FP64 weight as a pair)
 template <int DT>
-__device__ __forceinline__ void kick(const DF (&z)[P], DF (&d)[P], float kw, const MapConsts& c)
+__device__ __forceinline__ void kick(const DF (&z)[P], DF (&d)[P], float kh, float kl,
+                                     const MapConsts& c)
 {
 #pragma unroll
-    for (int p = 0; p < P; ++p) acc(d[p], __fmul_rn(kw, rf_force<DT>(c, z[p])));
+    for (int p = 0; p < P; ++p) {
+        if (DT == PHTL_F32CS) {
+            const float f = c.linear ? c.lin_hi * (z[p].hi + z[p].c)
+                                     : sin_sfu(phase_f(c, z[p])) - c.sinphis_hi;
+            acc(d[p], __fmaf_rn(kh, f, __fmul_rn(kl, f)));
+        } else {
+            const DF2 f = c.linear ? df_mul(DF2{c.lin_hi, c.lin_lo}, as2(z[p]))
+                                   : df_add(sin_df(phase_df<DT>(c, z[p])),
+                                            DF2{-c.sinphis_hi, -c.sinphis_lo});
+            acc2(d[p], df_mul(DF2{kh, kl}, f));
+        }
+    }
 }
 
-__device__ __forceinline__ void drift(DF (&z)[P], const DF (&d)[P], float dc)
+// drift: z -= dc * delta, dc = dh + dl
+template <int DT>
+__device__ __forceinline__ void drift(DF (&z)[P], const DF (&d)[P], float dh, float dl)
 {
 #pragma unroll
-    for (int p = 0; p < P; ++p) acc(z[p], __fmul_rn(-dc, d[p].hi));
+    for (int p = 0; p < P; ++p) {
+        if (DT == PHTL_F32CS) {
+            const float inc = __fmaf_rn(dh, d[p].hi, __fmaf_rn(dl, d[p].hi, __fmul_rn(dh, d[p].c)));
+            acc(z[p], -inc);
+        } else {
+            acc2(z[p], neg2(df_mul(DF2{dh, dl}, as2(d[p]))));
+        }
+    }
 }
 
-// dc, kw: FP32 drift and kick weights of this bunch's scheme (the single-bunch kernel
-// passes c.dc_hi, c.kw_hi, the batched kernel the job table's copies).
+// dh, dl, kh, kl: the drift and kick weights of this bunch's scheme split into FP32
+// hi + lo (the single-bunch kernel passes the MapConsts copies, the batched kernel the
+// job table's).
 template <int SCHEME, int DT>
 __device__ __forceinline__ void long_turn(DF (&z)[P], DF (&d)[P], const MapConsts& c,
-                                          const float* dc, const float* kw)
+                                          const float* dh, const float* dl, const float* kh,
+                                          const float* kl)
 {
     if (SCHEME == PHTL_EULER_CROMER) {
-        kick<DT>(z, d, kw[0], c);
-        drift(z, d, dc[0]);
+        kick<DT>(z, d, kh[0], kl[0], c);
+        drift<DT>(z, d, dh[0], dl[0]);
     } else if (SCHEME == PHTL_LEAPFROG) {
-        drift(z, d, dc[0]);
-        kick<DT>(z, d, kw[0], c);
-        drift(z, d, dc[1]);
+        drift<DT>(z, d, dh[0], dl[0]);
+        kick<DT>(z, d, kh[0], kl[0], c);
+        drift<DT>(z, d, dh[1], dl[1]);
     } else {
-        drift(z, d, dc[0]);
-        kick<DT>(z, d, kw[0], c);
-        drift(z, d, dc[1]);
-        kick<DT>(z, d, kw[1], c);
-        drift(z, d, dc[2]);
-        kick<DT>(z, d, kw[2], c);
-        drift(z, d, dc[3]);
+        drift<DT>(z, d, dh[0], dl[0]);
+        kick<DT>(z, d, kh[0], kl[0], c);
+        drift<DT>(z, d, dh[1], dl[1]);
+        kick<DT>(z, d, kh[1], kl[1], c);
+        drift<DT>(z, d, dh[2], dl[2]);
+        kick<DT>(z, d, kh[2], kl[2], c);
+        drift<DT>(z, d, dh[3], dl[3]);
     }
 }
 
@@ -189,7 +290,7 @@ __device__ __forceinline__ void record(const DF (&z)[P], const DF (&d)[P], const
     float f[NF];
     f[0] = cnt;
     pair_sums(z, d, f + 1);
-    if (TRANS) {
+    if constexpr (TRANS) {
         if (hx) {
             pair_sums(x, xp, f + 6);
         } else {

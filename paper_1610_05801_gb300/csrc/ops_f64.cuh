@@ -8,6 +8,7 @@
 
 #include "internal.h"
 #include "monitor.cuh"
+#include "dfloat.cuh"
 #include "sin_f64.cuh"
 
 namespace phtl {
@@ -59,8 +60,20 @@ __device__ __forceinline__ void long_turn(double (&z)[P], double (&d)[P], const 
     }
 }
 
-__device__ __forceinline__ void rotate(double (&u)[P], double (&v)[P], const double (&m)[4])
+// Transverse push of one plane (Sec. 1.1.1 matrix).  With use_shear the rotation is
+// applied as three shears (3 DFMA instead of 2 DMUL + 2 DFMA); the same map up to rounding.
+__device__ __forceinline__ void rotate(double (&u)[P], double (&v)[P], const double (&m)[4],
+                                       const double (&sh)[2], bool use_shear)
 {
+    if (use_shear) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            u[p] = fma(sh[0], v[p], u[p]);
+            v[p] = fma(sh[1], u[p], v[p]);
+            u[p] = fma(sh[0], v[p], u[p]);
+        }
+        return;
+    }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double un = fma(m[1], v[p], m[0] * u[p]);
@@ -70,23 +83,32 @@ __device__ __forceinline__ void rotate(double (&u)[P], double (&v)[P], const dou
     }
 }
 
-__device__ __forceinline__ void pair_sums(const double (&a)[P], const double (&b)[P], double* f)
+// Per-thread moment contributions of one plane (a, b): sum a, sum b, sum a^2, sum b^2,
+// sum ab over this thread's P particles, as double-float pairs.  The doubles are split
+// into float pairs with integer operations and the products formed with the exact FP32
+// product error, so the sums keep ~47 bits without using the FP64 pipe.
+__device__ __forceinline__ void pair_sums_df(const double (&a)[P], const double (&b)[P], DF2* f)
 {
-    f[0] = a[0];
-    f[1] = b[0];
-    f[2] = a[0] * a[0];
-    f[3] = b[0] * b[0];
-    f[4] = a[0] * b[0];
+    DF2 ap = split_bits(a[0]), bp = split_bits(b[0]);
+    f[0] = ap;
+    f[1] = bp;
+    f[2] = df_mul(ap, ap);
+    f[3] = df_mul(bp, bp);
+    f[4] = df_mul(ap, bp);
 #pragma unroll
     for (int p = 1; p < P; ++p) {
-        f[0] += a[p];
-        f[1] += b[p];
-        f[2] = fma(a[p], a[p], f[2]);
-        f[3] = fma(b[p], b[p], f[3]);
-        f[4] = fma(a[p], b[p], f[4]);
+        ap = split_bits(a[p]);
+        bp = split_bits(b[p]);
+        f[0] = df_add(f[0], ap);
+        f[1] = df_add(f[1], bp);
+        f[2] = df_add(f[2], df_mul(ap, ap));
+        f[3] = df_add(f[3], df_mul(bp, bp));
+        f[4] = df_add(f[4], df_mul(ap, bp));
     }
 }
 
+// Add this block's moment sums of the current turn into monitor row `row`.
+// smem: 2 * (blockDim.x / 32) * 16 DF2.
 template <bool TRANS>
 __device__ __forceinline__ void record(const double (&z)[P], const double (&d)[P],
                                        const double (&x)[P], const double (&xp)[P],
@@ -95,27 +117,28 @@ __device__ __forceinline__ void record(const double (&z)[P], const double (&d)[P
                                        double* rows, int64_t row)
 {
     constexpr int NF = TRANS ? 16 : 8;
-    double f[NF];
-    f[0] = cnt;
-    pair_sums(z, d, f + 1);
-    if (TRANS) {
+    const DF2 zero{0.0f, 0.0f};
+    DF2 f[NF];
+    f[0] = DF2{static_cast<float>(cnt), 0.0f};  // 0..P: exact
+    pair_sums_df(z, d, f + 1);
+    if constexpr (TRANS) {
         if (hx) {
-            pair_sums(x, xp, f + 6);
+            pair_sums_df(x, xp, f + 6);
         } else {
 #pragma unroll
-            for (int j = 6; j < 11; ++j) f[j] = 0.0;
+            for (int j = 6; j < 11; ++j) f[j] = zero;
         }
         if (hy) {
-            pair_sums(y, yp, f + 11);
+            pair_sums_df(y, yp, f + 11);
         } else {
 #pragma unroll
-            for (int j = 11; j < 16; ++j) f[j] = 0.0;
+            for (int j = 11; j < 16; ++j) f[j] = zero;
         }
     } else {
-        f[6] = 0.0;
-        f[7] = 0.0;
+        f[6] = zero;
+        f[7] = zero;
     }
-    block_record<NF>(f, smem, parity, rows, row, TRANS ? 16 : 6);
+    block_record_df<NF>(f, reinterpret_cast<DF2*>(smem), parity, rows, row, TRANS ? 16 : 6);
 }
 
 // 128-bit accesses only where the host allowed them (vec) AND the address really is

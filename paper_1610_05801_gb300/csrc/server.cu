@@ -59,7 +59,7 @@ public:
 
     ~CudaExec()
     {
-        for (int g = 0; g < 3; ++g) {
+        for (int g = 0; g < kNumDtypes; ++g) {
             if (dtab_[g]) cudaFree(dtab_[g]);
             if (htab_[g]) cudaFreeHost(htab_[g]);
         }
@@ -76,7 +76,7 @@ public:
         for (auto& s : stream_)
             if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return cuda_rc(cudaErrorUnknown);
         const size_t tb = sizeof(JobDesc) * static_cast<size_t>(cfg_.max_active);
-        for (int g = 0; g < 3; ++g) {
+        for (int g = 0; g < kNumDtypes; ++g) {
             if (cudaMalloc(reinterpret_cast<void**>(&dtab_[g]), tb) != cudaSuccess) return cuda_rc(cudaErrorMemoryAllocation);
             if (cudaMallocHost(reinterpret_cast<void**>(&htab_[g]), tb) != cudaSuccess) return cuda_rc(cudaErrorMemoryAllocation);
             phtl_tuning t;
@@ -143,7 +143,7 @@ public:
         const phtl_derived& d = h_->derived;
         int64_t nl = 0;
         bool used[2] = {false, false};
-        for (int g = 0; g < 3; ++g) {
+        for (int g = 0; g < kNumDtypes; ++g) {
             std::vector<size_t> idx;
             int64_t active = 0;
             for (size_t i = 0; i < act.size(); ++i)
@@ -184,8 +184,7 @@ public:
                 J.tile_begin = tiles;
                 J.scheme = j.req.integrator;
                 scheme_weights(J.scheme, kick_amplitude(h_->params, d, j.req.voltage_V), d.etaC, J.dc, J.kw);
-                for (int i = 0; i < 4; ++i) J.dc_hi[i] = static_cast<float>(J.dc[i]);
-                for (int i = 0; i < 3; ++i) J.kw_hi[i] = static_cast<float>(J.kw[i]);
+                fill_float_weights(J);
                 tiles += (j.req.n + per_tile - 1) / per_tile;
                 nt[idx[k]] = std::min<int64_t>(T, J.turns);
             }
@@ -258,10 +257,10 @@ private:
     phtl_handle* h_;
     phtl_server_config cfg_;
     cudaStream_t stream_[2] = {nullptr, nullptr};
-    JobDesc* dtab_[3] = {nullptr, nullptr, nullptr};
-    JobDesc* htab_[3] = {nullptr, nullptr, nullptr};
-    int block_[3] = {128, 128, 128};
-    double rate_[3] = {1e10, 1e11, 1e11};
+    JobDesc* dtab_[kNumDtypes] = {};
+    JobDesc* htab_[kNumDtypes] = {};
+    int block_[kNumDtypes] = {128, 128, 128, 128};
+    double rate_[kNumDtypes] = {1e10, 1e11, 1e11, 1e11};
     double target_ms_ = 20.0;
 };
 
@@ -286,7 +285,7 @@ int check_request(const phtl_handle* h, const phtl_request* r)
 {
     if (!r) return PHTL_E_INVALID;
     if (r->integrator < PHTL_EULER_CROMER || r->integrator > PHTL_RUTH4) return PHTL_E_INVALID;
-    if (r->dtype < PHTL_F64 || r->dtype > PHTL_F32CD) return PHTL_E_INVALID;
+    if (r->dtype < PHTL_F64 || r->dtype > PHTL_F32CS) return PHTL_E_INVALID;
     if (r->n < 0 || r->turns < 0 || !std::isfinite(r->voltage_V)) return PHTL_E_INVALID;
     if (r->n > 0) {
         if (!r->out[0] || !r->out[1]) return PHTL_E_INVALID;

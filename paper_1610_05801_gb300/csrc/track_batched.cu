@@ -45,8 +45,8 @@ __device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P]
     int64_t row = g0 / J.stride + 1;
     for (int t = 0; t < nt; ++t) {
         f64::long_turn<SCHEME>(z, d, c, J.dc, J.kw);
-        if (hx) f64::rotate(x, xp, c.mx);
-        if (hy) f64::rotate(y, yp, c.my);
+        if (hx) f64::rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
+        if (hy) f64::rotate(y, yp, c.my, c.shy, c.shear_y != 0);
         if (MON) {
             if (--until == 0) {
                 f64::record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
@@ -140,7 +140,7 @@ __device__ __forceinline__ void run_f32c(f32c::DF (&z)[f32c::P], f32c::DF (&d)[f
     int64_t until = J.stride - (g0 % J.stride);
     int64_t row = g0 / J.stride + 1;
     for (int t = 0; t < nt; ++t) {
-        long_turn<SCHEME, DT>(z, d, c, J.dc_hi, J.kw_hi);
+        long_turn<SCHEME, DT>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo);
         if (hx) {
 #pragma unroll
             for (int p = 0; p < P; ++p) df_rotate(x[p], xp[p], c.mx_hi, c.mx_lo);
@@ -237,6 +237,9 @@ const void* select_batched(int dtype, bool mon)
     if (dtype == PHTL_F32CD)
         return mon ? reinterpret_cast<const void*>(&k_batched_f32c<PHTL_F32CD, true>)
                    : reinterpret_cast<const void*>(&k_batched_f32c<PHTL_F32CD, false>);
+    if (dtype == PHTL_F32CS)
+        return mon ? reinterpret_cast<const void*>(&k_batched_f32c<PHTL_F32CS, true>)
+                   : reinterpret_cast<const void*>(&k_batched_f32c<PHTL_F32CS, false>);
     return nullptr;
 }
 

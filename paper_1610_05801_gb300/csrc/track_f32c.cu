@@ -1,12 +1,15 @@
-// FP32-compensated persistent multi-turn tracking kernel (PHTL_F32C, PHTL_F32CD).
+// FP32-compensated persistent multi-turn tracking kernel (PHTL_F32C, PHTL_F32CD,
+// PHTL_F32CS).
 //
 // Same structure as the FP64 kernel (Sec. 2.3: turn loop inside the kernel, state in
 // registers), but every coordinate is an unevaluated sum hi + comp of two floats:
-//   - each drift/kick increment is computed in FP32 and added with Knuth's TwoSum, the
-//     rounding error going into comp, followed by a Fast2Sum renormalisation;
+//   - each drift/kick increment is one FP32 product with the FP64 weight split into
+//     hi + lo floats, added with Knuth's TwoSum (the rounding error goes into comp) and
+//     renormalised with Fast2Sum;
 //   - the RF phase argument k z is formed from hi + comp either in FP64 (PHTL_F32C) or
-//     in double-float FP32-pair arithmetic (PHTL_F32CD), reduced to [-pi, pi] and
-//     rounded to FP32 for the SFU sine (__sinf);
+//     in double-float FP32-pair arithmetic (PHTL_F32CD, PHTL_F32CS) and rounded to FP32;
+//     the sine is the library's FP32 polynomial (PHTL_F32C, PHTL_F32CD) or the SFU's
+//     __sinf (PHTL_F32CS);
 //   - the transverse matrix (Sec. 1.1.1) is applied in double-float arithmetic (exact
 //     FP32 products by fmaf, TwoSum of the two terms), so the rotation keeps ~48 bits;
 //   - per-turn moment sums are FP32 per thread and across the warp (<= 128 particles),
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(256) k_track_f32c(LaunchDesc L, MapConsts c, M
             parity ^= 1;
         }
         for (int t = 0; t < L.nturns; ++t) {
-            long_turn<SCHEME, DT>(z, d, c, c.dc_hi, c.kw_hi);
+            long_turn<SCHEME, DT>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo);
             if (TRANS) {
                 if (hx) {
 #pragma unroll
@@ -113,6 +116,7 @@ const void* sel_d(int dtype, bool trans, bool mon)
 {
     if (dtype == PHTL_F32C) return sel_tm<S, PHTL_F32C>(trans, mon);
     if (dtype == PHTL_F32CD) return sel_tm<S, PHTL_F32CD>(trans, mon);
+    if (dtype == PHTL_F32CS) return sel_tm<S, PHTL_F32CS>(trans, mon);
     return nullptr;
 }
 

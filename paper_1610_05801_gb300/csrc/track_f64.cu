@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, Mo
         for (int t = 0; t < L.nturns; ++t) {
             long_turn<SCHEME>(z, d, c, c.dc, c.kw);
             if (TRANS) {
-                if (hx) rotate(x, xp, c.mx);
-                if (hy) rotate(y, yp, c.my);
+                if (hx) rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
+                if (hy) rotate(y, yp, c.my, c.shy, c.shear_y != 0);
             }
             if (MON) {
                 if (--until == 0) {

@@ -22,11 +22,11 @@ E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_TIMEOUT, E_CANCELLED, E_BADHANDLE, E_N
 E_TOOBIG = -9
 NOALLOC_MAX_JOBS = 256
 EULER_CROMER, LEAPFROG, RUTH4 = 0, 1, 2
-F64, F32C, F32CD = 0, 1, 2
+F64, F32C, F32CD, F32CS = 0, 1, 2, 3
 MON_FIELDS = 16
 INTEGRATORS = {"euler_cromer": EULER_CROMER, "ec": EULER_CROMER, "leapfrog": LEAPFROG,
                "lf": LEAPFROG, "ruth4": RUTH4}
-DTYPES = {"f64": F64, "f32c": F32C, "f32cd": F32CD}
+DTYPES = {"f64": F64, "f32c": F32C, "f32cd": F32CD, "f32cs": F32CS}
 MOMENT_NAMES = (
     "mean_z", "mean_dp", "rms_z", "rms_dp", "eps_z",
     "mean_x", "mean_xp", "rms_x", "rms_xp", "eps_x",
@@ -71,9 +71,9 @@ class Tuning(C.Structure):
 
 
 class BatchInfo(C.Structure):
-    _fields_ = [("njobs", C.c_int32), ("graph", C.c_int32), ("block_threads", C.c_int32 * 3),
-                ("pad_", C.c_int32), ("turns_per_launch", C.c_int64 * 3),
-                ("probe_particle_turns_per_s", C.c_double * 3), ("launches_per_run", C.c_int64),
+    _fields_ = [("njobs", C.c_int32), ("graph", C.c_int32), ("block_threads", C.c_int32 * 4),
+                ("turns_per_launch", C.c_int64 * 4),
+                ("probe_particle_turns_per_s", C.c_double * 4), ("launches_per_run", C.c_int64),
                 ("tiles_first_launch", C.c_int64), ("particle_turns_per_run", C.c_int64)]
 
 

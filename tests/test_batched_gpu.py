@@ -28,6 +28,7 @@ JOBS = [  # n, turns, voltage, integrator, dtype, monitor stride (0 = none), tra
     (0, 10, 2.0e6, "euler_cromer", "f32c", 1, False),
     (10, 0, 2.0e6, "leapfrog", "f64", 1, False),
     (4099, 64, 5.0e6, "euler_cromer", "f32c", 0, True),
+    (1500, 900, 3.5e6, "leapfrog", "f32cs", 2, True),
 ]
 
 
@@ -137,7 +138,8 @@ def test_batch_f64_against_oracle():
 
 def test_autotuner_picks_a_valid_shape():
     R = phtl.Ring(**synth.ring(2e6))
-    for dt, integ in (("f64", "leapfrog"), ("f32c", "leapfrog"), ("f32cd", "ruth4")):
+    for dt, integ in (("f64", "leapfrog"), ("f32c", "leapfrog"), ("f32cd", "ruth4"),
+                      ("f32cs", "euler_cromer")):
         t = R.autotune(dt, integ, active_particles=2_000_000, target_launch_ms=20.0)
         assert t.block_threads in (64, 128, 256)
         assert 8 <= t.turns_per_launch <= 1 << 20
@@ -164,7 +166,7 @@ def test_autotuned_batch_with_odd_sizes():
         refs.append((V, integ, dt, turns, [None if t is None else t.clone() for t in b]))
     B = phtl.Batch(R, jobs)
     info = B.info()
-    assert all(b in (0, 64, 128, 256) for b in info.block_threads)
+    assert all(b in (0, 64, 128, 256) for b in info.block_threads) and len(info.block_threads) == 4
     B.run()
     torch.cuda.synchronize()
     for j, (V, integ, dt, turns, b) in zip(jobs, refs):

@@ -203,7 +203,7 @@ def test_linear_mode_matches_closed_form():
     R.close()
 
 
-@pytest.mark.parametrize("dtype", ["f32c", "f32cd"])
+@pytest.mark.parametrize("dtype", ["f32c", "f32cd", "f32cs"])
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_f32c_moments_and_particles(dtype, scheme):
     inp = helpers.inputs(4096 + 7, seed=21)
@@ -216,3 +216,20 @@ def test_f32c_moments_and_particles(dtype, scheme):
     err = helpers.rel_errors(inp["d"], ref, got, inp["z"], inp["dp"])
     assert np.max(err) < 1e-2, np.max(err)
     assert np.median(err) < 1e-4, np.median(err)
+
+
+def test_f64_transverse_special_tunes():
+    """frac(Q) = 0.5 (mu = pi: the three-shear form degenerates, the matrix is used) and
+    frac(Q) = 0 (identity) against the oracle."""
+    from paper_1610_05801_gb300 import synth
+
+    inp = helpers.inputs(777, seed=17)
+    ring = dict(synth.ring(4.5e6, transverse=True), Qx=20.5, Qy=21.0)
+    d = oracle.derive(ring)
+    inp = dict(inp, ring=ring, d=d)
+    for scheme in SCHEMES:
+        got, _ = run_gpu(inp, scheme, 1000)
+        ref, _ = run_ref(inp, scheme, 1000)
+        err = helpers.rel_errors(d, ref, got, inp["z"], inp["dp"])
+        assert np.max(err) < 1e-10, (scheme, np.max(err))
+        assert np.allclose(got[4], inp["y"], rtol=0, atol=0) and np.allclose(got[5], inp["yp"], rtol=0, atol=0)
