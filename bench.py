@@ -49,6 +49,9 @@ WORKLOADS = {
     # one graph-captured batch per step
     "batched_64_bunches_f32c_lf": dict(kind="batched", nbunch=64, total=6e7, dtype="f32c",
                                        scheme="leapfrog", stride=1),
+    # the same batch with the double-float phase (no FP64 instruction on the path)
+    "batched_64_bunches_f32cd_lf": dict(kind="batched", nbunch=64, total=6e7, dtype="f32cd",
+                                        scheme="leapfrog", stride=1),
     # the same batch in FP64 (per-job FP64 reference point; turns scaled down by 100)
     "batched_64_bunches_f64_lf": dict(kind="batched", nbunch=64, total=6e7, dtype="f64",
                                       scheme="leapfrog", stride=1, turn_scale=0.01),
@@ -268,6 +271,7 @@ def run_ours(args, wl_name, wl):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
     ev = {s: [] for s in wl["schemes"]}
+    nlaunch = {s: 0 for s in wl["schemes"]}
     track = R.track_perturn if wl.get("perturn") else R.track
 
     def step(record=False):
@@ -275,11 +279,13 @@ def run_ours(args, wl_name, wl):
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
+                l0 = R.stats().launches
                 e0.record(stream)
             track(*bufs, turns=turns, integrator=s, dtype=dt, stream=stream)
             if record:
                 e1.record(stream)
                 ev[s].append((e0, e1))
+                nlaunch[s] += R.stats().launches - l0
 
     for _ in range(args.warmup):
         step()
@@ -317,7 +323,7 @@ def run_ours(args, wl_name, wl):
     # dominant kernel: the most expensive scheme's persistent kernel
     per_scheme_ms = {s: sum(a.elapsed_time(b) for a, b in ev[s]) / len(ev[s]) for s in ev}
     dom = max(per_scheme_ms, key=per_scheme_ms.get)
-    launches_per_call = max(1, launches // (args.steps * len(wl["schemes"])))
+    launches_per_call = max(1, nlaunch[dom] // args.steps)
     tpl = math.ceil(turns / launches_per_call)
     dur_s = per_scheme_ms[dom] / 1e3 / launches_per_call
     flops = alg_flops(dom, wl["transverse"], wl["stride"] > 0) * n * tpl
@@ -346,7 +352,8 @@ def run_ours(args, wl_name, wl):
         "roofline": roof or {
             "bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": kernel_traffic(dt, dom, wl, n),
             "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
                            "counts and max clock); DFMA rate confirmed by a microbenchmark",
             "alg_flops_per_particle_turn": alg_flops(dom, wl["transverse"], wl["stride"] > 0),
@@ -360,6 +367,19 @@ def run_ours(args, wl_name, wl):
         "wall_s_timed_region": wall,
     }
     return finish_line(line, args, wl, rank, R, dist)
+
+
+# DRAM bytes per particle per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# persistent FP64 kernel, from one ncu capture of the current kernel on a 3e6-particle case
+# (state larger than L2); the launch's traffic grows in proportion to its particles.
+# Summary: profiles/k_track_f64_ruth4_transverse_monitor_3e6x100.md.
+NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.328448e6 + 83.300352e6) / 3e6}
+
+
+def kernel_traffic(dt, scheme, wl, n):
+    key = (dt, scheme, bool(wl["transverse"]), bool(wl["stride"]))
+    b = NCU_TRAFFIC_BYTES_PER_PARTICLE.get(key)
+    return None if b is None or wl.get("perturn") else b * n
 
 
 def per_turn_roofline(wl, per_scheme_ms, n, turns, dt):
