@@ -92,6 +92,7 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
         c.sinphis = d.sin_phis;
         c.lin = d.cos_phis * d.k;
         c.linear = p.rf_linear != 0;
+        c.phis_zero = d.sin_phis == 0.0 ? 1 : 0;
         for (int i = 0; i < 4; ++i) {
             c.mx[i] = d.mx[i];
             c.my[i] = d.my[i];
@@ -265,7 +266,7 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     const bool mon = mon_rows != nullptr;
     const int block = h->block > 0 ? h->block : (perturn ? 256 : 128);
     const int es = dtype == PHTL_F64 ? 8 : 4;
-    const int ppt = perturn ? (dtype == PHTL_F64 ? 2 : 4) : (dtype == PHTL_F64 ? 2 : 4);
+    const int ppt = particles_per_thread(dtype);
     int64_t tpl = perturn ? 1 : (h->tpl > 0 ? h->tpl : auto_turns_per_launch(dtype, integrator, n));
     tpl = std::min<int64_t>(tpl, 1 << 30);
 

@@ -57,6 +57,20 @@ __device__ __forceinline__ DF2 split_bits(double x)
     return r;
 }
 
+// float -> double with integer operations (the F2F instruction runs at the FP64 pipe's
+// rate on this GPU).  Subnormal floats become zero; Inf / NaN use the conversion.
+__device__ __forceinline__ double widen_float_bits(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0xffu) return static_cast<double>(f);
+    const unsigned sign = u & 0x80000000u;
+    if (e == 0u) return __hiloint2double(static_cast<int>(sign), 0);
+    const unsigned m = u & 0x7fffffu;
+    return __hiloint2double(static_cast<int>(sign | ((e + 896u) << 20) | (m >> 3)),
+                            static_cast<int>(m << 29));
+}
+
 __device__ __forceinline__ DF2 df_two_sum(float a, float b)
 {
     const float s = __fadd_rn(a, b);

@@ -30,6 +30,7 @@ struct MapConsts {
     // p = beta tan(mu/2), q = -sin(mu)/beta (shear_* = 0: use the matrix instead)
     double shx[2], shy[2];
     int32_t shear_x, shear_y;
+    int32_t phis_zero;  // sin(phi_s) == 0: the kick skips the subtraction
     // double-float (FP32 pair) copies for the FP32 paths: value = hi + lo
     float dc_hi[4], dc_lo[4];
     float kw_hi[3], kw_lo[3];

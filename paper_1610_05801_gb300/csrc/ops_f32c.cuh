@@ -90,19 +90,7 @@ __device__ __forceinline__ void acc2(DF& a, DF2 inc)
     a.c = s.l;
 }
 
-// float -> double with integer operations (the F2F instruction runs at the FP64 pipe's
-// rate on this GPU).  Subnormal floats become zero; Inf / NaN use the conversion.
-__device__ __forceinline__ double widen_bits(float f)
-{
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0xffu) return static_cast<double>(f);
-    const unsigned sign = u & 0x80000000u;
-    if (e == 0u) return __hiloint2double(static_cast<int>(sign), 0);
-    const unsigned m = u & 0x7fffffu;
-    return __hiloint2double(static_cast<int>(sign | ((e + 896u) << 20) | (m >> 3)),
-                            static_cast<int>(m << 29));
-}
+__device__ __forceinline__ double widen_bits(float f) { return widen_float_bits(f); }
 
 // Phase argument phi = phi_s + k z as a double-float pair.  PHTL_F32C forms it in FP64 from
 // hi + comp (exact in double) with one DFMA; PHTL_F32CD in double-float arithmetic.
@@ -122,13 +110,16 @@ struct DFC {
     __host__ __device__ constexpr DFC(double v) : h(static_cast<float>(v)), l(static_cast<float>(v - static_cast<double>(static_cast<float>(v)))) {}
 };
 
-// Double-float sine, absolute error ~1e-14 on the kick's range.  Cody-Waite reduction
-// x = q pi/2 + r with a three-part pi/2 whose products with q are formed exactly, then on
-// |r| <= pi/4 one polynomial chosen per lane by the quadrant parity,
-// sin r = r + r^3 S(r^2), cos r = 1 - r^2/2 + r^4 C(r^2), with the coefficients of the FP64
-// sine (sin_f64.cuh): the three leading Horner steps in double-float, the three small
-// trailing terms (|t^3 S_3| <= 7e-7, |t^3 C_3| <= 6e-6) in plain FP32.  |x| >= 1e4 falls back
-// to the FP64 sine.
+// Double-float sine, absolute error ~1e-12 on the kick's range (a per-kick force error
+// far below what moves a particle's phase measurably in 1e6 turns).
+// Reduction x = q pi/2 + r with pi/2 = P1 + P2 + P3: q P1 is formed exactly (two_prod),
+// x.h - q P1 exactly as a TwoSum pair (its low part is zero whenever Sterbenz applies), and
+// the small remainder (x.l - e1 - q P2 - q P3, each ~1e-7) is summed in FP32 and
+// renormalised.  Then on |r| <= pi/4 one polynomial chosen per lane by the
+// quadrant parity, sin r = r + r^3 S(r^2), cos r = 1 - r^2/2 + r^4 C(r^2), with the
+// coefficients of the FP64 sine (sin_f64.cuh): the two leading Horner steps in
+// double-float, the four trailing terms (|t^2 S_2| <= 8e-5, |t^2 C_2| <= 1e-5) in FP32.
+// |x| >= 1e4 falls back to the FP64 sine.
 __device__ __forceinline__ DF2 sin_df(DF2 x)
 {
     if (!(fabsf(x.h) < 1.0e4f)) return split_bits(sin_f64(widen_bits(x.h) + widen_bits(x.l)));
@@ -136,25 +127,24 @@ __device__ __forceinline__ DF2 sin_df(DF2 x)
     const float t0 = __fmaf_rn(x.h, 0.6366197466850281f, magic);
     const float q = __fsub_rn(t0, magic);
     const int qi = __float_as_int(t0);
-    // r = x - q (P1 + P2 + P3), pi/2 = P1 + P2 + P3 (+1e-23)
     const float p1 = __fmul_rn(q, 1.5707963705062866f);
     const float e1 = __fmaf_rn(q, 1.5707963705062866f, -p1);
-    DF2 r = df_add(x, DF2{-p1, -e1});
-    const float p2 = __fmul_rn(q, -4.371138828673793e-08f);
-    const float e2 = __fmaf_rn(q, -4.371138828673793e-08f, -p2);
-    r = df_add(r, DF2{-p2, -e2});
-    r = df_add(r, DF2{__fmul_rn(q, 1.7151245100058819e-15f), 0.0f});
+    const DF2 hd = df_two_sum(x.h, -p1);  // exact as a pair (Sterbenz makes hd.l ~0)
+    float rest = __fadd_rn(__fsub_rn(x.l, e1), hd.l);
+    rest = __fmaf_rn(-q, -4.371138828673793e-08f, rest);
+    rest = __fmaf_rn(-q, -1.7151245100058819e-15f, rest);
+    const DF2 r = df_fast_two_sum(hd.h, rest);
     const DF2 t = df_mul(r, r);
     const bool odd = (qi & 1) != 0;
-    // trailing terms in FP32
+    // trailing terms in FP32: C_5..C_2 / S_5..S_2
     float tail = odd ? -1.1382632425521717e-11f : 1.5918129294866608e-10f;
     tail = __fmaf_rn(tail, t.h, odd ? 2.08761462684032e-09f : -2.5051131845003624e-08f);
     tail = __fmaf_rn(tail, t.h, odd ? -2.7557317271729793e-07f : 2.755731610255244e-06f);
+    tail = __fmaf_rn(tail, t.h, odd ? 2.480158729876569e-05f : -0.00019841269836758574f);
     // leading Horner steps in double-float
-    constexpr DFC s2(-0.00019841269836758574), s1(0.008333333333330948), s0(-0.16666666666666666);
-    constexpr DFC c2(2.480158729876569e-05), c1(-0.0013888888888887398), c0(0.041666666666666664);
-    DF2 u = df_add(df_mul(t, DF2{tail, 0.0f}), odd ? DF2{c2.h, c2.l} : DF2{s2.h, s2.l});
-    u = df_add(df_mul(t, u), odd ? DF2{c1.h, c1.l} : DF2{s1.h, s1.l});
+    constexpr DFC s1(0.008333333333330948), s0(-0.16666666666666666);
+    constexpr DFC c1(-0.0013888888888887398), c0(0.041666666666666664);
+    DF2 u = df_add(df_mul(t, DF2{tail, 0.0f}), odd ? DF2{c1.h, c1.l} : DF2{s1.h, s1.l});
     u = df_add(df_mul(t, u), odd ? DF2{c0.h, c0.l} : DF2{s0.h, s0.l});
     const DF2 m = df_mul(odd ? t : r, t);                                  // r^3 or r^4
     const DF2 a = odd ? df_add(DF2{1.0f, 0.0f}, DF2{-0.5f * t.h, -0.5f * t.l}) : r;

@@ -14,12 +14,18 @@
 namespace phtl {
 namespace f64 {
 
-constexpr int P = 2;
+// Particles per thread: independent FP64 dependency chains per thread (even).
+#ifndef PHTL_F64_PARTICLES_PER_THREAD
+#define PHTL_F64_PARTICLES_PER_THREAD 2
+#endif
+constexpr int P = PHTL_F64_PARTICLES_PER_THREAD;
+static_assert(P % 2 == 0, "P must be even (128-bit loads of two doubles)");
 
 __device__ __forceinline__ double rf_force(const MapConsts& c, double z)
 {
     if (c.linear) return c.lin * z;
-    return sin_f64(fma(c.k, z, c.phis)) - c.sinphis;
+    const double s = sin_f64(fma(c.k, z, c.phis));
+    return c.phis_zero ? s : s - c.sinphis;  // uniform integer test: no FP64 add for phi_s = 0
 }
 
 __device__ __forceinline__ void drift(double (&z)[P], const double (&d)[P], double dc)
@@ -113,13 +119,13 @@ template <bool TRANS>
 __device__ __forceinline__ void record(const double (&z)[P], const double (&d)[P],
                                        const double (&x)[P], const double (&xp)[P],
                                        const double (&y)[P], const double (&yp)[P],
-                                       double cnt, bool hx, bool hy, double* smem, int parity,
+                                       float cnt, bool hx, bool hy, double* smem, int parity,
                                        double* rows, int64_t row)
 {
     constexpr int NF = TRANS ? 16 : 8;
     const DF2 zero{0.0f, 0.0f};
     DF2 f[NF];
-    f[0] = DF2{static_cast<float>(cnt), 0.0f};  // 0..P: exact
+    f[0] = DF2{cnt, 0.0f};  // 0..P: exact
     pair_sums_df(z, d, f + 1);
     if constexpr (TRANS) {
         if (hx) {
@@ -152,9 +158,12 @@ __device__ __forceinline__ void load2(const double* __restrict__ g, int64_t base
                                       bool vec, double (&v)[P])
 {
     if (vec && base + P <= n && aligned16(g + base)) {
-        const double2 t = __ldcs(reinterpret_cast<const double2*>(g + base));
-        v[0] = t.x;
-        v[1] = t.y;
+#pragma unroll
+        for (int k = 0; k < P; k += 2) {
+            const double2 t = __ldcs(reinterpret_cast<const double2*>(g + base + k));
+            v[k] = t.x;
+            v[k + 1] = t.y;
+        }
     } else {
 #pragma unroll
         for (int p = 0; p < P; ++p) v[p] = (base + p < n) ? g[base + p] : 0.0;
@@ -165,7 +174,9 @@ __device__ __forceinline__ void store2(double* __restrict__ g, int64_t base, int
                                        bool vec, const double (&v)[P])
 {
     if (vec && base + P <= n && aligned16(g + base)) {
-        __stcs(reinterpret_cast<double2*>(g + base), make_double2(v[0], v[1]));
+#pragma unroll
+        for (int k = 0; k < P; k += 2)
+            __stcs(reinterpret_cast<double2*>(g + base + k), make_double2(v[k], v[k + 1]));
     } else {
 #pragma unroll
         for (int p = 0; p < P; ++p)

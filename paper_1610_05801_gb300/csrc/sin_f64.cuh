@@ -7,14 +7,16 @@
 // cosine) is selected per lane by the quadrant parity:
 //     sin r = r + r^3 S(r^2),   cos r = 1 - r^2/2 + r^4 C(r^2),   deg S = deg C = 5,
 // fitted by Chebyshev interpolation at 60 digits (gen_sin_coeffs.py; polynomial error
-// 2e-17 relative for S, 1.3e-18 for C).  13 FP64 operations per call, no branches and
-// no local memory on the path; the quadrant test and the range check use the integer
-// pipe.  |x| > 1e5 (far outside any RF bucket) falls back to CUDA's sin().
+// 2e-17 relative for S, 1.3e-18 for C).  11 FP64 operations per call, no branches and
+// no local memory on the path; the quadrant is found in FP32 and the range check on the
+// integer pipe.  |x| > 1e5 (far outside any RF bucket) falls back to CUDA's sin().
 // Accuracy: a few ulp on |x| <= 1e5 (checked against CUDA's sin and mpmath in the
 // tests through phtl_eval_sin).
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "dfloat.cuh"
 
 namespace phtl {
 namespace detail {
@@ -22,7 +24,6 @@ namespace detail {
 constexpr double kTwoOverPi = 0.63661977236758134308;
 constexpr double kPio2Hi = 1.5707963267948966;      // nearest double to pi/2
 constexpr double kPio2Lo = 6.123233995736766e-17;   // pi/2 - kPio2Hi
-constexpr double kRoundMagic = 6755399441055744.0;  // 1.5 * 2^52: adding it rounds to an integer
 
 __device__ __forceinline__ double sc_coef(bool odd, double s, double c) { return odd ? c : s; }
 
@@ -33,9 +34,13 @@ __device__ __forceinline__ double sin_f64(double x)
     using namespace detail;
     // |x| >= 1e5 (high word of 1e5 is 0x40f86a00): library sine
     if ((__double2hiint(x) & 0x7fffffff) >= 0x40f86a00) return sin(x);
-    const double t = fma(x, kTwoOverPi, kRoundMagic);
-    const double q = t - kRoundMagic;          // nearest integer to x * 2/pi
-    const int qi = __double2loint(t);          // q mod 2^32 (two's complement)
+    // quadrant q = nearest integer to x * 2/pi, found in FP32 from the top 24 bits of x
+    // (integer split: no FP64 instruction).  Near a half-integer q may be off by one,
+    // which only moves |r| a hair past pi/4, inside the polynomials' accuracy.
+    const float xf = split_bits(x).h;
+    const float tf = __fmaf_rn(xf, 0.6366197466850281f, 12582912.0f);
+    const int qi = __float_as_int(tf);         // q mod 2^22 in the low mantissa bits
+    const double q = widen_float_bits(__fsub_rn(tf, 12582912.0f));
     double r = fma(-q, kPio2Hi, x);
     r = fma(-q, kPio2Lo, r);
     const double r2 = r * r;

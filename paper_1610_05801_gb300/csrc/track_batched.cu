@@ -38,7 +38,7 @@ __device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P]
                                         double (&x)[f64::P], double (&xp)[f64::P],
                                         double (&y)[f64::P], double (&yp)[f64::P], bool hx,
                                         bool hy, const MapConsts& c, const JobDesc& J,
-                                        double cnt, int64_t t0, int nt, double* smem, int& parity)
+                                        float cnt, int64_t t0, int nt, double* smem, int& parity)
 {
     const int64_t g0 = t0 + J.turn_offset;  // turns done before this launch
     int64_t until = J.stride - (g0 % J.stride);
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_batched_f64(const JobDesc* __restrict__
         load2(gyp, base, J.n, vec, yp);
     }
     const int64_t left = J.n - base;
-    const double cnt = left >= P ? static_cast<double>(P) : (left > 0 ? static_cast<double>(left) : 0.0);
+    const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
     int parity = 0;
     if (mon && first) {
         record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, Mo
             load2(gyp, base, L.n, vec, yp);
         }
         const int64_t left = L.n - base;
-        const double cnt = left >= P ? static_cast<double>(P) : (left > 0 ? static_cast<double>(left) : 0.0);
+        const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
 
         int64_t until = m.until, row = m.row;
         if (MON && m.initial) {

@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libphtl.so")
+# PHTL_LIB selects another build of the library (e.g. a compile-time variant)
+LIB_PATH = os.environ.get("PHTL_LIB") or os.path.join(_HERE, "libphtl.so")
 
 OK = 0
 E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_TIMEOUT, E_CANCELLED, E_BADHANDLE, E_NODEVICE = (
