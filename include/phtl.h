@@ -296,7 +296,17 @@ typedef struct phtl_server_config {
                                     every round for a ~target_round_ms round               */
     int64_t chunk_turns_f32;     /* the same for the FP32-compensated jobs                 */
     double target_round_ms;      /* 0 = 20 ms                                              */
+    int32_t policy;              /* PHTL_POLICY_SRPT (0, default) or PHTL_POLICY_SHARE     */
+    int32_t pad_;
 } phtl_server_config;
+
+/* Which admitted jobs a scheduling round advances.
+ *  PHTL_POLICY_SRPT : per arithmetic, the jobs with the least remaining work
+ *                     (n x turns left) first, up to enough particles to keep the GPU busy,
+ *                     plus always the longest-admitted one (no starvation): short jobs
+ *                     finish early, lowering the median latency.
+ *  PHTL_POLICY_SHARE: every admitted job advances every round (processor sharing).    */
+enum { PHTL_POLICY_SRPT = 0, PHTL_POLICY_SHARE = 1 };
 
 /* One tracking request: host buffers in, host buffers out. */
 typedef struct phtl_request {

@@ -21,11 +21,14 @@ namespace f64 {
 constexpr int P = PHTL_F64_PARTICLES_PER_THREAD;
 static_assert(P % 2 == 0, "P must be even (128-bit loads of two doubles)");
 
+// ZS: sin(phi_s) == 0 (stationary bucket), so the subtraction is left out at compile time
+// (the kernels choose the instantiation once, outside the turn loop).
+template <bool ZS>
 __device__ __forceinline__ double rf_force(const MapConsts& c, double z)
 {
     if (c.linear) return c.lin * z;
     const double s = sin_f64(fma(c.k, z, c.phis));
-    return c.phis_zero ? s : s - c.sinphis;  // uniform integer test: no FP64 add for phi_s = 0
+    return ZS ? s : s - c.sinphis;
 }
 
 __device__ __forceinline__ void drift(double (&z)[P], const double (&d)[P], double dc)
@@ -34,34 +37,35 @@ __device__ __forceinline__ void drift(double (&z)[P], const double (&d)[P], doub
     for (int p = 0; p < P; ++p) z[p] = fma(-dc, d[p], z[p]);
 }
 
+template <bool ZS>
 __device__ __forceinline__ void kick(const double (&z)[P], double (&d)[P], double kw,
                                      const MapConsts& c)
 {
 #pragma unroll
-    for (int p = 0; p < P; ++p) d[p] = fma(kw, rf_force(c, z[p]), d[p]);
+    for (int p = 0; p < P; ++p) d[p] = fma(kw, rf_force<ZS>(c, z[p]), d[p]);
 }
 
 // One turn of the scheme; stage order as in Sec. 1.1.2's readings (see phtl.h).
 // dc, kw: the drift and kick weights of this bunch's scheme (w_i eta C, w_j A); the
 // single-bunch kernel passes c.dc, c.kw, the batched kernel the job table's copies.
-template <int SCHEME>
+template <int SCHEME, bool ZS>
 __device__ __forceinline__ void long_turn(double (&z)[P], double (&d)[P], const MapConsts& c,
                                           const double* dc, const double* kw)
 {
     if (SCHEME == PHTL_EULER_CROMER) {
-        kick(z, d, kw[0], c);
+        kick<ZS>(z, d, kw[0], c);
         drift(z, d, dc[0]);
     } else if (SCHEME == PHTL_LEAPFROG) {
         drift(z, d, dc[0]);
-        kick(z, d, kw[0], c);
+        kick<ZS>(z, d, kw[0], c);
         drift(z, d, dc[1]);
     } else {
         drift(z, d, dc[0]);
-        kick(z, d, kw[0], c);
+        kick<ZS>(z, d, kw[0], c);
         drift(z, d, dc[1]);
-        kick(z, d, kw[1], c);
+        kick<ZS>(z, d, kw[1], c);
         drift(z, d, dc[2]);
-        kick(z, d, kw[2], c);
+        kick<ZS>(z, d, kw[2], c);
         drift(z, d, dc[3]);
     }
 }

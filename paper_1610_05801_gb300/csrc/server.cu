@@ -131,6 +131,14 @@ public:
         return cuda_rc(cudaStreamSynchronize(s));
     }
 
+    // Two resident waves of the batched kernel of this arithmetic.
+    int64_t saturation(int dtype) const
+    {
+        const int g = dtype < 0 || dtype >= kNumDtypes ? 0 : dtype;
+        const int occ = std::max(1, occupancy_batched(g, true, block_[g]));
+        return 2ll * occ * h_->nsm * block_[g] * particles_per_thread(g);
+    }
+
     void adopt(sched::Job& to, sched::Job& from)
     {
         to.exec_state = from.exec_state;
@@ -317,6 +325,7 @@ int phtl_server_start(phtl_handle* h, const phtl_server_config* cfg)
     if (h->server) return PHTL_E_INVALID;
     phtl_server_config c{};
     if (cfg) c = *cfg;
+    if (c.policy != PHTL_POLICY_SRPT && c.policy != PHTL_POLICY_SHARE) return PHTL_E_INVALID;
     if (c.memory_budget_bytes < 0 || c.max_active < 0 || c.chunk_turns_f64 < 0 || c.chunk_turns_f32 < 0 ||
         c.target_round_ms < 0 || (c.block_threads != 0 && (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32)))
         return PHTL_E_INVALID;

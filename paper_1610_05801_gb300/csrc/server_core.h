@@ -14,6 +14,8 @@
 //   int  prepare(Job&)                             allocate + upload (a resumed job already
 //                                                  holds its state: only its monitor)
 //   void adopt(Job& to, Job& from)                 move a resident state to a resumed job
+//   int64_t saturation(int dtype)                 particles of one arithmetic that keep the
+//                                                  GPU busy (the SRPT policy's round size)
 //   int  run_round(std::vector<Job*>&, std::vector<int64_t>& nt, int64_t* launches)
 //   int  finish(Job&)                              download results; free unless resident
 //   void discard(Job&)                             free the job's device state
@@ -329,6 +331,7 @@ private:
                 std::lock_guard<std::mutex> g(mu_);
                 act.clear();
                 for (uint64_t t : active_) act.push_back(&jobs_.at(t));
+                if (cfg_.policy == PHTL_POLICY_SRPT) select_srpt(act);
             }
             if (act.empty()) continue;
             nt.assign(act.size(), 0);
@@ -368,6 +371,38 @@ private:
                 cv_.notify_all();
             }
         }
+    }
+
+    // Shortest remaining work first, per arithmetic: keep the jobs with the least
+    // n * (turns left) until their particles reach the executor's saturation size, and
+    // always the longest-admitted job of that arithmetic so no job starves.
+    void select_srpt(std::vector<Job*>& act)  // mu_ held
+    {
+        std::vector<Job*> keep;
+        for (int dt = PHTL_F64; dt <= PHTL_F32CS; ++dt) {
+            std::vector<Job*> g;
+            for (Job* j : act)
+                if (j->req.dtype == dt) g.push_back(j);
+            if (g.empty()) continue;
+            auto work = [](const Job* j) {
+                return static_cast<double>(j->req.n) * static_cast<double>(j->req.turns - j->turns_done);
+            };
+            std::stable_sort(g.begin(), g.end(), [&](Job* a, Job* b) { return work(a) < work(b); });
+            Job* oldest = *std::min_element(g.begin(), g.end(), [](Job* a, Job* b) {
+                return a->t_admit != b->t_admit ? a->t_admit < b->t_admit : a->ticket < b->ticket;
+            });
+            const int64_t sat = ex_.saturation(dt);
+            int64_t cum = 0;
+            bool has_oldest = false;
+            for (Job* j : g) {
+                if (cum > 0 && cum + j->req.n > sat) break;
+                keep.push_back(j);
+                cum += j->req.n;
+                has_oldest = has_oldest || j == oldest;
+            }
+            if (!has_oldest) keep.push_back(oldest);
+        }
+        act.swap(keep);
     }
 
     Exec& ex_;

@@ -53,9 +53,9 @@ __device__ __forceinline__ double sin_f64(double x)
     p = fma(p, r2, sc_coef(odd, -0.16666666666666666, 0.041666666666666664));
     const double m = (odd ? r2 : r) * r2;                 // r^3 or r^4
     const double a = odd ? fma(-0.5, r2, 1.0) : r;        // r or 1 - r^2/2
-    double res = fma(m, p, a);
-    if (qi & 2) res = -res;
-    return res;
+    const double res = fma(m, p, a);
+    // quadrants 2 and 3 flip the sign: an integer XOR of the sign bit, not an FP64 negate
+    return __longlong_as_double(__double_as_longlong(res) ^ (static_cast<long long>(qi & 2) << 62));
 }
 
 }  // namespace phtl

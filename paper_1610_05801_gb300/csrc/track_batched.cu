@@ -33,8 +33,8 @@ __device__ __forceinline__ int find_job(const JobDesc* __restrict__ jobs, int nj
 }
 
 // ---------------------------------------------------------------------------------- FP64
-template <int SCHEME, bool MON>
-__device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P],
+template <int SCHEME, bool MON, bool ZS>
+__device__ __forceinline__ void run_f64_zs(double (&z)[f64::P], double (&d)[f64::P],
                                         double (&x)[f64::P], double (&xp)[f64::P],
                                         double (&y)[f64::P], double (&yp)[f64::P], bool hx,
                                         bool hy, const MapConsts& c, const JobDesc& J,
@@ -44,7 +44,7 @@ __device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P]
     int64_t until = J.stride - (g0 % J.stride);
     int64_t row = g0 / J.stride + 1;
     for (int t = 0; t < nt; ++t) {
-        f64::long_turn<SCHEME>(z, d, c, J.dc, J.kw);
+        f64::long_turn<SCHEME, ZS>(z, d, c, J.dc, J.kw);
         if (hx) f64::rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
         if (hy) f64::rotate(y, yp, c.my, c.shy, c.shear_y != 0);
         if (MON) {
@@ -56,6 +56,19 @@ __device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P]
             }
         }
     }
+}
+
+template <int SCHEME, bool MON>
+__device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P],
+                                        double (&x)[f64::P], double (&xp)[f64::P],
+                                        double (&y)[f64::P], double (&yp)[f64::P], bool hx,
+                                        bool hy, const MapConsts& c, const JobDesc& J,
+                                        float cnt, int64_t t0, int nt, double* smem, int& parity)
+{
+    if (c.phis_zero)
+        run_f64_zs<SCHEME, MON, true>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
+    else
+        run_f64_zs<SCHEME, MON, false>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
 }
 
 template <bool MON>

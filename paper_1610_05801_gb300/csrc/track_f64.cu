@@ -20,6 +20,31 @@ namespace {
 
 using namespace f64;
 
+// The turn loop of one particle chunk (state in registers throughout).
+template <int SCHEME, bool TRANS, bool MON, bool ZS>
+__device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x)[P],
+                                      double (&xp)[P], double (&y)[P], double (&yp)[P], bool hx,
+                                      bool hy, float cnt, const MapConsts& c, const MonitorArgs& m,
+                                      int nturns, double* smem, int& parity)
+{
+    int64_t until = m.until, row = m.row;
+    for (int t = 0; t < nturns; ++t) {
+        long_turn<SCHEME, ZS>(z, d, c, c.dc, c.kw);
+        if (TRANS) {
+            if (hx) rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
+            if (hy) rotate(y, yp, c.my, c.shy, c.shear_y != 0);
+        }
+        if (MON) {
+            if (--until == 0) {
+                record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
+                parity ^= 1;
+                ++row;
+                until = m.stride;
+            }
+        }
+    }
+}
+
 template <int SCHEME, bool TRANS, bool MON>
 __global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
@@ -55,26 +80,14 @@ __global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, Mo
         const int64_t left = L.n - base;
         const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
 
-        int64_t until = m.until, row = m.row;
         if (MON && m.initial) {
             record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, 0);
             parity ^= 1;
         }
-        for (int t = 0; t < L.nturns; ++t) {
-            long_turn<SCHEME>(z, d, c, c.dc, c.kw);
-            if (TRANS) {
-                if (hx) rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
-                if (hy) rotate(y, yp, c.my, c.shy, c.shear_y != 0);
-            }
-            if (MON) {
-                if (--until == 0) {
-                    record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
-                    parity ^= 1;
-                    ++row;
-                    until = m.stride;
-                }
-            }
-        }
+        if (c.phis_zero)
+            turns<SCHEME, TRANS, MON, true>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns, smem, parity);
+        else
+            turns<SCHEME, TRANS, MON, false>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns, smem, parity);
         store2(gz, base, L.n, vec, z);
         store2(gd, base, L.n, vec, d);
         if (hx) {

@@ -16,6 +16,8 @@ using phtl::sched::Job;
 struct FakeExec {
     int64_t chunk = 100;
     double rate = 1e9;  // modelled particle-turns per second
+    int64_t sat = 1000000000;
+    int64_t saturation(int) const { return sat; }
     int64_t bytes_for(const phtl_request& r) const
     {
         const int64_t mon = r.mon_rows ? (r.turns / (r.mon_stride > 0 ? r.mon_stride : 1) + 1) * 128 : 0;
@@ -69,14 +71,17 @@ struct Fake {
 
 extern "C" {
 
-void* fake_start(int64_t budget, int32_t max_active, int64_t chunk, double rate)
+void* fake_start(int64_t budget, int32_t max_active, int64_t chunk, double rate, int32_t policy,
+                 int64_t sat)
 {
     phtl_server_config c{};
     c.memory_budget_bytes = budget;
     c.max_active = max_active;
+    c.policy = policy;
     Fake* f = new Fake(c);
     f->ex.chunk = chunk;
     f->ex.rate = rate;
+    f->ex.sat = sat;
     f->s.start();
     return f;
 }

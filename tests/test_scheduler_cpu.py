@@ -24,7 +24,7 @@ def fake(tmp_path_factory):
                     os.path.join(HERE, "sched_fake.cpp"), "-o", out], check=True)
     L = C.CDLL(out)
     L.fake_start.restype = C.c_void_p
-    L.fake_start.argtypes = [C.c_int64, C.c_int32, C.c_int64, C.c_double]
+    L.fake_start.argtypes = [C.c_int64, C.c_int32, C.c_int64, C.c_double, C.c_int32, C.c_int64]
     for name, args in (("fake_submit", [C.c_void_p, C.POINTER(phtl.Request), C.POINTER(C.c_uint64)]),
                        ("fake_poll", [C.c_void_p, C.c_uint64, C.POINTER(phtl.Status)]),
                        ("fake_wait", [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(phtl.Status)]),
@@ -39,9 +39,9 @@ def fake(tmp_path_factory):
 
 
 class FakeServer:
-    def __init__(self, L, budget=10**9, max_active=4, chunk=100, rate=1e9):
+    def __init__(self, L, budget=10**9, max_active=4, chunk=100, rate=1e9, policy=1, sat=10**9):
         self.L = L
-        self.h = L.fake_start(budget, max_active, chunk, rate)
+        self.h = L.fake_start(budget, max_active, chunk, rate, policy, sat)
         self.keep = []
 
     def submit(self, n, turns, keep=False, resume=0, mon=False):
@@ -196,3 +196,38 @@ def test_stop_cancels_pending(fake):
     st = [phtl.Status() for _ in ts]
     L.fake_stop(h)
     del st
+
+
+def test_srpt_policy_finishes_short_jobs_first(fake):
+    """Shortest remaining work first: with room for one job's particles per round, short jobs
+    submitted after a long one still finish first, and the long (oldest) job keeps moving."""
+    S = FakeServer(fake, max_active=8, chunk=50, rate=2e7, policy=0, sat=1000)
+    _, tl, _ = S.submit(1000, 2000)       # long, admitted first
+    shorts = [S.submit(1000, 100)[1] for _ in range(3)]
+    for t in shorts + [tl]:
+        assert S.wait(t)[0] == 0
+    done_short = max(S.poll(t).t_done_ns for t in shorts)
+    assert done_short < S.poll(tl).t_done_ns
+    assert S.poll(tl).turns_done == 2000
+    S.stop()
+    # processor sharing: every round advances every job; the short ones still finish first,
+    # but later than under SRPT relative to the long job's progress
+    S2 = FakeServer(fake, max_active=8, chunk=50, rate=2e7, policy=1, sat=1000)
+    _, tl2, _ = S2.submit(1000, 2000)
+    sh2 = [S2.submit(1000, 100)[1] for _ in range(3)]
+    for t in sh2 + [tl2]:
+        assert S2.wait(t)[0] == 0
+    assert S2.stats().completed == 4
+    S2.stop()
+
+
+def test_srpt_never_starves_the_oldest_job(fake):
+    S = FakeServer(fake, max_active=8, chunk=10, rate=1e7, policy=0, sat=1000)
+    _, tl, _ = S.submit(1000, 300)
+    # a stream of short jobs that would always win on remaining work
+    for _ in range(10):
+        S.submit(1000, 20)
+    time.sleep(0.05)
+    assert S.poll(tl).turns_done > 0         # the oldest job advanced meanwhile
+    assert S.wait(tl)[1].state == phtl.DONE
+    S.stop()
