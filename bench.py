@@ -256,6 +256,8 @@ def run_ours(args, wl_name, wl):
 
     ring = synth.ring(wl["voltage"], transverse=True)
     R = phtl.Ring(**ring)
+    if wl.get("block") or wl.get("tpl"):
+        R.set_tuning(block_threads=wl.get("block", 0), turns_per_launch=wl.get("tpl", 0))
     der = R.derived()
     host = make_inputs(wl, der, seed=1 + rank)
     n, turns, dt = wl["n"], wl["turns"], wl["dtype"]
@@ -734,6 +736,8 @@ def main(argv=None):
     ap.add_argument("--no-transverse", action="store_true")
     ap.add_argument("--perturn", action="store_true", help="one launch per turn (HBM-bound variant)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block", type=int, help="threads per block (default: the library's)")
+    ap.add_argument("--turns-per-launch", type=int, help="turns per launch (default: automatic)")
     args = ap.parse_args(argv)
     wl = dict(WORKLOADS[args.workload])
     kind = wl.get("kind", "single")
@@ -746,6 +750,8 @@ def main(argv=None):
         if args.no_transverse:
             wl["transverse"] = False
         wl["perturn"] = args.perturn
+        wl["block"] = args.block or 0
+        wl["tpl"] = args.turns_per_launch or 0
     if args.impl == "reference":
         if kind != "single":
             print(json.dumps({"impl": "reference", "unavailable":

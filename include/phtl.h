@@ -405,6 +405,14 @@ int phtl_moments_from_sums(const double* row, double* out15);
  * Errors: PHTL_E_INVALID, PHTL_E_NODEVICE, PHTL_E_CUDA.                           */
 int phtl_eval_sin(const double* x, double* y, int64_t n, int which, void* cuda_stream);
 
+/* Diagnostic: y[i] = sin(k * z[i]) for n device doubles, stream-ordered, through the
+ * form the FP64 kick takes for phi_s = 0 (Sec. 1.1.2's kick with a stationary bucket):
+ * the product k z is folded into the sine's argument reduction, so it is never rounded
+ * on its own.  |k z| beyond ~6000, Inf and NaN use which = 0 of phtl_eval_sin on the
+ * rounded product.  Errors: PHTL_E_INVALID (n < 0, null pointer with n > 0, k not
+ * finite), PHTL_E_NODEVICE, PHTL_E_CUDA.                                           */
+int phtl_eval_sin_kz(double k, const double* z, double* y, int64_t n, void* cuda_stream);
+
 /* Library version string, e.g. "phtl 0.1 sm_103a".                                 */
 const char* phtl_version(void);
 

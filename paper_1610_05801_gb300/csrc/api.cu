@@ -88,11 +88,12 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
         std::memset(&c, 0, sizeof(c));
         scheme_consts(d, s, c);
         c.k = d.k;
+        c.k2opi = static_cast<float>(d.k * (2.0 / kPi));
         c.phis = p.phi_s_rad;
         c.sinphis = d.sin_phis;
         c.lin = d.cos_phis * d.k;
         c.linear = p.rf_linear != 0;
-        c.phis_zero = d.sin_phis == 0.0 ? 1 : 0;
+        c.phis_zero = p.phi_s_rad == 0.0 ? 1 : 0;
         for (int i = 0; i < 4; ++i) {
             c.mx[i] = d.mx[i];
             c.my[i] = d.my[i];

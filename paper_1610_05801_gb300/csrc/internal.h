@@ -30,14 +30,14 @@ struct MapConsts {
     // p = beta tan(mu/2), q = -sin(mu)/beta (shear_* = 0: use the matrix instead)
     double shx[2], shy[2];
     int32_t shear_x, shear_y;
-    int32_t phis_zero;  // sin(phi_s) == 0: the kick skips the subtraction
+    int32_t phis_zero;  // phi_s == 0: the kick is sin(k z), with k z fused into the sine's reduction
     // double-float (FP32 pair) copies for the FP32 paths: value = hi + lo
     float dc_hi[4], dc_lo[4];
     float kw_hi[3], kw_lo[3];
     float k_hi, k_lo, phis_hi, phis_lo, sinphis_hi, sinphis_lo, lin_hi, lin_lo;
     float mx_hi[4], mx_lo[4], my_hi[4], my_lo[4];
     int32_t linear;  // rf_linear flag
-    int32_t pad_;
+    float k2opi;     // k * 2/pi rounded to FP32 (quadrant estimate of the fused FP64 sine)
 };
 
 // Where and when a launch records monitor rows.

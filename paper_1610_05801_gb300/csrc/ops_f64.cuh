@@ -21,14 +21,33 @@ namespace f64 {
 constexpr int P = PHTL_F64_PARTICLES_PER_THREAD;
 static_assert(P % 2 == 0, "P must be even (128-bit loads of two doubles)");
 
-// ZS: sin(phi_s) == 0 (stationary bucket), so the subtraction is left out at compile time
-// (the kernels choose the instantiation once, outside the turn loop).
+// Minimum resident 256-thread blocks per SM asked of the compiler (caps registers at
+// 65536 / (256 * this)): the FP64 kernels hide the FP64 pipe's latency with warps.
+// Euler-Cromer and leap-frog run faster with 3 (80 registers, 24 warps per SM); Ruth4,
+// with three kicks per turn in flight, with 2 (measured on GB300).
+#ifndef PHTL_F64_MIN_BLOCKS_256
+#define PHTL_F64_MIN_BLOCKS_256 3
+#endif
+#ifndef PHTL_F64_MIN_BLOCKS_256_RUTH4
+#define PHTL_F64_MIN_BLOCKS_256_RUTH4 2
+#endif
+// The batched kernel holds all three schemes; at 3 it would spill.
+constexpr int kBatchedMinBlocks256 = 2;
+template <int SCHEME>
+constexpr int min_blocks_256()
+{
+    return SCHEME == PHTL_RUTH4 ? PHTL_F64_MIN_BLOCKS_256_RUTH4 : PHTL_F64_MIN_BLOCKS_256;
+}
+
+// ZS: phi_s == 0 (stationary bucket): the force is sin(k z), with the phase product fused
+// into the sine's reduction and no subtraction (the kernels choose the instantiation
+// once, outside the turn loop).
 template <bool ZS>
 __device__ __forceinline__ double rf_force(const MapConsts& c, double z)
 {
     if (c.linear) return c.lin * z;
-    const double s = sin_f64(fma(c.k, z, c.phis));
-    return ZS ? s : s - c.sinphis;
+    if (ZS) return sin_kz(c.k, c.k2opi, z);
+    return sin_f64(fma(c.k, z, c.phis)) - c.sinphis;
 }
 
 __device__ __forceinline__ void drift(double (&z)[P], const double (&d)[P], double dc)

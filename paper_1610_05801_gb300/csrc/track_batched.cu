@@ -72,7 +72,7 @@ __device__ __forceinline__ void run_f64(double (&z)[f64::P], double (&d)[f64::P]
 }
 
 template <bool MON>
-__global__ void __launch_bounds__(256) k_batched_f64(const JobDesc* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(256, f64::kBatchedMinBlocks256) k_batched_f64(const JobDesc* __restrict__ jobs, int njobs,
                                                      MapConsts c, int64_t t0, int T)
 {
     using namespace f64;

@@ -6,11 +6,15 @@
 // and store per coordinate per launch), runs `nturns` turns of the chosen scheme
 // (Sec. 1.1.2) and the transverse matrix push (Sec. 1.1.1) on them, and adds the
 // per-turn moment sums into the monitor rows.  Blocks walk over particle chunks in a
-// grid-stride loop so the grid can be sized to the resident capacity of the GPU.
+// grid-stride loop so the grid can be sized to the resident capacity of the GPU.  (Equal
+// per-block shares were measured slower: the ragged warp at the end of every share costs
+// more than the lone extra chunk some blocks run in the last round.)
 //
 // On GB300 the FP64 pipe retires 2 DFMA per clock per SM (1/64 of FP32), so this
 // kernel is FP64-pipe bound: every FP64 operation per particle-turn counts.
 #include <cuda_runtime.h>
+
+#include <cmath>
 
 #include "internal.h"
 #include "ops_f64.cuh"
@@ -24,8 +28,8 @@ using namespace f64;
 template <int SCHEME, bool TRANS, bool MON, bool ZS>
 __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x)[P],
                                       double (&xp)[P], double (&y)[P], double (&yp)[P], bool hx,
-                                      bool hy, float cnt, const MapConsts& c, const MonitorArgs& m,
-                                      int nturns, double* smem, int& parity)
+                                      bool hy, float cnt, const MapConsts& c,
+                                      const MonitorArgs& m, int nturns, double* smem, int& parity)
 {
     int64_t until = m.until, row = m.row;
     for (int t = 0; t < nturns; ++t) {
@@ -46,7 +50,7 @@ __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x
 }
 
 template <int SCHEME, bool TRANS, bool MON>
-__global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
+__global__ void __launch_bounds__(256, min_blocks_256<SCHEME>()) k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
     extern __shared__ double smem[];
     double* gz = static_cast<double*>(L.c[0]);
@@ -85,9 +89,11 @@ __global__ void __launch_bounds__(256) k_track_f64(LaunchDesc L, MapConsts c, Mo
             parity ^= 1;
         }
         if (c.phis_zero)
-            turns<SCHEME, TRANS, MON, true>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns, smem, parity);
+            turns<SCHEME, TRANS, MON, true>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
+                                            smem, parity);
         else
-            turns<SCHEME, TRANS, MON, false>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns, smem, parity);
+            turns<SCHEME, TRANS, MON, false>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
+                                             smem, parity);
         store2(gz, base, L.n, vec, z);
         store2(gd, base, L.n, vec, d);
         if (hx) {
@@ -158,6 +164,20 @@ __global__ void k_eval_sin(const double* __restrict__ x, double* __restrict__ y,
         y[i] = which == 0 ? sin_f64(x[i]) : sin(x[i]);
 }
 
+__global__ void k_eval_sin_kz(double k, float k2opi, const double* __restrict__ z,
+                              double* __restrict__ y, int64_t n)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        y[i] = sin_kz(k, k2opi, z[i]);
+}
+
+int eval_grid(int64_t n, int block)
+{
+    const int64_t want = (n + block - 1) / block;
+    return static_cast<int>(want < 152 * 16 ? want : 152 * 16);
+}
+
 }  // namespace
 
 }  // namespace phtl
@@ -173,9 +193,26 @@ extern "C" int phtl_eval_sin(const double* x, double* y, int64_t n, int which, v
     }
     if (n == 0) return PHTL_OK;
     const int block = 256;
-    const int64_t want = (n + block - 1) / block;
-    const int grid = static_cast<int>(want < 152 * 16 ? want : 152 * 16);
-    phtl::k_eval_sin<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n, which);
+    phtl::k_eval_sin<<<phtl::eval_grid(n, block), block, 0, static_cast<cudaStream_t>(stream)>>>(
+        x, y, n, which);
+    if (cudaGetLastError() != cudaSuccess) return PHTL_E_CUDA;
+    return PHTL_OK;
+}
+
+extern "C" int phtl_eval_sin_kz(double k, const double* z, double* y, int64_t n, void* stream)
+{
+    if (n < 0 || !std::isfinite(k)) return PHTL_E_INVALID;
+    if (n > 0 && (!z || !y)) return PHTL_E_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PHTL_E_NODEVICE;
+    }
+    if (n == 0) return PHTL_OK;
+    const int block = 256;
+    const float k2opi = static_cast<float>(k * (2.0 / 3.14159265358979323846));
+    phtl::k_eval_sin_kz<<<phtl::eval_grid(n, block), block, 0, static_cast<cudaStream_t>(stream)>>>(
+        k, k2opi, z, y, n);
     if (cudaGetLastError() != cudaSuccess) return PHTL_E_CUDA;
     return PHTL_OK;
 }

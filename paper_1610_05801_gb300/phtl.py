@@ -127,6 +127,7 @@ SIGNATURES = {
     "phtl_moments_from_sums": (_int, [_vp, _vp]),
     "phtl_get_stats": (_int, [_vp, C.POINTER(Stats)]),
     "phtl_eval_sin": (_int, [_vp, _vp, _i64, _int, _vp]),
+    "phtl_eval_sin_kz": (_int, [C.c_double, _vp, _vp, _i64, _vp]),
     "phtl_autotune": (_int, [_vp, _int, _int, _i64, C.c_double, C.POINTER(Tuning)]),
     "phtl_batch_create": (_int, [_vp, C.POINTER(Job), C.c_int32, C.c_int32, C.POINTER(_vp)]),
     "phtl_batch_run": (_int, [_vp, _vp]),
@@ -363,6 +364,17 @@ def eval_sin(x, which: int = 0, stream=None):
     y = torch.empty_like(x)
     _check(load().phtl_eval_sin(x.data_ptr(), y.data_ptr(), x.numel(), int(which),
                                 _stream_ptr(stream)), "phtl_eval_sin")
+    return y
+
+
+def eval_sin_kz(k: float, z, stream=None):
+    """sin(k z) of a CUDA float64 tensor through the phi_s = 0 kick's fused form."""
+    import torch
+
+    _check_tensor(z, "float64", "z")
+    y = torch.empty_like(z)
+    _check(load().phtl_eval_sin_kz(float(k), z.data_ptr(), y.data_ptr(), z.numel(),
+                                   _stream_ptr(stream)), "phtl_eval_sin_kz")
     return y
 
 

@@ -240,3 +240,48 @@ def test_f64_transverse_special_tunes():
         err = helpers.rel_errors(d, ref, got, inp["z"], inp["dp"])
         assert np.max(err) < 1e-10, (scheme, np.max(err))
         assert np.allclose(got[4], inp["y"], rtol=0, atol=0) and np.allclose(got[5], inp["yp"], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("case", ["accelerating_phi_s_0.3", "below_transition_phi_s_pi"])
+def test_f64_nonzero_phi_s(scheme, case):
+    """phi_s != 0 takes the kick's general form (phase product, sine, minus sin phi_s)
+    rather than the fused sin(k z) of the phi_s = 0 bucket."""
+    from paper_1610_05801_gb300 import synth
+    over = dict(phi_s_rad=0.3) if case.startswith("acc") else dict(p0_eVc=10e9, phi_s_rad=math.pi)
+    ring = synth.ring(4.5e6, transverse=True, **over)
+    d = oracle.load().derive(ring)
+    n, turns = 2001, 3000
+    s = synth.Stream(31)
+    zb = math.pi / d.k
+    db = 2 * math.sqrt(d.A / (d.k * abs(d.etaC)))
+    # a box of +-10 % of the bucket around the fixed point z = dp = 0: inside the bucket
+    z = (2 * s.uniform(n) - 1) * 0.1 * zb
+    dp = (2 * s.uniform(n) - 1) * 0.1 * db
+    x, xp = synth.transverse_gaussian(32, n, 50.0, 2e-6, d.betagamma)
+    y, yp = synth.transverse_gaussian(33, n, 50.0, 2e-6, d.betagamma)
+    inp = dict(ring=ring, d=d, z=z, dp=dp, x=x, xp=xp, y=y, yp=yp)
+    got, mg = run_gpu(inp, scheme, turns, stride=50)
+    ref, mr = run_ref(inp, scheme, turns, stride=50)
+    assert np.max(np.abs(got[0] - ref[0])) < 1e-11 * zb
+    assert np.max(np.abs(got[1] - ref[1])) < 1e-11 * db
+    # the motion stayed bounded near the fixed point (a real bucket, not a drift away)
+    assert np.max(np.abs(ref[0])) < 0.5 * zb
+    assert moment_errors(d, mg, mr) < 1e-9
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32cd"])
+def test_grids_and_blocks_are_invisible(dtype):
+    """Capped grids, odd block sizes and turns-per-launch give the same particles bitwise
+    and the same moments up to the order of the FP64 block sums (the per-thread and
+    per-warp partials group the same particles whatever the grid)."""
+    inp = helpers.inputs(4099, seed=17)
+    a, ma = run_gpu(inp, "leapfrog", 300, dtype=dtype, stride=3,
+                    tuning=dict(block_threads=256, max_blocks=5))
+    b, mb = run_gpu(inp, "leapfrog", 300, dtype=dtype, stride=3,
+                    tuning=dict(block_threads=96, max_blocks=13, turns_per_launch=41))
+    c, mc = run_gpu(inp, "leapfrog", 300, dtype=dtype, stride=3)
+    for u, v, w in zip(a, b, c):
+        assert np.array_equal(u, v) and np.array_equal(u, w)
+    for m in (mb, mc):
+        assert moment_errors(inp["d"], m, ma) < 1e-11

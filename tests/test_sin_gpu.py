@@ -50,3 +50,47 @@ def test_own_sine_vs_mpmath():
         exact = np.array([float(mp.sin(mp.mpf(v))) for v in x])
     ulp = np.spacing(np.abs(exact))
     assert np.max(np.abs(own - exact) / ulp) <= 4
+
+
+def _sin_kz_reference(k, z):
+    """sin(k z) of the exact product k z: Dekker's two-product (Veltkamp split, exact in
+    FP64 without FMA) gives k z = p + e, then sin(p + e) ~ sin p + e cos p."""
+    def split(a):
+        c = 134217729.0 * a
+        hi = c - (c - a)
+        return hi, a - hi
+    p = k * z
+    kh, kl = split(np.full_like(z, k))
+    zh, zl = split(z)
+    e = ((kh * zh - p) + kh * zl + kl * zh) + kl * zl
+    return np.sin(p) + e * np.cos(p), p
+
+
+def test_fused_sin_kz_of_the_phi_s_zero_kick():
+    """sin(k z) with the product folded into the reduction (the phi_s = 0 kick): within a
+    few ulp of the sine of the exact product, across the bucket, far outside it, through
+    the fallback range, and NaN for non-finite z."""
+    k = 2 * math.pi * 4620 / 6911.5038
+    rng = np.random.default_rng(5)
+    zb = math.pi / k
+    parts = [np.linspace(-3 * zb, 3 * zb, 300001), rng.uniform(-1, 1, 100000) * 1400.0,
+             rng.uniform(-1e-6, 1e-6, 20000),
+             np.array([0.0, -0.0, 1e-300, -1e-300, zb, -zb, zb / 2, 5e-324])]
+    z = np.concatenate(parts)
+    t = torch.tensor(z, dtype=torch.float64, device="cuda:0")
+    own = phtl.eval_sin_kz(k, t).cpu().numpy()
+    ref, p = _sin_kz_reference(k, z)
+    assert np.max(np.abs(own - ref)) <= 4 * 2.0 ** -53, np.max(np.abs(own - ref))
+    big = np.abs(ref) > 1e-3
+    assert np.max(np.abs(own[big] / ref[big] - 1)) < 4e-15
+    tiny = (np.abs(p) < 1e-3) & (np.abs(p) > 1e-290)
+    assert np.max(np.abs(own[tiny] / ref[tiny] - 1)) < 3e-16
+    # far outside any bucket (|k z| beyond the fused range) the kick uses the plain sine
+    # of the rounded product: bitwise what phtl_eval_sin gives for k * z
+    far = np.array([7e3, -1e4, 5e4, -1e5, 3e7, 1e300]) / k
+    own_far = phtl.eval_sin_kz(k, torch.tensor(far, dtype=torch.float64, device="cuda:0")).cpu().numpy()
+    ref_far = phtl.eval_sin(torch.tensor(k * far, dtype=torch.float64, device="cuda:0"), 0).cpu().numpy()
+    assert np.array_equal(own_far, ref_far)
+    bad = phtl.eval_sin_kz(k, torch.tensor([np.inf, -np.inf, np.nan], dtype=torch.float64,
+                                           device="cuda:0")).cpu().numpy()
+    assert np.all(np.isnan(bad))
