@@ -401,7 +401,9 @@ int phtl_moments_from_sums(const double* row, double* out15);
 
 /* Diagnostic: y[i] = sine of x[i] on the device, for n device doubles, stream-ordered.
  * which = 0: the library's own FP64 sine used by the FP64 kick (Cody-Waite reduction
- * plus a fitted polynomial); which = 1: CUDA's sin(), for comparison.
+ * plus a fitted polynomial); which = 1: CUDA's sin(), for comparison; which = 2: the
+ * double-float sine of the PHTL_F32C / PHTL_F32CD kicks, applied to x[i] truncated to
+ * a float pair (48 bits) and returned as hi + lo.
  * Errors: PHTL_E_INVALID, PHTL_E_NODEVICE, PHTL_E_CUDA.                           */
 int phtl_eval_sin(const double* x, double* y, int64_t n, int which, void* cuda_stream);
 

@@ -94,14 +94,16 @@ __device__ __forceinline__ double widen_bits(float f) { return widen_float_bits(
 
 // Phase argument phi = phi_s + k z as a double-float pair.  PHTL_F32C forms it in FP64 from
 // hi + comp (exact in double) with one DFMA; PHTL_F32CD in double-float arithmetic.
-template <int DT>
+// ZS: phi_s == 0, so the phase is k z alone (chosen once, outside the turn loop).
+template <int DT, bool ZS>
 __device__ __forceinline__ DF2 phase_df(const MapConsts& c, const DF& z)
 {
     if (DT == PHTL_F32C) {
         const double zd = widen_bits(z.hi) + widen_bits(z.c);
-        return split_bits(fma(c.k, zd, c.phis));
+        return split_bits(ZS ? c.k * zd : fma(c.k, zd, c.phis));
     }
-    return df_add(df_mul(DF2{c.k_hi, c.k_lo}, as2(z)), DF2{c.phis_hi, c.phis_lo});
+    const DF2 kz = df_mul(DF2{c.k_hi, c.k_lo}, as2(z));
+    return ZS ? kz : df_add(kz, DF2{c.phis_hi, c.phis_lo});
 }
 
 // Double-float split of an FP64 constant at compile time.
@@ -119,7 +121,9 @@ struct DFC {
 // quadrant parity, sin r = r + r^3 S(r^2), cos r = 1 - r^2/2 + r^4 C(r^2), with the
 // coefficients of the FP64 sine (sin_f64.cuh): the two leading Horner steps in
 // double-float, the four trailing terms (|t^2 S_2| <= 8e-5, |t^2 C_2| <= 1e-5) in FP32.
-// |x| >= 1e4 falls back to the FP64 sine.
+// Every double-float addition after the reduction adds a smaller term to a larger one
+// (Horner constant vs product, r vs r^3 S, 1 - t/2 vs r^4 C), so it uses Fast2Sum on the
+// heads.  |x| >= 1e4 falls back to the FP64 sine.
 __device__ __forceinline__ DF2 sin_df(DF2 x)
 {
     if (!(fabsf(x.h) < 1.0e4f)) return split_bits(sin_f64(widen_bits(x.h) + widen_bits(x.l)));
@@ -144,21 +148,22 @@ __device__ __forceinline__ DF2 sin_df(DF2 x)
     // leading Horner steps in double-float
     constexpr DFC s1(0.008333333333330948), s0(-0.16666666666666666);
     constexpr DFC c1(-0.0013888888888887398), c0(0.041666666666666664);
-    DF2 u = df_add(df_mul(t, DF2{tail, 0.0f}), odd ? DF2{c1.h, c1.l} : DF2{s1.h, s1.l});
-    u = df_add(df_mul(t, u), odd ? DF2{c0.h, c0.l} : DF2{s0.h, s0.l});
+    DF2 u = df_add_dominant(odd ? DF2{c1.h, c1.l} : DF2{s1.h, s1.l}, df_mul_f(t, tail));
+    u = df_add_dominant(odd ? DF2{c0.h, c0.l} : DF2{s0.h, s0.l}, df_mul(t, u));
     const DF2 m = df_mul(odd ? t : r, t);                                  // r^3 or r^4
-    const DF2 a = odd ? df_add(DF2{1.0f, 0.0f}, DF2{-0.5f * t.h, -0.5f * t.l}) : r;
-    const DF2 res = df_add(a, df_mul(m, u));
-    return (qi & 2) ? neg2(res) : res;
+    const DF2 a = odd ? df_add_dominant(DF2{1.0f, 0.0f}, DF2{-0.5f * t.h, -0.5f * t.l}) : r;
+    const DF2 res = df_add_dominant(a, df_mul(m, u));
+    return df_xor_sign(res, static_cast<unsigned>(qi & 2) << 30);      // quadrants 2, 3: -res
 }
 
 // ---------------------------------------------------------------------------------------
 // Arithmetic of PHTL_F32CS: FP32 increments and the SFU sine (fast, less accurate).
 
 // Phase argument rounded to FP32 (double-float formation, then rounded).
+template <bool ZS>
 __device__ __forceinline__ float phase_f(const MapConsts& c, const DF& z)
 {
-    const DF2 ph = df_add(df_mul(DF2{c.k_hi, c.k_lo}, as2(z)), DF2{c.phis_hi, c.phis_lo});
+    const DF2 ph = phase_df<PHTL_F32CD, ZS>(c, z);
     return __fadd_rn(ph.h, ph.l);
 }
 
@@ -169,21 +174,31 @@ __device__ __forceinline__ float sin_sfu(float x)
 }
 
 // ---------------------------------------------------------------------------------------
-// kick: delta += kw * (sin(phi) - sin(phi_s)), kw = kh + kl (the FP64 weight as a pair)
-template <int DT>
+// kick: delta += kw * (sin(phi) - sin(phi_s)), kw = kh + kl (the FP64 weight as a pair);
+// ZS: phi_s == 0, no subtraction
+template <int DT, bool ZS>
 __device__ __forceinline__ void kick(const DF (&z)[P], DF (&d)[P], float kh, float kl,
                                      const MapConsts& c)
 {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         if (DT == PHTL_F32CS) {
-            const float f = c.linear ? c.lin_hi * (z[p].hi + z[p].c)
-                                     : sin_sfu(phase_f(c, z[p])) - c.sinphis_hi;
+            float f;
+            if (c.linear) {
+                f = c.lin_hi * (z[p].hi + z[p].c);
+            } else {
+                f = sin_sfu(phase_f<ZS>(c, z[p]));
+                if (!ZS) f -= c.sinphis_hi;
+            }
             acc(d[p], __fmaf_rn(kh, f, __fmul_rn(kl, f)));
         } else {
-            const DF2 f = c.linear ? df_mul(DF2{c.lin_hi, c.lin_lo}, as2(z[p]))
-                                   : df_add(sin_df(phase_df<DT>(c, z[p])),
-                                            DF2{-c.sinphis_hi, -c.sinphis_lo});
+            DF2 f;
+            if (c.linear) {
+                f = df_mul(DF2{c.lin_hi, c.lin_lo}, as2(z[p]));
+            } else {
+                f = sin_df(phase_df<DT, ZS>(c, z[p]));
+                if (!ZS) f = df_add(f, DF2{-c.sinphis_hi, -c.sinphis_lo});
+            }
             acc2(d[p], df_mul(DF2{kh, kl}, f));
         }
     }
@@ -207,25 +222,25 @@ __device__ __forceinline__ void drift(DF (&z)[P], const DF (&d)[P], float dh, fl
 // dh, dl, kh, kl: the drift and kick weights of this bunch's scheme split into FP32
 // hi + lo (the single-bunch kernel passes the MapConsts copies, the batched kernel the
 // job table's).
-template <int SCHEME, int DT>
+template <int SCHEME, int DT, bool ZS>
 __device__ __forceinline__ void long_turn(DF (&z)[P], DF (&d)[P], const MapConsts& c,
                                           const float* dh, const float* dl, const float* kh,
                                           const float* kl)
 {
     if (SCHEME == PHTL_EULER_CROMER) {
-        kick<DT>(z, d, kh[0], kl[0], c);
+        kick<DT, ZS>(z, d, kh[0], kl[0], c);
         drift<DT>(z, d, dh[0], dl[0]);
     } else if (SCHEME == PHTL_LEAPFROG) {
         drift<DT>(z, d, dh[0], dl[0]);
-        kick<DT>(z, d, kh[0], kl[0], c);
+        kick<DT, ZS>(z, d, kh[0], kl[0], c);
         drift<DT>(z, d, dh[1], dl[1]);
     } else {
         drift<DT>(z, d, dh[0], dl[0]);
-        kick<DT>(z, d, kh[0], kl[0], c);
+        kick<DT, ZS>(z, d, kh[0], kl[0], c);
         drift<DT>(z, d, dh[1], dl[1]);
-        kick<DT>(z, d, kh[1], kl[1], c);
+        kick<DT, ZS>(z, d, kh[1], kl[1], c);
         drift<DT>(z, d, dh[2], dl[2]);
-        kick<DT>(z, d, kh[2], kl[2], c);
+        kick<DT, ZS>(z, d, kh[2], kl[2], c);
         drift<DT>(z, d, dh[3], dl[3]);
     }
 }

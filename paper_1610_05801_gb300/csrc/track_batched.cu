@@ -141,19 +141,20 @@ __global__ void __launch_bounds__(256, f64::kBatchedMinBlocks256) k_batched_f64(
 }
 
 // ---------------------------------------------------------------------------------- FP32C
-template <int SCHEME, int DT, bool MON>
-__device__ __forceinline__ void run_f32c(f32c::DF (&z)[f32c::P], f32c::DF (&d)[f32c::P],
-                                         f32c::DF (&x)[f32c::P], f32c::DF (&xp)[f32c::P],
-                                         f32c::DF (&y)[f32c::P], f32c::DF (&yp)[f32c::P], bool hx,
-                                         bool hy, const MapConsts& c, const JobDesc& J, float cnt,
-                                         int64_t t0, int nt, double* smem, int& parity)
+template <int SCHEME, int DT, bool MON, bool ZS>
+__device__ __forceinline__ void run_f32c_zs(f32c::DF (&z)[f32c::P], f32c::DF (&d)[f32c::P],
+                                            f32c::DF (&x)[f32c::P], f32c::DF (&xp)[f32c::P],
+                                            f32c::DF (&y)[f32c::P], f32c::DF (&yp)[f32c::P],
+                                            bool hx, bool hy, const MapConsts& c,
+                                            const JobDesc& J, float cnt, int64_t t0, int nt,
+                                            double* smem, int& parity)
 {
     using namespace f32c;
     const int64_t g0 = t0 + J.turn_offset;  // turns done before this launch
     int64_t until = J.stride - (g0 % J.stride);
     int64_t row = g0 / J.stride + 1;
     for (int t = 0; t < nt; ++t) {
-        long_turn<SCHEME, DT>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo);
+        long_turn<SCHEME, DT, ZS>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo);
         if (hx) {
 #pragma unroll
             for (int p = 0; p < P; ++p) df_rotate(x[p], xp[p], c.mx_hi, c.mx_lo);
@@ -171,6 +172,20 @@ __device__ __forceinline__ void run_f32c(f32c::DF (&z)[f32c::P], f32c::DF (&d)[f
             }
         }
     }
+}
+
+// phi_s == 0 chosen once, outside the turn loop
+template <int SCHEME, int DT, bool MON>
+__device__ __forceinline__ void run_f32c(f32c::DF (&z)[f32c::P], f32c::DF (&d)[f32c::P],
+                                         f32c::DF (&x)[f32c::P], f32c::DF (&xp)[f32c::P],
+                                         f32c::DF (&y)[f32c::P], f32c::DF (&yp)[f32c::P], bool hx,
+                                         bool hy, const MapConsts& c, const JobDesc& J, float cnt,
+                                         int64_t t0, int nt, double* smem, int& parity)
+{
+    if (c.phis_zero)
+        run_f32c_zs<SCHEME, DT, MON, true>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
+    else
+        run_f32c_zs<SCHEME, DT, MON, false>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
 }
 
 template <int DT, bool MON>

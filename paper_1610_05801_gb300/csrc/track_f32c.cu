@@ -3,13 +3,13 @@
 //
 // Same structure as the FP64 kernel (Sec. 2.3: turn loop inside the kernel, state in
 // registers), but every coordinate is an unevaluated sum hi + comp of two floats:
-//   - each drift/kick increment is one FP32 product with the FP64 weight split into
-//     hi + lo floats, added with Knuth's TwoSum (the rounding error goes into comp) and
-//     renormalised with Fast2Sum;
-//   - the RF phase argument k z is formed from hi + comp either in FP64 (PHTL_F32C) or
-//     in double-float FP32-pair arithmetic (PHTL_F32CD, PHTL_F32CS) and rounded to FP32;
-//     the sine is the library's FP32 polynomial (PHTL_F32C, PHTL_F32CD) or the SFU's
-//     __sinf (PHTL_F32CS);
+//   - PHTL_F32C / PHTL_F32CD: each drift/kick increment is a double-float product of the
+//     FP64 weight (split into hi + lo) and the pair, added with Knuth's TwoSum and
+//     renormalised with Fast2Sum; the RF phase argument is formed from hi + comp in FP64
+//     (PHTL_F32C) or in double-float arithmetic (PHTL_F32CD), and the sine is the
+//     double-float polynomial sin_df (~1e-12 absolute);
+//   - PHTL_F32CS: FP32 increments with split weights, the phase rounded to FP32 and the
+//     SFU's __sinf;
 //   - the transverse matrix (Sec. 1.1.1) is applied in double-float arithmetic (exact
 //     FP32 products by fmaf, TwoSum of the two terms), so the rotation keeps ~48 bits;
 //   - per-turn moment sums are FP32 per thread and across the warp (<= 128 particles),
@@ -26,6 +26,37 @@ namespace phtl {
 namespace {
 
 using namespace f32c;
+
+// The turn loop of one particle chunk (state in registers throughout); ZS: phi_s == 0.
+template <int SCHEME, int DT, bool TRANS, bool MON, bool ZS>
+__device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&xp)[P],
+                                      DF (&y)[P], DF (&yp)[P], bool hx, bool hy, float cnt,
+                                      const MapConsts& c, const MonitorArgs& m, int nturns,
+                                      double* smem, int& parity)
+{
+    int64_t until = m.until, row = m.row;
+    for (int t = 0; t < nturns; ++t) {
+        long_turn<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo);
+        if (TRANS) {
+            if (hx) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) df_rotate(x[p], xp[p], c.mx_hi, c.mx_lo);
+            }
+            if (hy) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) df_rotate(y[p], yp[p], c.my_hi, c.my_lo);
+            }
+        }
+        if (MON) {
+            if (--until == 0) {
+                record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
+                parity ^= 1;
+                ++row;
+                until = m.stride;
+            }
+        }
+    }
+}
 
 template <int SCHEME, int DT, bool TRANS, bool MON>
 __global__ void __launch_bounds__(256) k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
@@ -59,32 +90,16 @@ __global__ void __launch_bounds__(256) k_track_f32c(LaunchDesc L, MapConsts c, M
         const int64_t left = L.n - base;
         const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
 
-        int64_t until = m.until, row = m.row;
         if (MON && m.initial) {
             record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, 0);
             parity ^= 1;
         }
-        for (int t = 0; t < L.nturns; ++t) {
-            long_turn<SCHEME, DT>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo);
-            if (TRANS) {
-                if (hx) {
-#pragma unroll
-                    for (int p = 0; p < P; ++p) df_rotate(x[p], xp[p], c.mx_hi, c.mx_lo);
-                }
-                if (hy) {
-#pragma unroll
-                    for (int p = 0; p < P; ++p) df_rotate(y[p], yp[p], c.my_hi, c.my_lo);
-                }
-            }
-            if (MON) {
-                if (--until == 0) {
-                    record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
-                    parity ^= 1;
-                    ++row;
-                    until = m.stride;
-                }
-            }
-        }
+        if (c.phis_zero)
+            turns<SCHEME, DT, TRANS, MON, true>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
+                                                smem, parity);
+        else
+            turns<SCHEME, DT, TRANS, MON, false>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
+                                                 smem, parity);
         store4(g[0], base, L.n, vec, z);
         store4(g[1], base, L.n, vec, d);
         if (hx) {

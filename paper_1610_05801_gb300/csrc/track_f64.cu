@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "ops_f32c.cuh"
 #include "ops_f64.cuh"
 
 namespace phtl {
@@ -161,7 +162,14 @@ __global__ void k_eval_sin(const double* __restrict__ x, double* __restrict__ y,
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        y[i] = which == 0 ? sin_f64(x[i]) : sin(x[i]);
+    {
+        if (which == 2) {
+            const DF2 r = f32c::sin_df(split_bits(x[i]));
+            y[i] = static_cast<double>(r.h) + static_cast<double>(r.l);
+        } else {
+            y[i] = which == 0 ? sin_f64(x[i]) : sin(x[i]);
+        }
+    }
 }
 
 __global__ void k_eval_sin_kz(double k, float k2opi, const double* __restrict__ z,
@@ -184,7 +192,7 @@ int eval_grid(int64_t n, int block)
 
 extern "C" int phtl_eval_sin(const double* x, double* y, int64_t n, int which, void* stream)
 {
-    if (n < 0 || (which != 0 && which != 1)) return PHTL_E_INVALID;
+    if (n < 0 || which < 0 || which > 2) return PHTL_E_INVALID;
     if (n > 0 && (!x || !y)) return PHTL_E_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {

@@ -94,3 +94,35 @@ def test_fused_sin_kz_of_the_phi_s_zero_kick():
     bad = phtl.eval_sin_kz(k, torch.tensor([np.inf, -np.inf, np.nan], dtype=torch.float64,
                                            device="cuda:0")).cpu().numpy()
     assert np.all(np.isnan(bad))
+
+
+def _float_pair_value(x):
+    """The value of the float pair the double-float sine receives: x with its significand
+    cut to 24 bits for the head and the next 24 significant bits for the tail (both
+    truncated, as the device's integer split does)."""
+    b = x.view(np.uint64)
+    m29 = b & np.uint64(0x1FFFFFFF)
+    msb = np.zeros(len(x), dtype=np.int64)
+    nz = m29 != 0
+    msb[nz] = np.floor(np.log2(m29[nz].astype(np.float64))).astype(np.int64)
+    drop = np.maximum(msb - 23, 0).astype(np.uint64)
+    kept = (m29 >> drop) << drop
+    return ((b & ~np.uint64(0x1FFFFFFF)) | kept).view(np.float64)
+
+
+def test_double_float_sine_of_the_f32c_kicks():
+    """The double-float sine (FP32C / FP32CD kicks) against the FP64 sine of the exact pair
+    value.  Bounds from its arithmetic: <= 4e-12 absolute on the bucket's phase range
+    (|x| <= 2 pi: the trailing Horner terms are summed in FP32 and contribute up to
+    |r^3 t tail| <= 6e-5, so 6e-5 * 2^-24 ~ 4e-12; the double-float steps ~1e-14),
+    <= 1e-10 for |x| <= 1e3 (the FP32 reduction remainder grows with the quadrant q)."""
+    rng = np.random.default_rng(7)
+    near = np.concatenate([np.linspace(-2 * math.pi, 2 * math.pi, 200001),
+                           rng.uniform(-1e-4, 1e-4, 20000), np.array([0.0, math.pi / 4, 1e-30])])
+    far = rng.uniform(-1e3, 1e3, 100000)
+    for x, bound in ((near, 4e-12), (far, 1e-10)):
+        got = phtl.eval_sin(torch.tensor(x, dtype=torch.float64, device="cuda:0"), 2).cpu().numpy()
+        ref = np.sin(_float_pair_value(x))
+        err = np.max(np.abs(got - ref))
+        assert err <= bound, (err, bound)
+    assert phtl.eval_sin(torch.tensor([0.0], dtype=torch.float64, device="cuda:0"), 2).item() == 0.0
