@@ -40,13 +40,15 @@ MOMENT_NAMES = (
 class RefParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "circumference_m", "gamma_t", "p0_eVc", "mass_eV", "charge_e", "harmonic",
-        "voltage_V", "phi_s_rad", "rf_linear", "beta_x_m", "beta_y_m", "Qx", "Qy")]
+        "voltage_V", "phi_s_rad", "rf_linear", "beta_x_m", "beta_y_m", "Qx", "Qy",
+        "eta1", "eta2", "xi_x", "xi_y")]
 
 
 class RefDerived(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "betagamma", "gamma", "beta", "eta", "k", "A", "etaC", "phi_s", "sin_phis",
-        "cos_phis", "K", "Qs", "rf_linear")] + [("mx", C.c_double * 4), ("my", C.c_double * 4)]
+        "cos_phis", "K", "Qs", "rf_linear")] + [("mx", C.c_double * 4), ("my", C.c_double * 4)] + [
+        (n, C.c_double) for n in ("eta1C", "eta2C", "qx", "qy", "bx", "by", "xi_x", "xi_y")]
 
 
 def build(openmp: bool = True, force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:

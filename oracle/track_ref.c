@@ -18,13 +18,16 @@
  * The paper prints none of the formulas.  The readings used here are the
  * textbook single-harmonic synchrotron map:
  *   kick  K(w):  phi = phi_s + k z;  delta <- delta + w A (sin phi - sin phi_s)
- *   drift D(w):  z <- z - w eta C delta
+ *   drift D(w):  z <- z - w eta(delta) C delta,  eta(delta) = eta0 + eta1 delta + eta2 delta^2
+ *                (the slippage expansion; eta1 = eta2 = 0 is the linear slippage)
  *   EC    = K(1) then D(1)           (momentum first, then position)
  *   LF    = D(1/2) K(1) D(1/2)       (Verlet drift-kick-drift)
  *   RUTH4 = D(t/2) K(t) D((1-t)/2) K(1-2t) D((1-t)/2) K(t) D(t/2),
  *           t = 1/(2 - 2^(1/3))      (Forest & Ruth 1990; Yoshida 1990)
  *   transverse, per plane: [u; u'] <- [[cos mu, b sin mu], [-sin mu / b, cos mu]] [u; u']
- *           mu = 2 pi frac(Q), alpha = 0, no chromaticity.
+ *           mu = 2 pi (frac(Q) + xi delta), alpha = 0, with the particle's delta after the
+ *           turn's longitudinal step (xi = dQ/d delta, the chromaticity; xi = 0 gives the
+ *           same matrix for every particle).
  * Derived constants (all FP64, from the ring parameters):
  *   beta*gamma = p0/m; gamma = sqrt(1 + (beta gamma)^2); beta = beta gamma / gamma
  *   eta = 1/gamma_t^2 - 1/gamma^2;  k = 2 pi h / C;  A = q V / (beta p0)   [p0 in eV/c]
@@ -35,7 +38,9 @@
  * rounds as written.  Parity status: pinned (closed-form linear map, textbook
  * synchrotron tune and bucket height, pendulum detuning, time-reversal
  * symmetry, symplecticity, order scaling, high-precision brute force, exact
- * transverse rotation); see the tests.
+ * transverse rotation; for eta(delta): the closed-form drift with the RF off, the
+ * fixed points at eta(delta) = 0 and the order of the smooth Hamiltonian's error;
+ * for the chromaticity: the summed-angle rotation); see the tests.
  */
 #include <math.h>
 #include <stddef.h>
@@ -68,6 +73,8 @@ typedef struct {
     double phi_s_rad;       /* synchronous phase */
     double rf_linear;       /* nonzero: sin(phi) - sin(phi_s) -> cos(phi_s) k z */
     double beta_x_m, beta_y_m, Qx, Qy;
+    double eta1, eta2;      /* slippage expansion: eta(delta) = eta0 + eta1 delta + eta2 delta^2 */
+    double xi_x, xi_y;      /* chromaticities dQ/d delta */
 } ref_params;
 
 typedef struct {
@@ -75,6 +82,10 @@ typedef struct {
     double K, Qs; /* linear strength eta C A k cos(phi_s) and sqrt(K)/(2 pi) */
     double rf_linear;
     double mx[4], my[4]; /* transverse one-turn matrices, row-major */
+    double eta1C, eta2C; /* eta1 C, eta2 C */
+    double qx, qy;       /* frac(Qx), frac(Qy) */
+    double bx, by;       /* beta functions used by the rotations */
+    double xi_x, xi_y;
 } ref_derived;
 
 static const double REF_PI = 3.14159265358979323846;
@@ -84,6 +95,8 @@ int ref_derive(const ref_params* p, ref_derived* d)
     if (!p || !d) return REF_E_INVALID;
     if (!(p->circumference_m > 0) || !(p->p0_eVc > 0) || !(p->mass_eV > 0) ||
         !(p->gamma_t > 0) || !(p->harmonic > 0))
+        return REF_E_INVALID;
+    if (!isfinite(p->eta1) || !isfinite(p->eta2) || !isfinite(p->xi_x) || !isfinite(p->xi_y))
         return REF_E_INVALID;
     memset(d, 0, sizeof(*d));
     d->betagamma = p->p0_eVc / p->mass_eV;
@@ -108,6 +121,14 @@ int ref_derive(const ref_params* p, ref_derived* d)
     d->mx[2] = -sin(mux) / bx; d->mx[3] = cos(mux);
     d->my[0] = cos(muy);       d->my[1] = by * sin(muy);
     d->my[2] = -sin(muy) / by; d->my[3] = cos(muy);
+    d->eta1C = p->eta1 * p->circumference_m;
+    d->eta2C = p->eta2 * p->circumference_m;
+    d->qx = p->Qx - floor(p->Qx);
+    d->qy = p->Qy - floor(p->Qy);
+    d->bx = bx;
+    d->by = by;
+    d->xi_x = p->xi_x;
+    d->xi_y = p->xi_y;
 
     /* a zero voltage is a pure drift: allowed.  Otherwise the linearised
      * motion must oscillate: eta cos(phi_s) > 0 and 0 < K < 4. */
@@ -130,7 +151,8 @@ static void ref_kick(const ref_derived* d, double w, double z, double* dp)
 
 static void ref_drift(const ref_derived* d, double w, double* z, double dp)
 {
-    *z = *z - (w * d->etaC) * dp;
+    double etaC = d->etaC + d->eta1C * dp + d->eta2C * dp * dp; /* eta(delta) C */
+    *z = *z - (w * etaC) * dp;
 }
 
 /* Forest-Ruth coefficient t = 1/(2 - 2^(1/3)). */
@@ -169,6 +191,32 @@ static void ref_rotate(const double* m, double sign, double* u, double* up)
     double upn = m2 * *u + m[3] * *up;
     *u = un;
     *up = upn;
+}
+
+/* Chromatic rotation of one plane: the phase advance 2 pi (q + xi delta) of this
+ * particle; sign = -1 rotates back by the same angle. */
+static void ref_rotate_chroma(double q, double xi, double b, double dp, double sign, double* u,
+                              double* up)
+{
+    double mu = 2.0 * REF_PI * (q + xi * dp);
+    double c = cos(mu), s = sign * sin(mu);
+    double un = c * *u + b * s * *up;
+    double upn = -s / b * *u + c * *up;
+    *u = un;
+    *up = upn;
+}
+
+static void ref_transverse(const ref_derived* d, double sign, int dox, int doy, double dp,
+                           double* x, double* xp, double* y, double* yp)
+{
+    if (dox) {
+        if (d->xi_x != 0.0) ref_rotate_chroma(d->qx, d->xi_x, d->bx, dp, sign, x, xp);
+        else ref_rotate(d->mx, sign, x, xp);
+    }
+    if (doy) {
+        if (d->xi_y != 0.0) ref_rotate_chroma(d->qy, d->xi_y, d->by, dp, sign, y, yp);
+        else ref_rotate(d->my, sign, y, yp);
+    }
 }
 
 /* Two-pass moments of (a, b): mean, population rms and emittance. */
@@ -228,9 +276,17 @@ int ref_track_signed(const ref_derived* d, int scheme, double sign, double* z, d
 #pragma omp parallel for schedule(static)
 #endif
         for (i = 0; i < n; i++) {
-            ref_turn(d, scheme, sign, &z[i], &dp[i]);
-            if (dox) ref_rotate(d->mx, sign, &x[i], &xp[i]);
-            if (doy) ref_rotate(d->my, sign, &y[i], &yp[i]);
+            /* forward: longitudinal step, then the transverse rotation with the new delta;
+             * the inverse undoes them in the opposite order */
+            if (sign > 0) {
+                ref_turn(d, scheme, sign, &z[i], &dp[i]);
+                ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                               doy ? &y[i] : 0, doy ? &yp[i] : 0);
+            } else {
+                ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                               doy ? &y[i] : 0, doy ? &yp[i] : 0);
+                ref_turn(d, scheme, sign, &z[i], &dp[i]);
+            }
         }
         if (moments && t % stride == 0)
             ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n,
@@ -274,10 +330,14 @@ static void ref_dual_turn(const ref_derived* d, int scheme, ref_dual* z, ref_dua
             dp->dz = dp->dz + w * fp * z->dz;
             dp->dd = dp->dd + w * fp * z->dd;
         } else {
-            double w = ws_d[di++] * d->etaC;
-            z->v = z->v - w * dp->v;
-            z->dz = z->dz - w * dp->dz;
-            z->dd = z->dd - w * dp->dd;
+            /* z -= w g(delta), g(delta) = eta(delta) C delta, g' = etaC + 2 eta1C delta + 3 eta2C delta^2 */
+            double w = ws_d[di++];
+            double x = dp->v;
+            double etaC = d->etaC + d->eta1C * x + d->eta2C * x * x;
+            double gp = d->etaC + 2.0 * d->eta1C * x + 3.0 * d->eta2C * x * x;
+            z->v = z->v - (w * etaC) * x;
+            z->dz = z->dz - w * gp * dp->dz;
+            z->dd = z->dd - w * gp * dp->dd;
         }
     }
 }

@@ -397,7 +397,157 @@ def pin_brute_force(O, turns=(10000, 10000, 3000), nparticles=4):
             assert ez < 1e-11 and ed < 1e-11, (scheme, i, ez, ed)
 
 
+# ---- nonlinear slippage eta(delta) and chromaticity ---------------------------------------
+# eta(delta) = eta0 + eta1 delta + eta2 delta^2 in the drift; per-particle transverse phase
+# advance 2 pi (frac(Q) + xi delta) with delta after the turn's longitudinal step.
+# Coefficients exaggerated so that every term moves the result far above rounding.
+ETA1, ETA2 = 0.5, 20.0
+XI_X, XI_Y = 5.0, -3.0
+# milder coefficients for the pins that need bounded motion inside the bucket
+ETA1_B, ETA2_B = 0.05, 2.0
+
+
+def pin_nonlinear_slippage_closed_form(O):
+    """RF off: delta is constant and the drift stages of every scheme add up to one turn,
+    z_N = z_0 - N C (eta0 + eta1 d + eta2 d^2) d, with eta0 from the textbook formula."""
+    r = ring(voltage_V=0.0, eta1=ETA1, eta2=ETA2)
+    tb = textbook(r)
+    d = O.derive(r)
+    N = 1000
+    z0 = np.array([0.0, 0.1, -0.2, 0.05])
+    d0 = np.array([-1e-2, 3e-3, 7e-3, 0.0])
+    C = r["circumference_m"]
+    shift = N * C * (tb["eta"] + ETA1 * d0 + ETA2 * d0 ** 2) * d0
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        zf, df, *_ = O.track(d, scheme, z0, d0, turns=N)
+        assert np.array_equal(df, d0), scheme
+        err = np.abs(zf - (z0 - shift))
+        assert np.all(err <= 1e-12 * np.abs(shift) + 1e-15), (scheme, err, shift)
+
+
+def pin_nonlinear_slippage_fixed_points(O):
+    """With RF on, (z, delta*) with eta(delta*) = 0 and sin(k z) = 0 is a fixed point of
+    every scheme (no slip, no force); the roots come from the quadratic formula.  Half of
+    these points are hyperbolic (rounding grows ~e^(0.06 t)), so 60 turns."""
+    for e1, e2 in ((ETA1, 0.0), (ETA1, ETA2)):
+        r = ring(voltage_V=4.5e6, eta1=e1, eta2=e2)
+        tb = textbook(r)
+        d = O.derive(r)
+        e0 = tb["eta"]
+        if e2 == 0.0:
+            roots = [-e0 / e1]
+        else:
+            q = -0.5 * (e1 + math.sqrt(e1 * e1 - 4 * e2 * e0))
+            roots = [e0 / q, q / e2]  # both roots, each in its stable form
+        for ds in roots:
+            for zs in (0.0, math.pi / d.k):
+                for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+                    zf, df, *_ = O.track(d, scheme, [zs], [ds], turns=60)
+                    assert abs(zf[0] - zs) < 1e-12 and abs(df[0] - ds) < 1e-14, \
+                        (e1, e2, ds, zs, scheme, zf, df)
+
+
+def _energy_err_nl(O, scheme, V, turns):
+    r = ring(voltage_V=V, eta1=ETA1_B, eta2=ETA2_B)
+    tb = textbook(r)
+    d = O.derive(r)
+    C = r["circumference_m"]
+    z, dp = _traj(O, d, scheme, 0.4 * tb["zhat"], 0.0, turns)
+    # invariant of the smooth motion with eta(delta): dz/dt = -dH/d delta, d delta/dt = dH/dz
+    H = C * (tb["eta"] * dp ** 2 / 2 + ETA1_B * dp ** 3 / 3 + ETA2_B * dp ** 4 / 4) \
+        + (d.A / d.k) * (1 - np.cos(d.k * z))
+    return np.max(np.abs(H - H[0])) / H[0]
+
+
+def pin_nonlinear_slippage_energy(O):
+    """The maps with eta(delta) conserve the smooth Hamiltonian
+    C (eta0 d^2/2 + eta1 d^3/3 + eta2 d^4/4) + (A/k)(1 - cos k z) to their order:
+    quartering V divides the bounded error by ~2 (EC), ~4 (LF), ~16 (Ruth4; 25 measured at
+    this amplitude, where the next order still contributes)."""
+    expect = {"euler_cromer": (1.6, 2.8, 0.06), "leapfrog": (3.2, 5.5, 2e-3),
+              "ruth4": (14.0, 34.0, 2e-6)}
+    for scheme, (lo, hi, cap) in expect.items():
+        e_hi = _energy_err_nl(O, scheme, 4e6, 6000)
+        e_lo = _energy_err_nl(O, scheme, 1e6, 6000)
+        assert e_hi < cap, (scheme, e_hi)
+        assert lo < e_hi / e_lo < hi, (scheme, e_hi, e_lo, e_hi / e_lo)
+
+
+def pin_chromatic_phase_sum(O):
+    """Rotations about the same centre commute, so N chromatic turns rotate (u, u') by the
+    summed angle 2 pi sum_t (frac(Q) + xi delta_t), delta_t being delta after turn t's
+    longitudinal step.  The delta_t come from the achromatic map (the transverse push does
+    not act back on (z, delta)); the angle sum and the rotation are evaluated at 30 digits."""
+    import mpmath as mp
+
+    r = ring(voltage_V=4.5e6, xi_x=XI_X, xi_y=XI_Y)
+    tb = textbook(r)
+    d = O.derive(r)
+    d0 = O.derive(ring(voltage_V=4.5e6))
+    N = 500
+    z0 = np.array([0.3, -0.6]) * tb["zhat"]
+    p0 = np.array([0.2, 0.4]) * tb["dhat"]
+    u0, up0 = np.array([1e-3, -2e-3]), np.array([3e-5, 1e-5])
+    v0, vp0 = np.array([-5e-4, 1.5e-3]), np.array([-2e-5, 4e-5])
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        zf, df, xf, xpf, yf, ypf, _ = O.track(d, scheme, z0, p0, u0, up0, v0, vp0, turns=N)
+        for i in range(2):
+            _, dps = _traj(O, d0, scheme, z0[i], p0[i], N)
+            for (Q, xi, beta, a0, b0, a1, b1) in ((r["Qx"], XI_X, r["beta_x_m"], u0[i], up0[i], xf[i], xpf[i]),
+                                                  (r["Qy"], XI_Y, r["beta_y_m"], v0[i], vp0[i], yf[i], ypf[i])):
+                with mp.workdps(30):
+                    q = mp.mpf(Q) - math.floor(Q)
+                    th = 2 * mp.pi * mp.fsum(q + mp.mpf(xi) * mp.mpf(float(x)) for x in dps[1:])
+                    c, sn = mp.cos(th), mp.sin(th)
+                    ae = float(c * a0 + beta * sn * b0)
+                    be = float(-sn / beta * a0 + c * b0)
+                amp = math.hypot(a0, beta * b0)
+                assert abs(a1 - ae) < N * 1e-15 * amp, (scheme, i, a1, ae)
+                assert abs(b1 - be) * beta < N * 1e-15 * amp, (scheme, i, b1, be)
+
+
+def pin_nonlinear_inverse_map(O):
+    """The inverse map undoes N turns with eta(delta) and chromaticity (it rotates back with
+    the same delta before undoing the longitudinal step)."""
+    r = ring(voltage_V=4.5e6, eta1=ETA1_B, eta2=ETA2_B, xi_x=XI_X, xi_y=XI_Y)
+    tb = textbook(r)
+    d = O.derive(r)
+    z0 = np.array([0.05, 0.4, -0.3]) * tb["zhat"]
+    d0 = np.array([0.1, -0.3, 0.2]) * tb["dhat"]
+    x0, xp0 = np.array([1e-3, -2e-3, 5e-4]), np.array([2e-5, 1e-5, -3e-5])
+    y0, yp0 = np.array([-1e-3, 1e-3, 2e-4]), np.array([1e-5, -2e-5, 3e-5])
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        out = O.track(d, scheme, z0, d0, x0, xp0, y0, yp0, turns=5000)
+        back = O.track(d, scheme, *out[:6], turns=5000, sign=-1.0)
+        assert np.max(np.abs(back[0] - z0)) / tb["zhat"] < 1e-12, scheme
+        assert np.max(np.abs(back[1] - d0)) / tb["dhat"] < 1e-12, scheme
+        assert np.max(np.abs(back[2] - x0)) < 1e-12 * 3e-3, scheme
+        assert np.max(np.abs(back[4] - y0)) < 1e-12 * 3e-3, scheme
+
+
+def pin_nonlinear_symplectic(O):
+    """det J = 1 with eta(delta) (the drift stays a shear), dual numbers against finite
+    differences of the tracked map."""
+    r = ring(voltage_V=4.5e6, eta1=ETA1_B, eta2=ETA2_B)
+    tb = textbook(r)
+    d = O.derive(r)
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        for fz, fd in ((0.3, 0.2), (0.6, -0.4)):
+            z0, dp0 = fz * tb["zhat"], fd * tb["dhat"]
+            J = O.jacobian(d, scheme, z0, dp0, 1)
+            assert abs(np.linalg.det(J) - 1) < 1e-13, (scheme, J)
+            hz, hd = 1e-6 * tb["zhat"], 1e-6 * tb["dhat"]
+            zp, dpp, *_ = O.track(d, scheme, [z0 + hz, z0 - hz, z0, z0],
+                                  [dp0, dp0, dp0 + hd, dp0 - hd], turns=1)
+            Jfd = np.array([[(zp[0] - zp[1]) / (2 * hz), (zp[2] - zp[3]) / (2 * hd)],
+                            [(dpp[0] - dpp[1]) / (2 * hz), (dpp[2] - dpp[3]) / (2 * hd)]])
+            scale = np.array([[1.0, tb["zhat"] / tb["dhat"]], [tb["dhat"] / tb["zhat"], 1.0]])
+            assert np.max(np.abs(J - Jfd) / scale) < 1e-6, (scheme, J, Jfd)
+
+
 ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_pendulum_detuning, pin_separatrix, pin_time_reversal, pin_inverse_map,
             pin_symplectic, pin_energy_order, pin_symmetry_and_fixed_point,
-            pin_transverse_rotation, pin_moments)
+            pin_transverse_rotation, pin_moments, pin_nonlinear_slippage_closed_form,
+            pin_nonlinear_slippage_fixed_points, pin_nonlinear_slippage_energy,
+            pin_chromatic_phase_sum, pin_nonlinear_inverse_map, pin_nonlinear_symplectic)

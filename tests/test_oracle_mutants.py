@@ -12,7 +12,39 @@ import pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "track_ref.c")
 
 MUTANTS = {
-    "drift_sign": ("*z = *z - (w * d->etaC) * dp;", "*z = *z + (w * d->etaC) * dp;"),
+    "drift_sign": ("*z = *z - (w * etaC) * dp;", "*z = *z + (w * etaC) * dp;"),
+    "eta1_sign": ("d->etaC + d->eta1C * dp + d->eta2C * dp * dp; /* eta(delta) C */",
+                  "d->etaC - d->eta1C * dp + d->eta2C * dp * dp; /* eta(delta) C */"),
+    "eta2_wrong_power": ("d->etaC + d->eta1C * dp + d->eta2C * dp * dp; /* eta(delta) C */",
+                         "d->etaC + d->eta1C * dp + d->eta2C * dp; /* eta(delta) C */"),
+    "eta1_from_eta2": ("d->eta1C = p->eta1 * p->circumference_m;",
+                       "d->eta1C = p->eta2 * p->circumference_m;"),
+    "chroma_sign": ("double mu = 2.0 * REF_PI * (q + xi * dp);",
+                    "double mu = 2.0 * REF_PI * (q - xi * dp);"),
+    "chroma_no_2pi": ("double mu = 2.0 * REF_PI * (q + xi * dp);",
+                      "double mu = 2.0 * REF_PI * q + xi * dp;"),
+    "chroma_beta_misplaced": ("double un = c * *u + b * s * *up;\n    double upn = -s / b * *u + c * *up;",
+                              "double un = c * *u + s / b * *up;\n    double upn = -s * b * *u + c * *up;"),
+    "chroma_old_delta": ("""            if (sign > 0) {
+                ref_turn(d, scheme, sign, &z[i], &dp[i]);
+                ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                               doy ? &y[i] : 0, doy ? &yp[i] : 0);""",
+                         """            if (sign > 0) {
+                ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                               doy ? &y[i] : 0, doy ? &yp[i] : 0);
+                ref_turn(d, scheme, sign, &z[i], &dp[i]);"""),
+    "chroma_plane_swapped": ("if (d->xi_x != 0.0) ref_rotate_chroma(d->qx, d->xi_x, d->bx, dp, sign, x, xp);",
+                             "if (d->xi_x != 0.0) ref_rotate_chroma(d->qx, d->xi_y, d->bx, dp, sign, x, xp);"),
+    "inverse_order_chroma": ("""            } else {
+                ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                               doy ? &y[i] : 0, doy ? &yp[i] : 0);
+                ref_turn(d, scheme, sign, &z[i], &dp[i]);
+            }""",
+                             """            } else {
+                ref_turn(d, scheme, sign, &z[i], &dp[i]);
+                ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                               doy ? &y[i] : 0, doy ? &yp[i] : 0);
+            }"""),
     "lf_half_weight": ("ref_drift(d, 0.5 * sign, z, *dp);\n        ref_kick(d, 1.0 * sign",
                        "ref_drift(d, 0.45 * sign, z, *dp);\n        ref_kick(d, 1.0 * sign"),
     "ruth_theta": ("cbrt(2.0)", "sqrt(2.0)"),
