@@ -41,6 +41,13 @@ WORKLOADS = {
     "single_bunch_1e6x1e4_ec_lf_ruth4_f64": dict(
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
         voltage=4.5e6, transverse=True, stride=1),
+    # the widened map (SURVEY next row f1): slippage expansion eta(d) = eta0 + 0.05 d + 2 d^2
+    # in the drift and chromaticities xi_x = 5, xi_y = -3 (per-particle transverse phase
+    # advance), the same bunch size and turns; a bunch inside half the separatrix
+    "widened_map_1e6x1e4_f64": dict(
+        n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
+        voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5,
+        ring=dict(eta1=0.05, eta2=2.0, xi_x=5.0, xi_y=-3.0)),
     # small case for quick checks (not a bench line)
     "tiny": dict(n=20_000, turns=200, schemes=("euler_cromer", "leapfrog", "ruth4"),
                  dtype="f64", voltage=4.5e6, transverse=True, stride=1),
@@ -83,9 +90,26 @@ MONITOR_FLOPS = 24
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
 
 
-def alg_flops(scheme, transverse, monitor):
+# The widened map: a drift with the slippage expansion is 3 FMA (6 flops); a chromatic
+# plane is the angle FMA (2), sine and cosine of 2 pi a (quarter-turn reduction: subtract,
+# multiply; r^2; two degree-5 Horner chains; r^3, r^4 and three final FMAs: 31) and the
+# rotation (b s, s / b, 2 MUL + 2 FMA: 8) = 41.
+DRIFT_FLOPS_NL = 6
+CHROMA_PLANE_FLOPS = 41
+
+
+def alg_flops(scheme, transverse, monitor, ring=None):
     """FP64-pipe algorithmic flops per particle-turn (the monitor is FP32-pipe work)."""
-    return SCHEME_FLOPS[scheme] + (TRANSVERSE_FLOPS if transverse else 0)
+    ring = ring or {}
+    nl = ring.get("eta1", 0.0) != 0.0 or ring.get("eta2", 0.0) != 0.0
+    chroma = [ring.get("xi_x", 0.0) != 0.0, ring.get("xi_y", 0.0) != 0.0]
+    f = SCHEME_FLOPS[scheme]
+    if nl or any(chroma):   # the general kernel evaluates every drift with the expansion
+        ndrift = {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4}[scheme]
+        f += ndrift * (DRIFT_FLOPS_NL - DRIFT_FLOPS)
+    if transverse:
+        f += sum(CHROMA_PLANE_FLOPS if c else TRANSVERSE_FLOPS // 2 for c in chroma)
+    return f
 
 
 # ----------------------------------------------------------------------------------------
@@ -171,7 +195,7 @@ def make_inputs(wl, derived, seed):
 
     b = synth.Bucket(k=derived.k, A=derived.A, etaC=derived.etaC, Qs=derived.Qs,
                      betagamma=derived.betagamma)
-    z, dp, _ = synth.matched_bunch(seed, wl["n"], b)
+    z, dp, _ = synth.matched_bunch(seed, wl["n"], b, sep_frac=wl.get("sep_frac", 1.0))
     out = [z, dp]
     if wl["transverse"]:
         out += list(synth.transverse_gaussian(seed + 1, wl["n"], 50.0, 2e-6, derived.betagamma))
@@ -187,7 +211,7 @@ def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
     from paper_1610_05801_gb300 import synth
 
     turns = turns_sample or wl["turns"]
-    ring = synth.ring(wl["voltage"], transverse=True)
+    ring = synth.ring(wl["voltage"], transverse=True, **(wl.get("ring") or {}))
     O = oracle.load()
     d = O.derive(ring)
     b = synth.Bucket(k=d.k, A=d.A, etaC=d.etaC, Qs=d.Qs, betagamma=d.betagamma)
@@ -254,7 +278,7 @@ def run_ours(args, wl_name, wl):
     torch.cuda.set_device(dev)
     _build.build()
 
-    ring = synth.ring(wl["voltage"], transverse=True)
+    ring = synth.ring(wl["voltage"], transverse=True, **(wl.get("ring") or {}))
     R = phtl.Ring(**ring)
     if wl.get("block") or wl.get("tpl"):
         R.set_tuning(block_threads=wl.get("block", 0), turns_per_launch=wl.get("tpl", 0))
@@ -330,7 +354,7 @@ def run_ours(args, wl_name, wl):
     launches_per_call = max(1, nlaunch[dom] // args.steps)
     tpl = math.ceil(turns / launches_per_call)
     dur_s = per_scheme_ms[dom] / 1e3 / launches_per_call
-    flops = alg_flops(dom, wl["transverse"], wl["stride"] > 0) * n * tpl
+    flops = alg_flops(dom, wl["transverse"], wl["stride"] > 0, wl.get("ring")) * n * tpl
     achieved = flops / dur_s / 1e12
 
     if args.no_e2e or wl.get("perturn"):
@@ -339,7 +363,8 @@ def run_ours(args, wl_name, wl):
         e2e_value, h2d, d2h, e2e_steps = e2e_host(R, host, wl, args, dist, dev, ws)
     roof = per_turn_roofline(wl, per_scheme_ms, n, turns, dt) if wl.get("perturn") else None
     kname = (f"k_track_{'f64' if dt == 'f64' else 'f32c'}<{dom}"
-             f"{', transverse' if wl['transverse'] else ''}{', monitor' if wl['stride'] else ''}>")
+             f"{', transverse' if wl['transverse'] else ''}{', monitor' if wl['stride'] else ''}"
+             f"{', widened map' if wl.get('ring') else ''}>")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -349,7 +374,8 @@ def run_ours(args, wl_name, wl):
         "config": {"workload": wl_name, "n_particles": n, "turns": turns,
                    "integrators": list(wl["schemes"]), "transverse": wl["transverse"],
                    "monitor_stride": wl["stride"], "ring": "C=6911.5 m h=4620 p0=26 GeV/c "
-                   "gamma_t=22.77 V=4.5 MV phi_s=0",
+                   "gamma_t=22.77 V=4.5 MV phi_s=0" + "".join(
+                       f" {k}={v}" for k, v in (wl.get("ring") or {}).items()),
                    "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
@@ -360,7 +386,8 @@ def run_ours(args, wl_name, wl):
             "traffic": kernel_traffic(dt, dom, wl, n),
             "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
                            "counts and max clock); DFMA rate confirmed by a microbenchmark",
-            "alg_flops_per_particle_turn": alg_flops(dom, wl["transverse"], wl["stride"] > 0),
+            "alg_flops_per_particle_turn": alg_flops(dom, wl["transverse"], wl["stride"] > 0,
+                                                     wl.get("ring")),
             "moment_flops_per_particle_turn_fp32_pipe": MONITOR_FLOPS if wl["stride"] else 0,
             "launch_ms": dur_s * 1e3, "turns_per_launch": tpl},
         "gpu_launches": launches,

@@ -8,15 +8,19 @@
  *               macro-particle independently, by Euler-Cromer (1st order), leap-frog
  *               (2nd-order Verlet, drift-kick-drift) or a 4th-order Ruth scheme:
  *                 kick  K(w): phi = phi_s + k z;  delta += w A (sin phi - sin phi_s)
- *                 drift D(w): z -= w eta C delta
+ *                 drift D(w): z -= w eta(delta) C delta,
+ *                             eta(delta) = eta0 + eta1 delta + eta2 delta^2
  *                 EC = K(1) D(1);  LF = D(1/2) K(1) D(1/2);
  *                 RUTH4 = D(t/2) K(t) D((1-t)/2) K(1-2t) D((1-t)/2) K(t) D(t/2),
  *                         t = 1/(2 - 2^(1/3))  (Forest & Ruth 1990)
  *               with k = 2 pi h / C, A = q V / (beta p0) [p0 in eV/c],
- *               eta = 1/gamma_t^2 - 1/gamma^2.
+ *               eta0 = 1/gamma_t^2 - 1/gamma^2 (eta1 = eta2 = 0: linear slippage; the
+ *               paper's profile evaluates eta per drift from delta, Fig. cprof).
  *   Sec. 1.1.1  transverse (x, x', y, y'): the same linear transfer matrix every turn,
  *               [u; u'] <- [[cos mu, b sin mu], [-sin mu / b, cos mu]] [u; u'],
- *               mu = 2 pi frac(Q), alpha = 0, no chromaticity.
+ *               mu = 2 pi (frac(Q) + xi delta), alpha = 0; with a chromaticity xi != 0
+ *               each particle turns by its own angle, delta taken after the turn's
+ *               longitudinal step (xi = 0: one matrix for all).
  *   Sec. 2.3    particles are independent, turns are sequential; the turn loop runs
  *               inside the kernel (state in registers), bounded per launch.
  * Per-turn bunch moments are accumulated into a caller-owned monitor buffer.
@@ -65,15 +69,17 @@ enum { PHTL_EULER_CROMER = 0, PHTL_LEAPFROG = 1, PHTL_RUTH4 = 2 };
 
 /* Arithmetic of the particle state.
  *  PHTL_F64   : every coordinate buffer holds n doubles.
- *  PHTL_F32C  : FP32 with compensated (TwoSum) accumulation.  Every coordinate buffer
+ *  PHTL_F32C  : FP32 compensated (double-float, ~48 bits).  Every coordinate buffer
  *               holds 2n floats: [hi(0..n-1) | comp(0..n-1)]; the value of particle i is
- *               hi[i] + comp[i].  Drift and kick increments are FP32 products with the
- *               FP64 coefficients split into hi + lo floats.  The RF phase argument k z
- *               is formed in FP64 from hi + comp and rounded to FP32; the sine is the
- *               library's FP32 polynomial sine (~1 ulp).
+ *               hi[i] + comp[i].  Increments are double-float products of the FP64
+ *               coefficients (split into hi + lo floats) and the pair, added with
+ *               TwoSum and renormalised with Fast2Sum.  The RF phase argument is formed
+ *               in FP64 from hi + comp; the sine is the library's double-float sine
+ *               (~4e-12 absolute on the bucket).
  *  PHTL_F32CD : as PHTL_F32C, but the phase argument is formed in double-float (FP32
  *               pair) arithmetic instead of FP64 (no FP64 instruction on the path).
- *  PHTL_F32CS : as PHTL_F32CD, but the sine is the SFU's (__sinf, absolute error
+ *  PHTL_F32CS : FP32 increments (coefficients split into hi + lo, TwoSum accumulation),
+ *               the phase rounded to FP32 and the SFU's sine (__sinf, absolute error
  *               ~2^-21 on [-pi, pi]): fastest, least accurate over long horizons.    */
 enum { PHTL_F64 = 0, PHTL_F32C = 1, PHTL_F32CD = 2, PHTL_F32CS = 3 };
 
@@ -92,6 +98,12 @@ typedef struct phtl_params {
     double Qy;
     int32_t harmonic;       /* RF harmonic number h > 0                               */
     int32_t rf_linear;      /* nonzero: sin(phi) - sin(phi_s) -> cos(phi_s) k z      */
+    /* Widened map (all 0 = the linear slippage and achromatic rotation above):      */
+    double eta1, eta2;      /* slippage expansion eta(d) = eta0 + eta1 d + eta2 d^2 in  */
+                            /* the drift, z <- z - w eta(d) C d (eta0 from gamma_t)    */
+    double xi_x, xi_y;      /* chromaticities dQ/dd: per plane the phase advance is     */
+                            /* 2 pi (frac(Q) + xi d), d after the turn's longitudinal  */
+                            /* step                                                    */
 } phtl_params;
 
 /* Constants derived in FP64 on the host by phtl_create. */
@@ -125,7 +137,8 @@ typedef struct phtl_handle phtl_handle; /* opaque, library-owned */
 
 /* Validate the parameters and derive the FP64 constants (Sec. 1.1.2 map, see above).
  * Pure host work: touches no GPU.  *out receives a new handle on PHTL_OK.
- * Errors: PHTL_E_INVALID (null, non-positive C/p0/mass/gamma_t/h/beta),
+ * Errors: PHTL_E_INVALID (null, non-positive C/p0/mass/gamma_t/h/beta, a non-finite
+ *         eta1/eta2/xi),
  *         PHTL_E_UNSTABLE (V != 0 and not 0 < K < 4).                               */
 int phtl_create(const phtl_params* params, phtl_handle** out);
 

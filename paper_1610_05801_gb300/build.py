@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphtl.so")
-SOURCES = ["api.cu", "track_f64.cu", "track_f32c.cu", "track_batched.cu", "batch.cu", "server.cu", "batch_static.cu"]
+SOURCES = ["api.cu", "track_f64.cu", "track_f32c.cu", "track_batched.cu", "track_general.cu",
+           "track_general_batched.cu", "batch.cu", "server.cu", "batch_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

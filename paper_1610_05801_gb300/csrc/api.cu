@@ -54,7 +54,9 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
     if (!finite_pos(p.circumference_m) || !finite_pos(p.gamma_t) || !finite_pos(p.p0_eVc) ||
         !finite_pos(p.mass_eV) || !finite_pos(p.beta_x_m) || !finite_pos(p.beta_y_m) ||
         p.harmonic <= 0 || !std::isfinite(p.charge_e) || !std::isfinite(p.voltage_V) ||
-        !std::isfinite(p.phi_s_rad) || !std::isfinite(p.Qx) || !std::isfinite(p.Qy))
+        !std::isfinite(p.phi_s_rad) || !std::isfinite(p.Qx) || !std::isfinite(p.Qy) ||
+        !std::isfinite(p.eta1) || !std::isfinite(p.eta2) || !std::isfinite(p.xi_x) ||
+        !std::isfinite(p.xi_y))
         return PHTL_E_INVALID;
     std::memset(&d, 0, sizeof(d));
     d.betagamma = p.p0_eVc / p.mass_eV;
@@ -106,6 +108,30 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
         split_df(p.phi_s_rad, c.phis_hi, c.phis_lo);
         split_df(d.sin_phis, c.sinphis_hi, c.sinphis_lo);
         split_df(c.lin, c.lin_hi, c.lin_lo);
+        // widened map (eta(delta), chromaticity)
+        c.eta1C = p.eta1 * p.circumference_m;
+        c.eta2C = p.eta2 * p.circumference_m;
+        c.qx = p.Qx - std::floor(p.Qx);
+        c.qy = p.Qy - std::floor(p.Qy);
+        c.xi_x = p.xi_x;
+        c.xi_y = p.xi_y;
+        c.bx = p.beta_x_m;
+        c.by = p.beta_y_m;
+        c.ibx = 1.0 / p.beta_x_m;
+        c.iby = 1.0 / p.beta_y_m;
+        c.chroma_x = p.xi_x != 0.0 ? 1 : 0;
+        c.chroma_y = p.xi_y != 0.0 ? 1 : 0;
+        c.general = (p.eta1 != 0.0 || p.eta2 != 0.0 || c.chroma_x || c.chroma_y) ? 1 : 0;
+        split_df(c.eta1C, c.eta1C_hi, c.eta1C_lo);
+        split_df(c.eta2C, c.eta2C_hi, c.eta2C_lo);
+        split_df(c.qx, c.qx_hi, c.qx_lo);
+        split_df(c.qy, c.qy_hi, c.qy_lo);
+        split_df(c.xi_x, c.xi_x_hi, c.xi_x_lo);
+        split_df(c.xi_y, c.xi_y_hi, c.xi_y_lo);
+        split_df(c.bx, c.bx_hi, c.bx_lo);
+        split_df(c.by, c.by_hi, c.by_lo);
+        split_df(c.ibx, c.ibx_hi, c.ibx_lo);
+        split_df(c.iby, c.iby_hi, c.iby_lo);
     }
     return PHTL_OK;
 }
@@ -215,17 +241,17 @@ cudaError_t launch_perturn(const LaunchDesc& L, const MapConsts& c, const Monito
     return dtype == PHTL_F64 ? launch_track_f64(L, c, m, s) : launch_track_f32c(L, c, m, dtype, s);
 }
 
-int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block)
+int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, bool general)
 {
-    return dtype == PHTL_F64 ? occupancy_f64(scheme, trans, mon, block)
-                             : occupancy_f32c(scheme, trans, mon, dtype, block);
+    return dtype == PHTL_F64 ? occupancy_f64(scheme, trans, mon, block, general)
+                             : occupancy_f32c(scheme, trans, mon, dtype, block, general);
 }
 
-int occupancy(int dtype, int scheme, bool trans, bool mon, int block, bool perturn)
+int occupancy(int dtype, int scheme, bool trans, bool mon, int block, bool perturn, bool general)
 {
-    if (perturn) return occupancy_perturn(scheme, trans, mon, dtype, block);
-    if (dtype == PHTL_F64) return occupancy_f64(scheme, trans, mon, block);
-    return occupancy_f32c(scheme, trans, mon, dtype, block);
+    if (perturn) return occupancy_perturn(scheme, trans, mon, dtype, block, general);
+    if (dtype == PHTL_F64) return occupancy_f64(scheme, trans, mon, block, general);
+    return occupancy_f32c(scheme, trans, mon, dtype, block, general);
 }
 
 int check_track_args(const phtl_handle* h, void* const* c, int64_t n, int64_t turns,
@@ -277,7 +303,8 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     // FP32C buffers are [hi | comp]: the comp half is 16-byte aligned only if n % 4 == 0
     if (dtype != PHTL_F64 && (n * es) % 16 != 0) vec = false;
 
-    const int occ = occupancy(dtype, integrator, trans, mon, block, perturn);
+    const int occ = occupancy(dtype, integrator, trans, mon, block, perturn,
+                              h->mc[integrator].general != 0);
     if (occ <= 0) return PHTL_E_INVALID;
     const int64_t chunk = static_cast<int64_t>(block) * ppt;
     const int64_t nchunks = (n + chunk - 1) / chunk;

@@ -115,7 +115,7 @@ int autotune(phtl_handle* h, int dtype, int scheme, int64_t active, double targe
     int best_block = 0;
     double best_rate = 0.0;
     for (int b : candidates) {
-        const int occ = occupancy_batched(dtype, false, b);
+        const int occ = occupancy_batched(dtype, false, b, h->mc[0].general != 0);
         if (occ <= 0) continue;
         const int64_t cap = static_cast<int64_t>(occ) * h->nsm * b * ppt;  // one full wave
         const int64_t m = std::max<int64_t>(std::min<int64_t>(std::max<int64_t>(active, 1), cap), b * ppt);
@@ -286,7 +286,7 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
             G.T = h->tpl > 0 ? h->tpl : t.turns_per_launch;
             G.rate = t.particle_turns_per_s;
         }
-        if (occupancy_batched(dt, G.mon, G.block) <= 0) {
+        if (occupancy_batched(dt, G.mon, G.block, h->mc[0].general != 0) <= 0) {
             delete b;
             return PHTL_E_INVALID;
         }

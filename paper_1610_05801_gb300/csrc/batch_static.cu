@@ -110,7 +110,7 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
             mon = mon || jobs[order[k]].mon_rows != nullptr;
         }
         const int block = h->block > 0 ? h->block : 128;
-        if (occupancy_batched(dt, mon, block) <= 0) return PHTL_E_INVALID;
+        if (occupancy_batched(dt, mon, block, h->mc[0].general != 0) <= 0) return PHTL_E_INVALID;
         const int64_t T = h->tpl > 0 ? h->tpl : auto_turns_per_launch(dt, jobs[order[0]].integrator, active);
         const int64_t per_tile = static_cast<int64_t>(block) * particles_per_thread(dt);
         JobDesc* G = host + used;

@@ -38,7 +38,28 @@ struct MapConsts {
     float mx_hi[4], mx_lo[4], my_hi[4], my_lo[4];
     int32_t linear;  // rf_linear flag
     float k2opi;     // k * 2/pi rounded to FP32 (quadrant estimate of the fused FP64 sine)
+    // widened map: nonlinear slippage eta(d) = eta0 + eta1 d + eta2 d^2 and chromaticity
+    int32_t general;             // eta1, eta2 or a chromaticity nonzero: general turn loop
+    int32_t chroma_x, chroma_y;  // xi != 0 in that plane
+    int32_t pad2_;
+    double eta1C, eta2C;         // eta1 C, eta2 C
+    double qx, qy;               // frac(Q): the phase advance in turns
+    double xi_x, xi_y;           // chromaticities dQ/d delta
+    double bx, by, ibx, iby;     // beta and 1/beta of the chromatic rotations
+    float eta1C_hi, eta1C_lo, eta2C_hi, eta2C_lo;
+    float qx_hi, qx_lo, qy_hi, qy_lo, xi_x_hi, xi_x_lo, xi_y_hi, xi_y_lo;
+    float bx_hi, bx_lo, by_hi, by_lo, ibx_hi, ibx_lo, iby_hi, iby_lo;
 };
+
+// Drift stage weights w_i of each scheme (the drift of stage i is w_i eta(d) C d); the
+// Ruth4 values are theta/2 and (1 - theta)/2 with theta = 1/(2 - 2^(1/3)).
+__host__ __device__ constexpr double drift_weight(int scheme, int i)
+{
+    return scheme == PHTL_EULER_CROMER ? (i == 0 ? 1.0 : 0.0)
+         : scheme == PHTL_LEAPFROG     ? (i < 2 ? 0.5 : 0.0)
+         : (i == 0 || i == 3)          ? 0.6756035959798289
+                                       : -0.17560359597982889;
+}
 
 // Where and when a launch records monitor rows.
 struct MonitorArgs {
@@ -111,12 +132,17 @@ cudaError_t launch_perturn(const LaunchDesc& L, const MapConsts& c, const Monito
 // (grid = the tiles of those jobs), or row-0 records only when T == 0.
 cudaError_t launch_batched(const JobDesc* jobs, int32_t njobs, const MapConsts& c, int dtype,
                            bool mon, int64_t t0, int32_t T, int grid, int block, cudaStream_t s);
-int occupancy_batched(int dtype, bool mon, int block);
+int occupancy_batched(int dtype, bool mon, int block, bool general);
 int particles_per_thread(int dtype);
 
-// Resident blocks per SM of a kernel variant at a block size (0 = cannot launch).
-int occupancy_f64(int scheme, bool trans, bool mon, int block);
-int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block);
-int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block);
+// Resident blocks per SM of a kernel variant at a block size (0 = cannot launch);
+// general: the widened map's kernels (MapConsts::general).
+int occupancy_f64(int scheme, bool trans, bool mon, int block, bool general);
+int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, bool general);
+int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, bool general);
+
+// Kernels of the widened map (track_general.cu, track_general_batched.cu).
+const void* general_kernel_single(int scheme, int dtype);
+const void* general_kernel_batched(int dtype);
 
 }  // namespace phtl

@@ -245,6 +245,172 @@ __device__ __forceinline__ void long_turn(DF (&z)[P], DF (&d)[P], const MapConst
     }
 }
 
+// ---- widened map: nonlinear slippage and chromaticity -------------------------------
+
+// Drift with the slippage expansion, z -= (dc + g1 d + g2 d^2) d (each coefficient a
+// float pair: dc = w eta0 C, g1 = w eta1 C, g2 = w eta2 C).
+template <int DT>
+__device__ __forceinline__ void drift_nl(DF (&z)[P], const DF (&d)[P], float dh, float dl,
+                                         float g1h, float g1l, float g2h, float g2l)
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (DT == PHTL_F32CS) {
+            const float e = __fmul_rn(__fmaf_rn(g2h, d[p].hi, g1h), d[p].hi);  // (g1 + g2 d) d
+            const float inc = __fmaf_rn(dh + e, d[p].hi, __fmaf_rn(dl, d[p].hi, __fmul_rn(dh, d[p].c)));
+            acc(z[p], -inc);
+        } else {
+            const DF2 dd = as2(d[p]);
+            DF2 e = df_add(df_mul(DF2{g2h, g2l}, dd), DF2{g1h, g1l});
+            e = df_add(df_mul(e, dd), DF2{dh, dl});
+            acc2(z[p], neg2(df_mul(e, dd)));
+        }
+    }
+}
+
+template <int SCHEME, int DT, bool ZS>
+__device__ __forceinline__ void long_turn_nl(DF (&z)[P], DF (&d)[P], const MapConsts& c,
+                                             const float* dh, const float* dl, const float* kh,
+                                             const float* kl, const float (&g1h)[4],
+                                             const float (&g1l)[4], const float (&g2h)[4],
+                                             const float (&g2l)[4])
+{
+    if (SCHEME == PHTL_EULER_CROMER) {
+        kick<DT, ZS>(z, d, kh[0], kl[0], c);
+        drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
+    } else if (SCHEME == PHTL_LEAPFROG) {
+        drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
+        kick<DT, ZS>(z, d, kh[0], kl[0], c);
+        drift_nl<DT>(z, d, dh[1], dl[1], g1h[1], g1l[1], g2h[1], g2l[1]);
+    } else {
+        drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
+        kick<DT, ZS>(z, d, kh[0], kl[0], c);
+        drift_nl<DT>(z, d, dh[1], dl[1], g1h[1], g1l[1], g2h[1], g2l[1]);
+        kick<DT, ZS>(z, d, kh[1], kl[1], c);
+        drift_nl<DT>(z, d, dh[2], dl[2], g1h[2], g1l[2], g2h[2], g2l[2]);
+        kick<DT, ZS>(z, d, kh[2], kl[2], c);
+        drift_nl<DT>(z, d, dh[3], dl[3], g1h[3], g1l[3], g2h[3], g2l[3]);
+    }
+}
+
+// Stage constants w_i eta1 C and w_i eta2 C of this scheme as float pairs (loop-invariant).
+template <int SCHEME>
+__device__ __forceinline__ void slip_stages(const MapConsts& c, float (&g1h)[4], float (&g1l)[4],
+                                            float (&g2h)[4], float (&g2l)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const DF2 a = split_bits(drift_weight(SCHEME, i) * c.eta1C);
+        const DF2 b = split_bits(drift_weight(SCHEME, i) * c.eta2C);
+        g1h[i] = a.h;
+        g1l[i] = a.l;
+        g2h[i] = b.h;
+        g2l[i] = b.l;
+    }
+}
+
+// sin and cos of 2 pi a, a in turns as a float pair (the chromatic phase advance):
+// quarter-turn reduction a = n/4 + f with a.h - n/4 exact (Sterbenz), r = 2 pi f in
+// double-float, then the sine and cosine polynomials of sin_df on r (the two leading
+// Horner steps in double-float, the trailing terms in FP32) and the quadrant's swap and
+// signs.  |a| >= 1e4 turns takes the FP64 form.
+__device__ __forceinline__ void sincos_df_turns(DF2 a, DF2& s, DF2& c)
+{
+    if (!(fabsf(a.h) < 1.0e4f)) {
+        double sd, cd;
+        sincos_turns(widen_bits(a.h) + widen_bits(a.l), sd, cd);
+        s = split_bits(sd);
+        c = split_bits(cd);
+        return;
+    }
+    const float magic = 12582912.0f;
+    const float tf = __fmaf_rn(a.h, 4.0f, magic);
+    const int ni = __float_as_int(tf);
+    const float nq = __fmul_rn(__fsub_rn(tf, magic), 0.25f);
+    const DF2 hd = df_two_sum(a.h, -nq);
+    const DF2 f = df_fast_two_sum(hd.h, __fadd_rn(hd.l, a.l));
+    constexpr DFC tp(6.283185307179586);
+    const DF2 r = df_mul(f, DF2{tp.h, tp.l});
+    const DF2 t = df_mul(r, r);
+    float ts = 1.5918129294866608e-10f, tc = -1.1382632425521717e-11f;
+    ts = __fmaf_rn(ts, t.h, -2.5051131845003624e-08f);
+    tc = __fmaf_rn(tc, t.h, 2.08761462684032e-09f);
+    ts = __fmaf_rn(ts, t.h, 2.755731610255244e-06f);
+    tc = __fmaf_rn(tc, t.h, -2.7557317271729793e-07f);
+    ts = __fmaf_rn(ts, t.h, -0.00019841269836758574f);
+    tc = __fmaf_rn(tc, t.h, 2.480158729876569e-05f);
+    constexpr DFC s1(0.008333333333330948), s0(-0.16666666666666666);
+    constexpr DFC c1(-0.0013888888888887398), c0(0.041666666666666664);
+    DF2 us = df_add_dominant(DF2{s1.h, s1.l}, df_mul_f(t, ts));
+    us = df_add_dominant(DF2{s0.h, s0.l}, df_mul(t, us));
+    DF2 uc = df_add_dominant(DF2{c1.h, c1.l}, df_mul_f(t, tc));
+    uc = df_add_dominant(DF2{c0.h, c0.l}, df_mul(t, uc));
+    const DF2 sr = df_add_dominant(r, df_mul(df_mul(r, t), us));
+    const DF2 cr = df_add_dominant(df_add_dominant(DF2{1.0f, 0.0f}, DF2{-0.5f * t.h, -0.5f * t.l}),
+                                   df_mul(df_mul(t, t), uc));
+    const bool swap = (ni & 1) != 0;
+    // n mod 4 = 0: (sr, cr); 1: (cr, -sr); 2: (-sr, -cr); 3: (-cr, sr)
+    s = df_xor_sign(swap ? cr : sr, static_cast<unsigned>(ni & 2) << 30);
+    c = df_xor_sign(swap ? sr : cr, static_cast<unsigned>((ni + 1) & 2) << 30);
+}
+
+// Chromatic rotation of one plane, each particle by 2 pi (q + xi d) with its own d.
+// PHTL_F32C / PHTL_F32CD: angle, sine and cosine and the rotation in double-float;
+// PHTL_F32CS: the angle in FP32, the SFU's sine and cosine, the rotation in double-float.
+template <int DT>
+__device__ __forceinline__ void rotate_chroma(DF (&u)[P], DF (&v)[P], const DF (&d)[P], float qh,
+                                              float ql, float xh, float xl, float bh, float bl,
+                                              float ibh, float ibl)
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (DT == PHTL_F32CS) {
+            float a = __fmaf_rn(xh, d[p].hi, qh);
+            a = __fsub_rn(a, rintf(a));
+            float sn, cs;
+            __sincosf(6.28318530717958647692f * a, &sn, &cs);
+            const float mh[4] = {cs, bh * sn, -(sn * ibh), cs};
+            const float ml[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            df_rotate(u[p], v[p], mh, ml);
+        } else {
+            DF2 sn, cs;
+            sincos_df_turns(df_add(DF2{qh, ql}, df_mul(DF2{xh, xl}, as2(d[p]))), sn, cs);
+            const DF2 bs = df_mul(DF2{bh, bl}, sn);
+            const DF2 sib = df_mul(DF2{ibh, ibl}, sn);
+            const DF2 un = df_add(df_mul(cs, as2(u[p])), df_mul(bs, as2(v[p])));
+            const DF2 vn = df_add(df_mul(cs, as2(v[p])), neg2(df_mul(sib, as2(u[p]))));
+            u[p] = DF{un.h, un.l};
+            v[p] = DF{vn.h, vn.l};
+        }
+    }
+}
+
+// The transverse step of the general loop: chromatic where xi != 0, else the one matrix.
+template <int DT>
+__device__ __forceinline__ void transverse_gen(DF (&x)[P], DF (&xp)[P], DF (&y)[P], DF (&yp)[P],
+                                               const DF (&d)[P], bool hx, bool hy,
+                                               const MapConsts& c)
+{
+    if (hx) {
+        if (c.chroma_x) {
+            rotate_chroma<DT>(x, xp, d, c.qx_hi, c.qx_lo, c.xi_x_hi, c.xi_x_lo, c.bx_hi, c.bx_lo,
+                              c.ibx_hi, c.ibx_lo);
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) df_rotate(x[p], xp[p], c.mx_hi, c.mx_lo);
+        }
+    }
+    if (hy) {
+        if (c.chroma_y) {
+            rotate_chroma<DT>(y, yp, d, c.qy_hi, c.qy_lo, c.xi_y_hi, c.xi_y_lo, c.by_hi, c.by_lo,
+                              c.iby_hi, c.iby_lo);
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) df_rotate(y[p], yp[p], c.my_hi, c.my_lo);
+        }
+    }
+}
+
 __device__ __forceinline__ void pair_sums(const DF (&a)[P], const DF (&b)[P], float* f)
 {
     f[0] = a[0].hi;

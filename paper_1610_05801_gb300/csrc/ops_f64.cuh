@@ -112,6 +112,88 @@ __device__ __forceinline__ void rotate(double (&u)[P], double (&v)[P], const dou
     }
 }
 
+// ---- widened map: nonlinear slippage and chromaticity -------------------------------
+
+// Drift with the slippage expansion: z -= (dc + g1 d + g2 d^2) d for this stage's
+// w eta(d) C, i.e. dc = w eta0 C, g1 = w eta1 C, g2 = w eta2 C.  With g1 = g2 = 0 it
+// is bitwise the linear drift.
+__device__ __forceinline__ void drift_nl(double (&z)[P], const double (&d)[P], double dc,
+                                         double g1, double g2)
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const double e = fma(fma(g2, d[p], g1), d[p], dc);
+        z[p] = fma(-e, d[p], z[p]);
+    }
+}
+
+// One turn of the scheme with the slippage expansion (g1[i], g2[i]: stage i's w_i eta1 C,
+// w_i eta2 C).
+template <int SCHEME, bool ZS>
+__device__ __forceinline__ void long_turn_nl(double (&z)[P], double (&d)[P], const MapConsts& c,
+                                             const double* dc, const double* kw,
+                                             const double (&g1)[4], const double (&g2)[4])
+{
+    if (SCHEME == PHTL_EULER_CROMER) {
+        kick<ZS>(z, d, kw[0], c);
+        drift_nl(z, d, dc[0], g1[0], g2[0]);
+    } else if (SCHEME == PHTL_LEAPFROG) {
+        drift_nl(z, d, dc[0], g1[0], g2[0]);
+        kick<ZS>(z, d, kw[0], c);
+        drift_nl(z, d, dc[1], g1[1], g2[1]);
+    } else {
+        drift_nl(z, d, dc[0], g1[0], g2[0]);
+        kick<ZS>(z, d, kw[0], c);
+        drift_nl(z, d, dc[1], g1[1], g2[1]);
+        kick<ZS>(z, d, kw[1], c);
+        drift_nl(z, d, dc[2], g1[2], g2[2]);
+        kick<ZS>(z, d, kw[2], c);
+        drift_nl(z, d, dc[3], g1[3], g2[3]);
+    }
+}
+
+// Stage constants g1, g2 of the slippage expansion for this scheme (loop-invariant).
+template <int SCHEME>
+__device__ __forceinline__ void slip_stages(const MapConsts& c, double (&g1)[4], double (&g2)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        g1[i] = drift_weight(SCHEME, i) * c.eta1C;
+        g2[i] = drift_weight(SCHEME, i) * c.eta2C;
+    }
+}
+
+// Chromatic rotation of one plane: each particle turns by 2 pi (q + xi d) with its own d
+// (after the turn's longitudinal step).
+__device__ __forceinline__ void rotate_chroma(double (&u)[P], double (&v)[P], const double (&d)[P],
+                                              double q, double xi, double b, double ib)
+{
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        double sn, cs;
+        sincos_turns(fma(xi, d[p], q), sn, cs);
+        const double un = fma(b * sn, v[p], cs * u[p]);
+        const double vn = fma(-(sn * ib), u[p], cs * v[p]);
+        u[p] = un;
+        v[p] = vn;
+    }
+}
+
+// The transverse step of the general loop: chromatic where xi != 0, else the one matrix.
+__device__ __forceinline__ void transverse_gen(double (&x)[P], double (&xp)[P], double (&y)[P],
+                                               double (&yp)[P], const double (&d)[P], bool hx,
+                                               bool hy, const MapConsts& c)
+{
+    if (hx) {
+        if (c.chroma_x) rotate_chroma(x, xp, d, c.qx, c.xi_x, c.bx, c.ibx);
+        else rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
+    }
+    if (hy) {
+        if (c.chroma_y) rotate_chroma(y, yp, d, c.qy, c.xi_y, c.by, c.iby);
+        else rotate(y, yp, c.my, c.shy, c.shear_y != 0);
+    }
+}
+
 // Per-thread moment contributions of one plane (a, b): sum a, sum b, sum a^2, sum b^2,
 // sum ab over this thread's P particles, as double-float pairs.  The doubles are split
 // into float pairs with integer operations and the products formed with the exact FP32

@@ -135,7 +135,7 @@ public:
     int64_t saturation(int dtype) const
     {
         const int g = dtype < 0 || dtype >= kNumDtypes ? 0 : dtype;
-        const int occ = std::max(1, occupancy_batched(g, true, block_[g]));
+        const int occ = std::max(1, occupancy_batched(g, true, block_[g], h_->mc[0].general != 0));
         return 2ll * occ * h_->nsm * block_[g] * particles_per_thread(g);
     }
 

@@ -35,6 +35,22 @@ constexpr float kPio2H12 = 1.57080078125f;          // 3217 / 2048
 constexpr double kPio2L12 = -4.454455103380769e-06; // pi/2 - 3217/2048
 constexpr float kMagic = 12582912.0f;               // 1.5 * 2^23: rounds to an integer
 
+// sin r = r + r^3 S(r^2), cos r = 1 - r^2/2 + r^4 C(r^2): coefficients of S and C from the
+// highest degree down (Chebyshev fits, gen_sin_coeffs.py)
+__host__ __device__ constexpr double kS(int i)
+{
+    return i == 0 ? 1.5918129294866608e-10 : i == 1 ? -2.5051131845003624e-08
+         : i == 2 ? 2.755731610255244e-06  : i == 3 ? -0.00019841269836758574
+         : i == 4 ? 0.008333333333330948   : -0.16666666666666666;
+}
+__host__ __device__ constexpr double kC(int i)
+{
+    return i == 0 ? -1.1382632425521717e-11 : i == 1 ? 2.08761462684032e-09
+         : i == 2 ? -2.7557317271729793e-07 : i == 3 ? 2.480158729876569e-05
+         : i == 4 ? -0.0013888888888887398  : 0.041666666666666664;
+}
+constexpr double kTwoPi = 6.283185307179586;
+
 __device__ __forceinline__ double sc_coef(bool odd, double s, double c) { return odd ? c : s; }
 
 // sin(q pi/2 + r) for |r| <= pi/4 (a hair more when q came out one off), given the low
@@ -43,12 +59,9 @@ __device__ __forceinline__ double sin_quadrant(double r, int qi)
 {
     const double r2 = r * r;
     const bool odd = (qi & 1) != 0;
-    double p = sc_coef(odd, 1.5918129294866608e-10, -1.1382632425521717e-11);
-    p = fma(p, r2, sc_coef(odd, -2.5051131845003624e-08, 2.08761462684032e-09));
-    p = fma(p, r2, sc_coef(odd, 2.755731610255244e-06, -2.7557317271729793e-07));
-    p = fma(p, r2, sc_coef(odd, -0.00019841269836758574, 2.480158729876569e-05));
-    p = fma(p, r2, sc_coef(odd, 0.008333333333330948, -0.0013888888888887398));
-    p = fma(p, r2, sc_coef(odd, -0.16666666666666666, 0.041666666666666664));
+    double p = sc_coef(odd, kS(0), kC(0));
+#pragma unroll
+    for (int i = 1; i < 6; ++i) p = fma(p, r2, sc_coef(odd, kS(i), kC(i)));
     const double m = (odd ? r2 : r) * r2;                 // r^3 or r^4
     const double a = odd ? fma(-0.5, r2, 1.0) : r;        // r or 1 - r^2/2
     const double res = fma(m, p, a);
@@ -89,6 +102,41 @@ __device__ __forceinline__ double sin_kz(double k, float k2opi, double z)
     double r = fma(k, z, mqh);
     r = fma(widen_float_bits(qf), -kPio2L12, r);
     return sin_quadrant(r, qi);
+}
+
+// sin and cos of 2 pi a, a in turns (the chromatic phase advance).  Quarter-turn
+// reduction a = n/4 + f: f = a - n/4 is exact (Sterbenz; n from FP32, so |f| may exceed
+// 1/8 by a hair), r = 2 pi f is rounded once, then both polynomials of sin_quadrant on r
+// and the quadrant's swap and signs as integer selects.  19 FP64 operations for the pair.
+// |a| >= 2^20 turns falls back to CUDA's sin and cos.
+__device__ __forceinline__ void sincos_turns(double a, double& s, double& c)
+{
+    using namespace detail;
+    const float af = split_bits(a).h;
+    if (!(fabsf(af) < 1048576.0f)) {
+        s = sin(kTwoPi * a);
+        c = cos(kTwoPi * a);
+        return;
+    }
+    const float tf = __fmaf_rn(af, 4.0f, kMagic);
+    const int ni = __float_as_int(tf);                       // n mod 2^22
+    const float nf = __fsub_rn(tf, kMagic);
+    const double r = (a - widen_float_bits(__fmul_rn(nf, 0.25f))) * kTwoPi;
+    const double r2 = r * r;
+    double ps = kS(0), pc = kC(0);
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+        ps = fma(ps, r2, kS(i));
+        pc = fma(pc, r2, kC(i));
+    }
+    const double sr = fma(r * r2, ps, r);
+    const double cr = fma(r2 * r2, pc, fma(-0.5, r2, 1.0));
+    const bool swap = (ni & 1) != 0;
+    // n mod 4 = 0: (sr, cr); 1: (cr, -sr); 2: (-sr, -cr); 3: (-cr, sr)
+    s = __longlong_as_double(__double_as_longlong(swap ? cr : sr) ^
+                             (static_cast<long long>(ni & 2) << 62));
+    c = __longlong_as_double(__double_as_longlong(swap ? sr : cr) ^
+                             (static_cast<long long>((ni + 1) & 2) << 62));
 }
 
 }  // namespace phtl

@@ -1,25 +1,9 @@
-// FP32-compensated persistent multi-turn tracking kernel (PHTL_F32C, PHTL_F32CD,
-// PHTL_F32CS).
-//
-// Same structure as the FP64 kernel (Sec. 2.3: turn loop inside the kernel, state in
-// registers), but every coordinate is an unevaluated sum hi + comp of two floats:
-//   - PHTL_F32C / PHTL_F32CD: each drift/kick increment is a double-float product of the
-//     FP64 weight (split into hi + lo) and the pair, added with Knuth's TwoSum and
-//     renormalised with Fast2Sum; the RF phase argument is formed from hi + comp in FP64
-//     (PHTL_F32C) or in double-float arithmetic (PHTL_F32CD), and the sine is the
-//     double-float polynomial sin_df (~1e-12 absolute);
-//   - PHTL_F32CS: FP32 increments with split weights, the phase rounded to FP32 and the
-//     SFU's __sinf;
-//   - the transverse matrix (Sec. 1.1.1) is applied in double-float arithmetic (exact
-//     FP32 products by fmaf, TwoSum of the two terms), so the rotation keeps ~48 bits;
-//   - per-turn moment sums are FP32 per thread and across the warp (<= 128 particles),
-//     then FP64 across warps and blocks.
-// Each thread owns P = 4 particles (one 128-bit load of hi and one of comp per
-// coordinate).  This kernel is FP32-pipe / issue bound; the FP64 variant of the phase
-// argument adds a handful of FP64-pipe operations per kick.
+// FP32-compensated tracking kernels of the linear map (the kernel template is in
+// kernels_f32c.cuh): selection, occupancy and launch.
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "kernels_f32c.cuh"
 #include "ops_f32c.cuh"
 
 namespace phtl {
@@ -27,96 +11,10 @@ namespace {
 
 using namespace f32c;
 
-// The turn loop of one particle chunk (state in registers throughout); ZS: phi_s == 0.
-template <int SCHEME, int DT, bool TRANS, bool MON, bool ZS>
-__device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&xp)[P],
-                                      DF (&y)[P], DF (&yp)[P], bool hx, bool hy, float cnt,
-                                      const MapConsts& c, const MonitorArgs& m, int nturns,
-                                      double* smem, int& parity)
-{
-    int64_t until = m.until, row = m.row;
-    for (int t = 0; t < nturns; ++t) {
-        long_turn<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo);
-        if (TRANS) {
-            if (hx) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) df_rotate(x[p], xp[p], c.mx_hi, c.mx_lo);
-            }
-            if (hy) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) df_rotate(y[p], yp[p], c.my_hi, c.my_lo);
-            }
-        }
-        if (MON) {
-            if (--until == 0) {
-                record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
-                parity ^= 1;
-                ++row;
-                until = m.stride;
-            }
-        }
-    }
-}
-
-template <int SCHEME, int DT, bool TRANS, bool MON>
-__global__ void __launch_bounds__(256) k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
-{
-    extern __shared__ double smem[];
-    float* g[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) g[i] = static_cast<float*>(L.c[i]);
-    const bool hx = TRANS && g[2] != nullptr;
-    const bool hy = TRANS && g[4] != nullptr;
-    const bool vec = L.vec != 0;
-    const int64_t chunk = static_cast<int64_t>(blockDim.x) * P;
-    const int64_t nchunks = (L.n + chunk - 1) / chunk;
-    int parity = 0;
-
-    for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
-        const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
-        DF z[P], d[P], x[P], xp[P], y[P], yp[P];
-        load4(g[0], base, L.n, vec, z);
-        load4(g[1], base, L.n, vec, d);
-#pragma unroll
-        for (int p = 0; p < P; ++p) x[p] = xp[p] = y[p] = yp[p] = DF{0.0f, 0.0f};
-        if (hx) {
-            load4(g[2], base, L.n, vec, x);
-            load4(g[3], base, L.n, vec, xp);
-        }
-        if (hy) {
-            load4(g[4], base, L.n, vec, y);
-            load4(g[5], base, L.n, vec, yp);
-        }
-        const int64_t left = L.n - base;
-        const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
-
-        if (MON && m.initial) {
-            record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, 0);
-            parity ^= 1;
-        }
-        if (c.phis_zero)
-            turns<SCHEME, DT, TRANS, MON, true>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
-                                                smem, parity);
-        else
-            turns<SCHEME, DT, TRANS, MON, false>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
-                                                 smem, parity);
-        store4(g[0], base, L.n, vec, z);
-        store4(g[1], base, L.n, vec, d);
-        if (hx) {
-            store4(g[2], base, L.n, vec, x);
-            store4(g[3], base, L.n, vec, xp);
-        }
-        if (hy) {
-            store4(g[4], base, L.n, vec, y);
-            store4(g[5], base, L.n, vec, yp);
-        }
-    }
-}
-
 template <int S, int D, bool T, bool M>
 const void* kptr()
 {
-    return reinterpret_cast<const void*>(&k_track_f32c<S, D, T, M>);
+    return reinterpret_cast<const void*>(&kf32::k_track_f32c<S, D, T, M, false>);
 }
 
 template <int S, int D>
@@ -145,9 +43,10 @@ const void* select_kernel(int scheme, int dtype, bool trans, bool mon)
 
 }  // namespace
 
-int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block)
+int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, bool general)
 {
-    const void* k = select_kernel(scheme, dtype, trans, mon);
+    const void* k = general ? general_kernel_single(scheme, dtype)
+                            : select_kernel(scheme, dtype, trans, mon);
     if (!k) return 0;
     int nb = 0;
     const size_t smem = mon ? 2u * (block / 32) * 16 * sizeof(double) : 0;
@@ -160,7 +59,8 @@ cudaError_t launch_track_f32c(const LaunchDesc& L, const MapConsts& c, const Mon
 {
     const bool trans = L.c[2] != nullptr || L.c[4] != nullptr;
     const bool mon = m.rows != nullptr;
-    const void* k = select_kernel(L.scheme, dtype, trans, mon);
+    const void* k = c.general ? general_kernel_single(L.scheme, dtype)
+                              : select_kernel(L.scheme, dtype, trans, mon);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = mon ? 2u * (L.block / 32) * 16 * sizeof(double) : 0;
     LaunchDesc Lc = L;

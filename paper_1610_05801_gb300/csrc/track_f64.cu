@@ -1,22 +1,11 @@
-// FP64 persistent multi-turn tracking kernel.
-//
-// Sec. 2.3 of the paper: particles are independent, turns are sequential, and the
-// turn loop belongs inside the kernel so that each particle's state stays in
-// registers between turns.  Here every thread owns P = 2 particles (one 128-bit load
-// and store per coordinate per launch), runs `nturns` turns of the chosen scheme
-// (Sec. 1.1.2) and the transverse matrix push (Sec. 1.1.1) on them, and adds the
-// per-turn moment sums into the monitor rows.  Blocks walk over particle chunks in a
-// grid-stride loop so the grid can be sized to the resident capacity of the GPU.  (Equal
-// per-block shares were measured slower: the ragged warp at the end of every share costs
-// more than the lone extra chunk some blocks run in the last round.)
-//
-// On GB300 the FP64 pipe retires 2 DFMA per clock per SM (1/64 of FP32), so this
-// kernel is FP64-pipe bound: every FP64 operation per particle-turn counts.
+// FP64 tracking kernels of the linear map (the kernel template is in kernels_f64.cuh),
+// their selection, occupancy and launch, and the sine diagnostics.
 #include <cuda_runtime.h>
 
 #include <cmath>
 
 #include "internal.h"
+#include "kernels_f64.cuh"
 #include "ops_f32c.cuh"
 #include "ops_f64.cuh"
 
@@ -25,93 +14,10 @@ namespace {
 
 using namespace f64;
 
-// The turn loop of one particle chunk (state in registers throughout).
-template <int SCHEME, bool TRANS, bool MON, bool ZS>
-__device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x)[P],
-                                      double (&xp)[P], double (&y)[P], double (&yp)[P], bool hx,
-                                      bool hy, float cnt, const MapConsts& c,
-                                      const MonitorArgs& m, int nturns, double* smem, int& parity)
-{
-    int64_t until = m.until, row = m.row;
-    for (int t = 0; t < nturns; ++t) {
-        long_turn<SCHEME, ZS>(z, d, c, c.dc, c.kw);
-        if (TRANS) {
-            if (hx) rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
-            if (hy) rotate(y, yp, c.my, c.shy, c.shear_y != 0);
-        }
-        if (MON) {
-            if (--until == 0) {
-                record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, row);
-                parity ^= 1;
-                ++row;
-                until = m.stride;
-            }
-        }
-    }
-}
-
-template <int SCHEME, bool TRANS, bool MON>
-__global__ void __launch_bounds__(256, min_blocks_256<SCHEME>()) k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
-{
-    extern __shared__ double smem[];
-    double* gz = static_cast<double*>(L.c[0]);
-    double* gd = static_cast<double*>(L.c[1]);
-    double* gx = static_cast<double*>(L.c[2]);
-    double* gxp = static_cast<double*>(L.c[3]);
-    double* gy = static_cast<double*>(L.c[4]);
-    double* gyp = static_cast<double*>(L.c[5]);
-    const bool hx = TRANS && gx != nullptr;
-    const bool hy = TRANS && gy != nullptr;
-    const bool vec = L.vec != 0;
-    const int64_t chunk = static_cast<int64_t>(blockDim.x) * P;
-    const int64_t nchunks = (L.n + chunk - 1) / chunk;
-    int parity = 0;
-
-    for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
-        const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
-        double z[P], d[P], x[P], xp[P], y[P], yp[P];
-        load2(gz, base, L.n, vec, z);
-        load2(gd, base, L.n, vec, d);
-#pragma unroll
-        for (int p = 0; p < P; ++p) x[p] = xp[p] = y[p] = yp[p] = 0.0;
-        if (hx) {
-            load2(gx, base, L.n, vec, x);
-            load2(gxp, base, L.n, vec, xp);
-        }
-        if (hy) {
-            load2(gy, base, L.n, vec, y);
-            load2(gyp, base, L.n, vec, yp);
-        }
-        const int64_t left = L.n - base;
-        const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
-
-        if (MON && m.initial) {
-            record<TRANS>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, m.rows, 0);
-            parity ^= 1;
-        }
-        if (c.phis_zero)
-            turns<SCHEME, TRANS, MON, true>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
-                                            smem, parity);
-        else
-            turns<SCHEME, TRANS, MON, false>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
-                                             smem, parity);
-        store2(gz, base, L.n, vec, z);
-        store2(gd, base, L.n, vec, d);
-        if (hx) {
-            store2(gx, base, L.n, vec, x);
-            store2(gxp, base, L.n, vec, xp);
-        }
-        if (hy) {
-            store2(gy, base, L.n, vec, y);
-            store2(gyp, base, L.n, vec, yp);
-        }
-    }
-}
-
 template <int S, bool T, bool M>
 const void* kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&k_track_f64<S, T, M>);
+    return reinterpret_cast<const void*>(&kf64::k_track_f64<S, T, M, false>);
 }
 
 const void* select_kernel(int scheme, bool trans, bool mon)
@@ -130,9 +36,10 @@ const void* select_kernel(int scheme, bool trans, bool mon)
 
 }  // namespace
 
-int occupancy_f64(int scheme, bool trans, bool mon, int block)
+int occupancy_f64(int scheme, bool trans, bool mon, int block, bool general)
 {
-    const void* k = select_kernel(scheme, trans, mon);
+    const void* k = general ? general_kernel_single(scheme, PHTL_F64)
+                            : select_kernel(scheme, trans, mon);
     if (!k) return 0;
     int nb = 0;
     const size_t smem = mon ? 2u * (block / 32) * 16 * sizeof(double) : 0;
@@ -145,7 +52,8 @@ cudaError_t launch_track_f64(const LaunchDesc& L, const MapConsts& c, const Moni
 {
     const bool trans = L.c[2] != nullptr || L.c[4] != nullptr;
     const bool mon = m.rows != nullptr;
-    const void* k = select_kernel(L.scheme, trans, mon);
+    const void* k = c.general ? general_kernel_single(L.scheme, PHTL_F64)
+                              : select_kernel(L.scheme, trans, mon);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = mon ? 2u * (L.block / 32) * 16 * sizeof(double) : 0;
     LaunchDesc Lc = L;

@@ -46,7 +46,8 @@ class Params(C.Structure):
                 ("mass_eV", C.c_double), ("charge_e", C.c_double), ("voltage_V", C.c_double),
                 ("phi_s_rad", C.c_double), ("beta_x_m", C.c_double), ("beta_y_m", C.c_double),
                 ("Qx", C.c_double), ("Qy", C.c_double), ("harmonic", C.c_int32),
-                ("rf_linear", C.c_int32)]
+                ("rf_linear", C.c_int32), ("eta1", C.c_double), ("eta2", C.c_double),
+                ("xi_x", C.c_double), ("xi_y", C.c_double)]
 
 
 class Derived(C.Structure):
