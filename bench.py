@@ -379,7 +379,7 @@ def run_ours(args, wl_name, wl):
                    "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
-        "roofline": roof or {
+        "roofline": roof or (issue_roofline(kname) if dt != "f64" else None) or {
             "bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
@@ -412,6 +412,16 @@ def kernel_traffic(dt, scheme, wl, n):
     key = (dt, scheme, bool(wl["transverse"]), bool(wl["stride"]))
     b = NCU_TRAFFIC_BYTES_PER_PARTICLE.get(key)
     return None if b is None or wl.get("perturn") else b * n
+
+
+def issue_roofline(kname):
+    """The FP32-compensated kernels are bound by instruction issue (double-float arithmetic
+    on the FP32 and integer pipes), not by FP64 flops: the FP64 roofline does not apply, and
+    an issue-rate fraction needs ncu's instruction count (profiles/), so none is claimed."""
+    return {"bound": "issue", "kernel": kname, "achieved": None,
+            "peak": 152 * 4 * 2.07, "unit": "G warp-instructions/s", "frac": None,
+            "traffic": None,
+            "note": "double-float FP32 path, issue-bound; the FP64-flop roofline does not apply"}
 
 
 def per_turn_roofline(wl, per_scheme_ms, n, turns, dt):
