@@ -74,7 +74,7 @@ __device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&x
 // GEN: the widened map, chosen on the host (separate kernels, built with TRANS = MON =
 // true; planes and monitor are checked at run time).
 template <int SCHEME, int DT, bool TRANS, bool MON, bool GEN>
-__global__ void __launch_bounds__(256) k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
+__global__ void PHTL_F32C_BOUNDS k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
     extern __shared__ double smem[];
     float* g[6];

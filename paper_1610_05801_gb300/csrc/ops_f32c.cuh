@@ -14,6 +14,14 @@ namespace phtl {
 namespace f32c {
 
 constexpr int P = 4;
+
+// Register cap of the FP32-compensated kernels: a build option (the default is the compiler's
+// choice under a 256-thread launch bound).
+#ifdef PHTL_F32C_MAXNREG
+#define PHTL_F32C_BOUNDS __maxnreg__(PHTL_F32C_MAXNREG)
+#else
+#define PHTL_F32C_BOUNDS __launch_bounds__(256)
+#endif
 constexpr float kTwoPiHi = 6.28318548202514648438f;     // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
 constexpr float kInvTwoPi = 0.159154943091895335769f;
