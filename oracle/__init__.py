@@ -27,8 +27,8 @@ _LIB_PATH = os.path.join(_BUILD, "libphtl_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-EULER_CROMER, LEAPFROG, RUTH4 = 0, 1, 2
-SCHEMES = {"euler_cromer": EULER_CROMER, "leapfrog": LEAPFROG, "ruth4": RUTH4}
+EULER_CROMER, LEAPFROG, RUTH4, RK4 = 0, 1, 2, 3
+SCHEMES = {"euler_cromer": EULER_CROMER, "leapfrog": LEAPFROG, "ruth4": RUTH4, "rk4": RK4}
 NMOM = 15
 MOMENT_NAMES = (
     "mean_z", "mean_dp", "rms_z", "rms_dp", "eps_z",
@@ -41,14 +41,15 @@ class RefParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "circumference_m", "gamma_t", "p0_eVc", "mass_eV", "charge_e", "harmonic",
         "voltage_V", "phi_s_rad", "rf_linear", "beta_x_m", "beta_y_m", "Qx", "Qy",
-        "eta1", "eta2", "xi_x", "xi_y")]
+        "eta1", "eta2", "xi_x", "xi_y", "harmonic2", "voltage2_V", "phi2_rad")]
 
 
 class RefDerived(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "betagamma", "gamma", "beta", "eta", "k", "A", "etaC", "phi_s", "sin_phis",
         "cos_phis", "K", "Qs", "rf_linear")] + [("mx", C.c_double * 4), ("my", C.c_double * 4)] + [
-        (n, C.c_double) for n in ("eta1C", "eta2C", "qx", "qy", "bx", "by", "xi_x", "xi_y")]
+        (n, C.c_double) for n in ("eta1C", "eta2C", "qx", "qy", "bx", "by", "xi_x", "xi_y",
+                                  "k2", "A2", "phi2", "sin_phi2", "cos_phi2")]
 
 
 def build(openmp: bool = True, force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:

@@ -24,6 +24,11 @@
  *   LF    = D(1/2) K(1) D(1/2)       (Verlet drift-kick-drift)
  *   RUTH4 = D(t/2) K(t) D((1-t)/2) K(1-2t) D((1-t)/2) K(t) D(t/2),
  *           t = 1/(2 - 2^(1/3))      (Forest & Ruth 1990; Yoshida 1990)
+ *   RK4   = classic Runge-Kutta on dz/dn = -eta(delta) C delta, d delta/dn = F(z) over one
+ *           turn (Sec. 1.1.2's "Runge-Kutta" read literally; not symplectic, no exact
+ *           inverse), F the kick's force per unit weight
+ *   double RF (optional): the kick adds w A2 (sin(phi_2 + k2 z) - sin phi_2) with
+ *           k2 = 2 pi h2 / C and A2 = q V2 / (beta p0)
  *   transverse, per plane: [u; u'] <- [[cos mu, b sin mu], [-sin mu / b, cos mu]] [u; u']
  *           mu = 2 pi (frac(Q) + xi delta), alpha = 0, with the particle's delta after the
  *           turn's longitudinal step (xi = dQ/d delta, the chromaticity; xi = 0 gives the
@@ -40,7 +45,10 @@
  * symmetry, symplecticity, order scaling, high-precision brute force, exact
  * transverse rotation; for eta(delta): the closed-form drift with the RF off, the
  * fixed points at eta(delta) = 0 and the order of the smooth Hamiltonian's error;
- * for the chromaticity: the summed-angle rotation); see the tests.
+ * for the chromaticity: the summed-angle rotation; for RK4: the Taylor polynomial of
+ * the linear flow, its determinant and the 5th-order local error against an
+ * mpmath Taylor-series flow; for the second RF system: the combined linear slope and
+ * the two-harmonic Hamiltonian's order); see the tests.
  */
 #include <math.h>
 #include <stddef.h>
@@ -54,7 +62,7 @@
 #define REF_E_INVALID (-1)
 #define REF_E_UNSTABLE (-2)
 
-enum { REF_EULER_CROMER = 0, REF_LEAPFROG = 1, REF_RUTH4 = 2 };
+enum { REF_EULER_CROMER = 0, REF_LEAPFROG = 1, REF_RUTH4 = 2, REF_RK4 = 3 };
 
 /* Number of moment values per recorded turn, in this order:
  *  0 mean z   1 mean delta   2 rms z   3 rms delta   4 eps_z
@@ -75,6 +83,7 @@ typedef struct {
     double beta_x_m, beta_y_m, Qx, Qy;
     double eta1, eta2;      /* slippage expansion: eta(delta) = eta0 + eta1 delta + eta2 delta^2 */
     double xi_x, xi_y;      /* chromaticities dQ/d delta */
+    double harmonic2, voltage2_V, phi2_rad; /* second RF system (voltage2 = 0: none) */
 } ref_params;
 
 typedef struct {
@@ -86,6 +95,7 @@ typedef struct {
     double qx, qy;       /* frac(Qx), frac(Qy) */
     double bx, by;       /* beta functions used by the rotations */
     double xi_x, xi_y;
+    double k2, A2, phi2, sin_phi2, cos_phi2; /* second RF system */
 } ref_derived;
 
 static const double REF_PI = 3.14159265358979323846;
@@ -97,6 +107,9 @@ int ref_derive(const ref_params* p, ref_derived* d)
         !(p->gamma_t > 0) || !(p->harmonic > 0))
         return REF_E_INVALID;
     if (!isfinite(p->eta1) || !isfinite(p->eta2) || !isfinite(p->xi_x) || !isfinite(p->xi_y))
+        return REF_E_INVALID;
+    if (!isfinite(p->voltage2_V) || !isfinite(p->phi2_rad) ||
+        (p->voltage2_V != 0.0 && !(p->harmonic2 > 0)))
         return REF_E_INVALID;
     memset(d, 0, sizeof(*d));
     d->betagamma = p->p0_eVc / p->mass_eV;
@@ -110,7 +123,15 @@ int ref_derive(const ref_params* p, ref_derived* d)
     d->sin_phis = sin(p->phi_s_rad);
     d->cos_phis = cos(p->phi_s_rad);
     d->rf_linear = p->rf_linear;
-    d->K = d->etaC * d->A * d->k * d->cos_phis;
+    if (p->voltage2_V != 0.0) {
+        d->k2 = 2.0 * REF_PI * p->harmonic2 / p->circumference_m;
+        d->A2 = p->charge_e * p->voltage2_V / (d->beta * p->p0_eVc);
+        d->phi2 = p->phi2_rad;
+        d->sin_phi2 = sin(p->phi2_rad);
+        d->cos_phi2 = cos(p->phi2_rad);
+    }
+    /* linear strength of both systems together */
+    d->K = d->etaC * (d->A * d->k * d->cos_phis + d->A2 * d->k2 * d->cos_phi2);
     d->Qs = d->K > 0 ? sqrt(d->K) / (2.0 * REF_PI) : 0.0;
 
     double mux = 2.0 * REF_PI * (p->Qx - floor(p->Qx));
@@ -131,8 +152,11 @@ int ref_derive(const ref_params* p, ref_derived* d)
     d->xi_y = p->xi_y;
 
     /* a zero voltage is a pure drift: allowed.  Otherwise the linearised
-     * motion must oscillate: eta cos(phi_s) > 0 and 0 < K < 4. */
-    if (p->voltage_V != 0.0 && !(d->K > 0.0 && d->K < 4.0)) return REF_E_UNSTABLE;
+     * motion must oscillate: eta cos(phi_s) > 0 and 0 < K < 4; with a second RF system
+     * the flat-bottomed bucket K = 0 is allowed too. */
+    if (p->voltage_V != 0.0 && p->voltage2_V == 0.0 && !(d->K > 0.0 && d->K < 4.0))
+        return REF_E_UNSTABLE;
+    if (p->voltage2_V != 0.0 && !(d->K >= 0.0 && d->K < 4.0)) return REF_E_UNSTABLE;
     return REF_OK;
 }
 
@@ -144,9 +168,39 @@ static double ref_force(const ref_derived* d, double z)
     return sin(d->phi_s + d->k * z) - d->sin_phis;
 }
 
+/* the second RF system's force per unit A2 */
+static double ref_force2(const ref_derived* d, double z)
+{
+    if (d->rf_linear != 0.0) return d->cos_phi2 * d->k2 * z;
+    return sin(d->phi2 + d->k2 * z) - d->sin_phi2;
+}
+
 static void ref_kick(const ref_derived* d, double w, double z, double* dp)
 {
     *dp = *dp + (w * d->A) * ref_force(d, z);
+    if (d->A2 != 0.0) *dp = *dp + (w * d->A2) * ref_force2(d, z);
+}
+
+/* Right-hand side of the smooth motion per turn: dz/dn = -eta(delta) C delta,
+ * d delta/dn = A F1(z) + A2 F2(z). */
+static void ref_rhs(const ref_derived* d, double z, double dp, double* fz, double* fd)
+{
+    double etaC = d->etaC + d->eta1C * dp + d->eta2C * dp * dp;
+    *fz = -etaC * dp;
+    *fd = d->A * ref_force(d, z);
+    if (d->A2 != 0.0) *fd = *fd + d->A2 * ref_force2(d, z);
+}
+
+/* One classic RK4 step of one turn. */
+static void ref_rk4(const ref_derived* d, double* z, double* dp)
+{
+    double k1z, k1d, k2z, k2d, k3z, k3d, k4z, k4d;
+    ref_rhs(d, *z, *dp, &k1z, &k1d);
+    ref_rhs(d, *z + 0.5 * k1z, *dp + 0.5 * k1d, &k2z, &k2d);
+    ref_rhs(d, *z + 0.5 * k2z, *dp + 0.5 * k2d, &k3z, &k3d);
+    ref_rhs(d, *z + k3z, *dp + k3d, &k4z, &k4d);
+    *z = *z + (k1z + 2.0 * k2z + 2.0 * k3z + k4z) / 6.0;
+    *dp = *dp + (k1d + 2.0 * k2d + 2.0 * k3d + k4d) / 6.0;
 }
 
 static void ref_drift(const ref_derived* d, double w, double* z, double dp)
@@ -162,7 +216,9 @@ static double ref_ruth_theta(void) { return 1.0 / (2.0 - cbrt(2.0)); }
  * (stages in reverse order with negated weights). */
 static void ref_turn(const ref_derived* d, int scheme, double sign, double* z, double* dp)
 {
-    if (scheme == REF_EULER_CROMER) {
+    if (scheme == REF_RK4) {
+        ref_rk4(d, z, dp); /* forward only (no exact inverse) */
+    } else if (scheme == REF_EULER_CROMER) {
         if (sign > 0) { ref_kick(d, 1.0, *z, dp); ref_drift(d, 1.0, z, *dp); }
         else          { ref_drift(d, -1.0, z, *dp); ref_kick(d, -1.0, *z, dp); }
     } else if (scheme == REF_LEAPFROG) {
@@ -266,7 +322,8 @@ int ref_track_signed(const ref_derived* d, int scheme, double sign, double* z, d
                      double* moments, long stride)
 {
     long t, i;
-    if (!d || n < 0 || turns < 0 || scheme < 0 || scheme > 2) return REF_E_INVALID;
+    if (!d || n < 0 || turns < 0 || scheme < 0 || scheme > 3) return REF_E_INVALID;
+    if (scheme == REF_RK4 && sign < 0) return REF_E_INVALID; /* no exact inverse */
     if (n > 0 && (!z || !dp)) return REF_E_INVALID;
     if (moments && stride <= 0) return REF_E_INVALID;
     int dox = x && xp, doy = y && yp;
@@ -305,11 +362,53 @@ int ref_track(const ref_derived* d, int scheme, double* z, double* dp, double* x
 
 typedef struct { double v, dz, dd; } ref_dual; /* value and d/dz0, d/ddelta0 */
 
+/* the kick's force A F1(z) + A2 F2(z) and its slope d/dz */
+static void ref_force_slope(const ref_derived* d, double z, double* f, double* fp)
+{
+    if (d->rf_linear != 0.0) { *f = d->A * d->cos_phis * d->k * z; *fp = d->A * d->cos_phis * d->k; }
+    else { double ph = d->phi_s + d->k * z; *f = d->A * (sin(ph) - d->sin_phis); *fp = d->A * d->k * cos(ph); }
+    if (d->A2 != 0.0) {
+        if (d->rf_linear != 0.0) { *f += d->A2 * d->cos_phi2 * d->k2 * z; *fp += d->A2 * d->cos_phi2 * d->k2; }
+        else { double ph = d->phi2 + d->k2 * z; *f += d->A2 * (sin(ph) - d->sin_phi2); *fp += d->A2 * d->k2 * cos(ph); }
+    }
+}
+
+/* dual right-hand side of the smooth motion (RK4) */
+static void ref_dual_rhs(const ref_derived* d, ref_dual z, ref_dual dp, ref_dual* fz, ref_dual* fd)
+{
+    double x = dp.v, f, fp;
+    double etaC = d->etaC + d->eta1C * x + d->eta2C * x * x;
+    double gp = d->etaC + 2.0 * d->eta1C * x + 3.0 * d->eta2C * x * x;
+    fz->v = -etaC * x; fz->dz = -gp * dp.dz; fz->dd = -gp * dp.dd;
+    ref_force_slope(d, z.v, &f, &fp);
+    fd->v = f; fd->dz = fp * z.dz; fd->dd = fp * z.dd;
+}
+
+static ref_dual ref_dual_axpy(double a, ref_dual x, ref_dual y) /* y + a x */
+{
+    ref_dual r = {y.v + a * x.v, y.dz + a * x.dz, y.dd + a * x.dd};
+    return r;
+}
+
+static void ref_dual_rk4(const ref_derived* d, ref_dual* z, ref_dual* dp)
+{
+    ref_dual k1z, k1d, k2z, k2d, k3z, k3d, k4z, k4d;
+    ref_dual_rhs(d, *z, *dp, &k1z, &k1d);
+    ref_dual_rhs(d, ref_dual_axpy(0.5, k1z, *z), ref_dual_axpy(0.5, k1d, *dp), &k2z, &k2d);
+    ref_dual_rhs(d, ref_dual_axpy(0.5, k2z, *z), ref_dual_axpy(0.5, k2d, *dp), &k3z, &k3d);
+    ref_dual_rhs(d, ref_dual_axpy(1.0, k3z, *z), ref_dual_axpy(1.0, k3d, *dp), &k4z, &k4d);
+    ref_dual sz = ref_dual_axpy(2.0, k3z, ref_dual_axpy(2.0, k2z, k1z));
+    ref_dual sd = ref_dual_axpy(2.0, k3d, ref_dual_axpy(2.0, k2d, k1d));
+    *z = ref_dual_axpy(1.0 / 6.0, ref_dual_axpy(1.0, k4z, sz), *z);
+    *dp = ref_dual_axpy(1.0 / 6.0, ref_dual_axpy(1.0, k4d, sd), *dp);
+}
+
 static void ref_dual_turn(const ref_derived* d, int scheme, ref_dual* z, ref_dual* dp)
 {
     /* the same stage sequence as ref_turn, carrying the tangent vectors */
     double ws_d[4], ws_k[3];
     int nd, nk, s;
+    if (scheme == REF_RK4) { ref_dual_rk4(d, z, dp); return; }
     if (scheme == REF_EULER_CROMER) { nk = 1; ws_k[0] = 1.0; nd = 1; ws_d[0] = 1.0; }
     else if (scheme == REF_LEAPFROG) { nd = 2; ws_d[0] = ws_d[1] = 0.5; nk = 1; ws_k[0] = 1.0; }
     else {
@@ -323,9 +422,8 @@ static void ref_dual_turn(const ref_derived* d, int scheme, ref_dual* z, ref_dua
     for (s = 0; s < nstages; s++) {
         int is_kick = (scheme == REF_EULER_CROMER) ? (s == 0) : (s % 2 == 1);
         if (is_kick) {
-            double w = ws_k[ki++] * d->A, f, fp;
-            if (d->rf_linear != 0.0) { f = d->cos_phis * d->k * z->v; fp = d->cos_phis * d->k; }
-            else { double ph = d->phi_s + d->k * z->v; f = sin(ph) - d->sin_phis; fp = d->k * cos(ph); }
+            double w = ws_k[ki++], f, fp;
+            ref_force_slope(d, z->v, &f, &fp);
             dp->v = dp->v + w * f;
             dp->dz = dp->dz + w * fp * z->dz;
             dp->dd = dp->dd + w * fp * z->dd;
@@ -345,7 +443,7 @@ static void ref_dual_turn(const ref_derived* d, int scheme, ref_dual* z, ref_dua
 /* J = d(z1, delta1)/d(z0, delta0) after `turns` turns, row-major 2x2. */
 int ref_jacobian(const ref_derived* d, int scheme, double z0, double dp0, long turns, double* J)
 {
-    if (!d || !J || scheme < 0 || scheme > 2 || turns < 0) return REF_E_INVALID;
+    if (!d || !J || scheme < 0 || scheme > 3 || turns < 0) return REF_E_INVALID;
     ref_dual z = {z0, 1.0, 0.0}, dp = {dp0, 0.0, 1.0};
     long t;
     for (t = 0; t < turns; t++) ref_dual_turn(d, scheme, &z, &dp);

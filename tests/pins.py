@@ -418,7 +418,7 @@ def pin_nonlinear_slippage_closed_form(O):
     d0 = np.array([-1e-2, 3e-3, 7e-3, 0.0])
     C = r["circumference_m"]
     shift = N * C * (tb["eta"] + ETA1 * d0 + ETA2 * d0 ** 2) * d0
-    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+    for scheme in ("euler_cromer", "leapfrog", "ruth4", "rk4"):
         zf, df, *_ = O.track(d, scheme, z0, d0, turns=N)
         assert np.array_equal(df, d0), scheme
         err = np.abs(zf - (z0 - shift))
@@ -545,9 +545,150 @@ def pin_nonlinear_symplectic(O):
             assert np.max(np.abs(J - Jfd) / scale) < 1e-6, (scheme, J, Jfd)
 
 
+# ---- classic RK4 and the second RF system ----------------------------------------------
+
+
+def pin_rk4_linear_closed_form(O):
+    """rf_linear: RK4 over one turn of y' = M y, M = [[0, -eta C], [a, 0]], is the 4th-order
+    Taylor polynomial of exp(M): R = I (1 - K/2 + K^2/24) + M (1 - K/6) with K = eta C a
+    (M^2 = -K I), so det R = 1 - K^3/72 + K^4/576 < 1 (not symplectic)."""
+    for phis in (0.0, 0.3):
+        r = ring(rf_linear=1.0, phi_s_rad=phis, voltage_V=4.5e6)
+        tb = textbook(r)
+        d = O.derive(r)
+        eC, a, K = tb["etaC"], tb["a"], tb["K"]
+        Mg = np.array([[0.0, -eC], [a, 0.0]])
+        Rc = np.eye(2) * (1 - K / 2 + K * K / 24) + Mg * (1 - K / 6)
+        R = _linear_matrix(O, d, "rk4")
+        scale = np.array([[1.0, eC], [a, 1.0]])
+        assert np.max(np.abs(R - Rc) / np.abs(scale)) < 1e-12, (phis, R, Rc)
+        detc = 1 - K ** 3 / 72 + K ** 4 / 576
+        assert abs(np.linalg.det(R) - detc) < 1e-14 and detc < 1, (np.linalg.det(R), detc)
+        # the dual-number Jacobian agrees, and 100 turns multiply the determinant
+        J = O.jacobian(d, "rk4", 0.01, 1e-4, 100)
+        assert abs(np.linalg.det(J) / detc ** 100 - 1) < 1e-10
+
+
+def _rk4_turn_error(O, V, fz):
+    """Largest one-turn error of the oracle's RK4 against the exact flow of the pendulum
+    dz/dn = -eta C d, d d/dn = A sin(k z), integrated by mpmath's Taylor-series solver."""
+    import mpmath as mp
+
+    r = ring(voltage_V=V)
+    tb = textbook(r)
+    d = O.derive(r)
+    eC, A, k = d.etaC, d.A, d.k
+    z0 = fz * tb["zhat"]
+    out = []
+    for z_init in z0:
+        zf, df, *_ = O.track(d, "rk4", [z_init], [0.0], turns=1)
+        with mp.workdps(25):
+            f = mp.odefun(lambda t, y: [-mp.mpf(eC) * y[1], mp.mpf(A) * mp.sin(mp.mpf(k) * y[0])],
+                          0, [mp.mpf(z_init), mp.mpf(0)])
+            ze, de = f(1)
+        # z alone would show the 6th-order cosine term (the start has delta = 0); delta
+        # carries the 5th-order sine term that dominates the local error
+        out.append(max(abs(float(ze) - zf[0]) / tb["zhat"], abs(float(de) - df[0]) / tb["dhat"]))
+    return max(out)
+
+
+def pin_rk4_order(O):
+    """RK4 has local error O(h^5): with the step's phase advance halved (V / 4) the one-turn
+    error against the exact flow drops ~2^5 = 32-fold at the same amplitude in z."""
+    fz = np.array([0.2, 0.5])
+    e_hi = _rk4_turn_error(O, 4e6, fz)
+    e_lo = _rk4_turn_error(O, 1e6, fz)
+    assert e_hi < 1e-7, e_hi
+    assert 24 < e_hi / e_lo < 40, (e_hi, e_lo, e_hi / e_lo)
+
+
+def pin_rk4_jacobian(O):
+    """The dual-number Jacobian of one RK4 turn (nonlinear, with eta(delta) and a second RF
+    system) is the derivative of the tracked map; its determinant is below 1."""
+    r = ring(voltage_V=4.5e6, eta1=ETA1_B, eta2=ETA2_B, harmonic2=2 * RING["harmonic"],
+             voltage2_V=1.5e6, phi2_rad=0.0)
+    tb = textbook(r)
+    d = O.derive(r)
+    for fz, fd in ((0.3, 0.2), (0.6, -0.4)):
+        z0, dp0 = fz * tb["zhat"], fd * tb["dhat"]
+        J = O.jacobian(d, "rk4", z0, dp0, 1)
+        hz, hd = 1e-6 * tb["zhat"], 1e-6 * tb["dhat"]
+        zp, dpp, *_ = O.track(d, "rk4", [z0 + hz, z0 - hz, z0, z0],
+                              [dp0, dp0, dp0 + hd, dp0 - hd], turns=1)
+        Jfd = np.array([[(zp[0] - zp[1]) / (2 * hz), (zp[2] - zp[3]) / (2 * hd)],
+                        [(dpp[0] - dpp[1]) / (2 * hz), (dpp[2] - dpp[3]) / (2 * hd)]])
+        scale = np.array([[1.0, tb["zhat"] / tb["dhat"]], [tb["dhat"] / tb["zhat"], 1.0]])
+        assert np.max(np.abs(J - Jfd) / scale) < 1e-6, (J, Jfd)
+        assert 0 < np.linalg.det(J) < 1
+    # no exact inverse: the oracle refuses sign = -1 for RK4
+    try:
+        O.track(d, "rk4", [0.1], [0.0], turns=1, sign=-1.0)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("RK4 has no exact inverse map")
+
+
+def _double_rf(V=4.5e6, ratio=0.3, h2mul=2, phi2=0.0, **over):
+    return ring(voltage_V=V, harmonic2=h2mul * RING["harmonic"], voltage2_V=ratio * V,
+                phi2_rad=phi2, **over)
+
+
+def pin_double_rf_linear(O):
+    """rf_linear with a second RF system: the linear slope is a = A k cos(phi_s) +
+    A2 k2 cos(phi_2) from the textbook constants of both systems, and EC / LF keep their
+    closed-form one-turn matrices with that slope; a flat bottom (a = 0) is allowed."""
+    for phis, phi2 in ((0.0, 0.0), (0.3, -0.4)):
+        r = _double_rf(rf_linear=1.0, phi_s_rad=phis, phi2=phi2)
+        tb = textbook(r)
+        tb2 = textbook(dict(r, harmonic=r["harmonic2"], voltage_V=r["voltage2_V"], phi_s_rad=phi2))
+        d = O.derive(r)
+        eC = tb["etaC"]
+        a = tb["a"] + tb2["a"]
+        K = eC * a
+        for scheme, Mc in (("euler_cromer", np.array([[1 - K, -eC], [a, 1.0]])),
+                           ("leapfrog", np.array([[1 - K / 2, -eC * (1 - K / 4)], [a, 1 - K / 2]]))):
+            M = _linear_matrix(O, d, scheme)
+            assert np.all(np.abs(M / Mc - 1) < 1e-12), (scheme, M, Mc)
+    # bunch-lengthening flat bottom: V2 = -V/2 at h2 = 2h cancels the linear slope
+    flat = _double_rf(ratio=-0.5)
+    d = O.derive(flat)
+    assert abs(d.K) < 1e-15 and O.derive_rc(_oracle.params(**flat)) == 0
+    # and a second system that over-cancels it has no bucket
+    assert O.derive_rc(_oracle.params(**_double_rf(ratio=-0.7))) == -2
+
+
+def _energy_err_rf2(O, scheme, V, turns):
+    r = _double_rf(V=V)
+    tb = textbook(r)
+    d = O.derive(r)
+    z, dp = _traj(O, d, scheme, 0.4 * tb["zhat"], 0.0, turns)
+    # invariant of the smooth motion with both systems (phi_s = phi_2 = 0)
+    H = 0.5 * d.etaC * dp ** 2 + (d.A / d.k) * (1 - np.cos(d.k * z)) \
+        + (0.3 * d.A / (2 * d.k)) * (1 - np.cos(2 * d.k * z))
+    return np.max(np.abs(H - H[0])) / H[0]
+
+
+def pin_double_rf_energy(O):
+    """The symplectic schemes conserve the two-harmonic Hamiltonian (A2 = 0.3 A at k2 = 2 k,
+    both from the textbook scaling) to their order: quartering both voltages divides the
+    bounded error by ~2 (EC), ~4 (LF), ~16 (Ruth4)."""
+    expect = {"euler_cromer": (1.6, 2.7, 0.05), "leapfrog": (3.2, 5.2, 2e-3),
+              "ruth4": (12.0, 24.0, 2e-6)}
+    for scheme, (lo, hi, cap) in expect.items():
+        e_hi = _energy_err_rf2(O, scheme, 4e6, 6000)
+        e_lo = _energy_err_rf2(O, scheme, 1e6, 6000)
+        assert e_hi < cap, (scheme, e_hi)
+        assert lo < e_hi / e_lo < hi, (scheme, e_hi, e_lo, e_hi / e_lo)
+
+
 ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_pendulum_detuning, pin_separatrix, pin_time_reversal, pin_inverse_map,
             pin_symplectic, pin_energy_order, pin_symmetry_and_fixed_point,
             pin_transverse_rotation, pin_moments, pin_nonlinear_slippage_closed_form,
             pin_nonlinear_slippage_fixed_points, pin_nonlinear_slippage_energy,
-            pin_chromatic_phase_sum, pin_nonlinear_inverse_map, pin_nonlinear_symplectic)
+            pin_chromatic_phase_sum, pin_nonlinear_inverse_map, pin_nonlinear_symplectic,
+            pin_rk4_linear_closed_form, pin_rk4_jacobian, pin_double_rf_linear,
+            pin_double_rf_energy)
+# pins that need mpmath (skipped where it is missing)
+ALL_MPMATH = (pin_rk4_order,)

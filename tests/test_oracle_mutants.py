@@ -35,6 +35,21 @@ MUTANTS = {
                 ref_turn(d, scheme, sign, &z[i], &dp[i]);"""),
     "chroma_plane_swapped": ("if (d->xi_x != 0.0) ref_rotate_chroma(d->qx, d->xi_x, d->bx, dp, sign, x, xp);",
                              "if (d->xi_x != 0.0) ref_rotate_chroma(d->qx, d->xi_y, d->bx, dp, sign, x, xp);"),
+    "rk4_k2_weight": ("*z = *z + (k1z + 2.0 * k2z + 2.0 * k3z + k4z) / 6.0;",
+                      "*z = *z + (k1z + 1.0 * k2z + 2.0 * k3z + k4z) / 6.0;"),
+    "rk4_midpoint": ("ref_rhs(d, *z + 0.5 * k1z, *dp + 0.5 * k1d, &k2z, &k2d);",
+                     "ref_rhs(d, *z + k1z, *dp + k1d, &k2z, &k2d);"),
+    "rk4_last_stage_half": ("ref_rhs(d, *z + k3z, *dp + k3d, &k4z, &k4d);",
+                            "ref_rhs(d, *z + 0.5 * k3z, *dp + 0.5 * k3d, &k4z, &k4d);"),
+    "rk4_rhs_linear_slip": ("    *fz = -etaC * dp;", "    *fz = -d->etaC * dp;"),
+    "rf2_k2_from_h": ("d->k2 = 2.0 * REF_PI * p->harmonic2 / p->circumference_m;",
+                      "d->k2 = 2.0 * REF_PI * p->harmonic / p->circumference_m;"),
+    "rf2_A2_without_beta": ("d->A2 = p->charge_e * p->voltage2_V / (d->beta * p->p0_eVc);",
+                            "d->A2 = p->charge_e * p->voltage2_V / (p->p0_eVc);"),
+    "rf2_kick_sign": ("if (d->A2 != 0.0) *dp = *dp + (w * d->A2) * ref_force2(d, z);",
+                      "if (d->A2 != 0.0) *dp = *dp - (w * d->A2) * ref_force2(d, z);"),
+    "rf2_linear_drops_cos": ("if (d->rf_linear != 0.0) return d->cos_phi2 * d->k2 * z;",
+                             "if (d->rf_linear != 0.0) return d->k2 * z;"),
     "inverse_order_chroma": ("""            } else {
                 ref_transverse(d, sign, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
                                doy ? &y[i] : 0, doy ? &yp[i] : 0);
@@ -78,7 +93,13 @@ def test_mutant_is_caught(name, tmp_path):
     lib = oracle.build(openmp=False, force=True, src=str(src), out=str(tmp_path / "libm.so"))
     O = oracle.Oracle(lib)
     caught = []
-    for pin in pins.ALL_FAST:
+    extra = ()
+    try:
+        import mpmath  # noqa: F401
+        extra = pins.ALL_MPMATH
+    except ImportError:
+        pass
+    for pin in pins.ALL_FAST + extra:
         try:
             pin(O)
         except (AssertionError, ValueError, ZeroDivisionError, FloatingPointError):

@@ -14,3 +14,9 @@ def test_pin(ref, pin):
 def test_brute_force_mpmath(ref):
     pytest.importorskip("mpmath")
     pins.pin_brute_force(ref)
+
+
+@pytest.mark.parametrize("pin", pins.ALL_MPMATH, ids=lambda f: f.__name__)
+def test_pin_mpmath(ref, pin):
+    pytest.importorskip("mpmath")
+    pin(ref)
