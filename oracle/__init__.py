@@ -30,6 +30,9 @@ _lib = None
 EULER_CROMER, LEAPFROG, RUTH4, RK4 = 0, 1, 2, 3
 SCHEMES = {"euler_cromer": EULER_CROMER, "leapfrog": LEAPFROG, "ruth4": RUTH4, "rk4": RK4}
 NMOM = 15
+# per-turn constants of a ramp programme: eta_n C, A_n, phi_s,n, sin(phi_s,n),
+# r_n = p0_n / p0_{n+1}, beta_n gamma_n
+RAMP_NC = 6
 MOMENT_NAMES = (
     "mean_z", "mean_dp", "rms_z", "rms_dp", "eps_z",
     "mean_x", "mean_xp", "rms_x", "rms_xp", "eps_x",
@@ -107,6 +110,11 @@ class Oracle:
         L.ref_jacobian.argtypes = [C.POINTER(RefDerived), C.c_int, C.c_double, C.c_double,
                                    C.c_long, dp]
         L.ref_jacobian.restype = C.c_int
+        L.ref_ramp_derive.argtypes = [C.POINTER(RefParams), dp, dp, C.c_long, dp]
+        L.ref_ramp_derive.restype = C.c_int
+        L.ref_track_ramp.argtypes = [C.POINTER(RefDerived), dp, C.c_long, C.c_long, C.c_int,
+                                     dp, dp, dp, dp, dp, dp, C.c_long, C.c_long, dp, C.c_long]
+        L.ref_track_ramp.restype = C.c_int
         L.ref_num_threads.argtypes = []
         L.ref_num_threads.restype = C.c_int
         self.lib = L
@@ -161,6 +169,44 @@ class Oracle:
             raise ValueError(f"ref_jacobian returned {rc}")
         return J.reshape(2, 2)
 
+    def ramp_derive_rc(self, p, V, p0):
+        """(rc, per-turn constants (N, RAMP_NC)) of the programme V[0..N-1], p0[0..N]."""
+        if isinstance(p, dict):
+            p = params(**p)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        p0 = np.ascontiguousarray(p0, dtype=np.float64)
+        if p0.shape[0] != V.shape[0] + 1:
+            raise ValueError("p0 needs one more entry than V")
+        out = np.zeros((V.shape[0], RAMP_NC))
+        rc = self.lib.ref_ramp_derive(C.byref(p), _ptr(V), _ptr(p0), V.shape[0], _ptr(out))
+        return int(rc), out
+
+    def ramp_derive(self, p, V, p0):
+        rc, out = self.ramp_derive_rc(p, V, p0)
+        if rc != 0:
+            raise ValueError(f"ref_ramp_derive returned {rc}")
+        return out
+
+    def track_ramp(self, d: RefDerived, tc, scheme, z, dp, x=None, xp=None, y=None, yp=None,
+                   turn0=0, turns=None, moments=False, stride=1):
+        """Track turns [turn0, turn0 + turns) of a programme (tc from ramp_derive) on copies of
+        the inputs; returns (z, dp, x, xp, y, yp, moments-or-None) like track()."""
+        if isinstance(scheme, str):
+            scheme = SCHEMES[scheme]
+        tc = np.ascontiguousarray(tc, dtype=np.float64)
+        if turns is None:
+            turns = tc.shape[0] - turn0
+        arrs = [None if a is None else np.array(a, dtype=np.float64, copy=True, order="C").reshape(-1)
+                for a in (z, dp, x, xp, y, yp)]
+        n = arrs[0].shape[0]
+        mom = np.zeros((turns // stride + 1, NMOM)) if moments else None
+        rc = self.lib.ref_track_ramp(C.byref(d), _ptr(tc), tc.shape[0], int(turn0), int(scheme),
+                                     *[_ptr(a) for a in arrs], n, int(turns), _ptr(mom),
+                                     int(stride))
+        if rc != 0:
+            raise ValueError(f"ref_track_ramp returned {rc}")
+        return (*arrs, mom)
+
     def num_threads(self) -> int:
         return int(self.lib.ref_num_threads())
 
@@ -196,3 +242,11 @@ def jacobian(*a, **k):
 
 def num_threads() -> int:
     return load().num_threads()
+
+
+def ramp_derive(*a, **k):
+    return load().ramp_derive(*a, **k)
+
+
+def track_ramp(*a, **k):
+    return load().track_ramp(*a, **k)

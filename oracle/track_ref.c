@@ -358,6 +358,115 @@ int ref_track(const ref_derived* d, int scheme, double* z, double* dp, double* x
     return ref_track_signed(d, scheme, 1.0, z, dp, x, xp, y, yp, n, turns, moments, stride);
 }
 
+/* ---- ramp: a per-turn machine programme (accelerating bucket) ---------- */
+
+/* Per-turn constants of a programme, REF_RAMP_NC doubles per turn:
+ *  0 eta_n C   1 A_n = q V_n / (beta_n p0_n)   2 phi_s,n   3 sin(phi_s,n)
+ *  4 r_n = p0_n / p0_{n+1}                     5 beta_n gamma_n = p0_n / m       */
+#define REF_RAMP_NC 6
+
+/*
+ * Derive the per-turn constants of a ramp from the voltage programme V[0..N-1] and the
+ * reference momenta p0[0..N] (p0[n] at the start of turn n, p0[n+1] at its end).
+ * Reading (the paper changes machine parameters between runs but prints no formulas):
+ *   - a particle's momentum grows by q V_n sin(phi) / beta_n per turn (dE = beta c dp),
+ *     the synchronous particle's by p0[n+1] - p0[n], so
+ *     sin(phi_s,n) = beta_n (p0[n+1] - p0[n]) / (q V_n),
+ *     phi_s,n on the branch with eta_n cos(phi_s,n) > 0 (asin above transition,
+ *     pi - asin below it);
+ *   - turn n runs the scheme's stages with eta_n, A_n and phi_s,n (measured against p0[n],
+ *     so the synchronous particle stays at (0, 0) within the turn), then delta and the
+ *     transverse slopes are re-expressed against p0[n+1]: delta <- r_n delta,
+ *     u' <- r_n u' (for a single kick this is exact: p0[n](1 + delta + A(sin phi -
+ *     sin phi_s)) / p0[n+1] - 1 = r_n (delta + A (sin phi - sin phi_s)) - 1 + 1 when the
+ *     synchronous gain is p0[n] A sin phi_s).
+ * Returns REF_E_INVALID (non-finite or non-positive momenta, V = 0 with a momentum change)
+ * or REF_E_UNSTABLE (|sin phi_s| >= 1, or a turn's linear strength outside (0, 4)).
+ */
+int ref_ramp_derive(const ref_params* p, const double* V, const double* p0, long nturns,
+                    double* out)
+{
+    long t;
+    if (!p || nturns < 0 || (nturns > 0 && (!V || !p0 || !out))) return REF_E_INVALID;
+    if (!(p->circumference_m > 0) || !(p->mass_eV > 0) || !(p->gamma_t > 0) || !(p->harmonic > 0))
+        return REF_E_INVALID;
+    double k = 2.0 * REF_PI * p->harmonic / p->circumference_m;
+    for (t = 0; t < nturns; t++) {
+        double pa = p0[t], pb = p0[t + 1];
+        if (!(pa > 0) || !(pb > 0) || !isfinite(pa) || !isfinite(pb) || !isfinite(V[t]))
+            return REF_E_INVALID;
+        double bg = pa / p->mass_eV;
+        double g = sqrt(1.0 + bg * bg);
+        double b = bg / g;
+        double eta = 1.0 / (p->gamma_t * p->gamma_t) - 1.0 / (g * g);
+        double* o = out + t * REF_RAMP_NC;
+        o[0] = eta * p->circumference_m;
+        o[1] = p->charge_e * V[t] / (b * pa);
+        if (V[t] == 0.0) {
+            if (pb != pa) return REF_E_INVALID;
+            o[2] = 0.0;
+            o[3] = 0.0;
+        } else {
+            double x = b * (pb - pa) / (p->charge_e * V[t]);
+            if (!(fabs(x) < 1.0)) return REF_E_UNSTABLE;
+            o[2] = eta > 0 ? asin(x) : REF_PI - asin(x);
+            o[3] = sin(o[2]); /* the kick's own sin(phi_s): (0, 0) stays fixed exactly */
+            double K = o[0] * o[1] * k * cos(o[2]);
+            if (!(K > 0.0 && K < 4.0)) return REF_E_UNSTABLE;
+        }
+        o[4] = pa / pb;
+        o[5] = bg;
+    }
+    return REF_OK;
+}
+
+/*
+ * Track turns [turn0, turn0 + turns) of a programme (tc from ref_ramp_derive).  The
+ * ring's own voltage, phi_s and p0 are replaced turn by turn; the harmonic, gamma_t,
+ * the transverse optics and the rf_linear flag are the ring's.  Monitor rows as
+ * ref_track.  The programme runs the linear map only (single RF, eta0, no chromaticity).
+ */
+int ref_track_ramp(const ref_derived* d, const double* tc, long nprog, long turn0, int scheme,
+                   double* z, double* dp, double* x, double* xp, double* y, double* yp, long n,
+                   long turns, double* moments, long stride)
+{
+    long t, i;
+    if (!d || !tc || n < 0 || turns < 0 || scheme < 0 || scheme > 2) return REF_E_INVALID;
+    if (turn0 < 0 || turn0 + turns > nprog) return REF_E_INVALID;
+    if (n > 0 && (!z || !dp)) return REF_E_INVALID;
+    if (moments && stride <= 0) return REF_E_INVALID;
+    if (d->eta1C != 0.0 || d->eta2C != 0.0 || d->xi_x != 0.0 || d->xi_y != 0.0 || d->A2 != 0.0)
+        return REF_E_INVALID;
+    int dox = x && xp, doy = y && yp;
+    if (moments) ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n, moments);
+    for (t = 1; t <= turns; t++) {
+        const double* c = tc + (turn0 + t - 1) * REF_RAMP_NC;
+        ref_derived dt = *d;
+        dt.etaC = c[0];
+        dt.A = c[1];
+        dt.phi_s = c[2];
+        dt.sin_phis = c[3];
+        dt.cos_phis = cos(c[2]);
+        double r = c[4];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (i = 0; i < n; i++) {
+            ref_turn(&dt, scheme, 1.0, &z[i], &dp[i]);
+            ref_transverse(&dt, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                           doy ? &y[i] : 0, doy ? &yp[i] : 0);
+            /* re-express against the next turn's reference momentum */
+            dp[i] = r * dp[i];
+            if (dox) xp[i] = r * xp[i];
+            if (doy) yp[i] = r * yp[i];
+        }
+        if (moments && t % stride == 0)
+            ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n,
+                        moments + (t / stride) * REF_NMOM);
+    }
+    return REF_OK;
+}
+
 /* ---- one-turn Jacobian by forward-mode dual numbers -------------------- */
 
 typedef struct { double v, dz, dd; } ref_dual; /* value and d/dz0, d/ddelta0 */

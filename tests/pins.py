@@ -682,6 +682,120 @@ def pin_double_rf_energy(O):
         assert lo < e_hi / e_lo < hi, (scheme, e_hi, e_lo, e_hi / e_lo)
 
 
+# ---- ramp: a per-turn machine programme (accelerating bucket) ----------------------------
+
+
+def _linear_ramp(pa, pb, N):
+    """Reference momenta p0[0..N] of a linear momentum ramp."""
+    return pa + (pb - pa) * np.arange(N + 1) / N
+
+
+def _ramp_textbook(r, pn, pn1, V):
+    """Textbook (a, eta C) of one turn of a ramp: the synchronous particle gains the energy
+    E(p0[n+1]) - E(p0[n]) = q V sin(phi_s) per turn (exact energies), phi_s on the stable
+    branch (eta cos phi_s > 0)."""
+    E0, E1 = math.hypot(pn, r["mass_eV"]), math.hypot(pn1, r["mass_eV"])
+    x = (E1 - E0) / V
+    g = E0 / r["mass_eV"]
+    above = 1.0 / r["gamma_t"] ** 2 - 1.0 / g ** 2 > 0
+    phis = math.asin(x) if above else math.pi - math.asin(x)
+    tb = textbook(dict(r, p0_eVc=pn, voltage_V=V, phi_s_rad=phis))
+    return tb["a"], tb["etaC"], x
+
+
+def pin_ramp_constant_programme(O):
+    """A programme with constant momentum and voltage is the fixed machine: bitwise the
+    same particles as the ring's own tracking, every scheme."""
+    r = ring(voltage_V=4.5e6)
+    d = O.derive(r)
+    N = 300
+    tc = O.ramp_derive(r, np.full(N, 4.5e6), np.full(N + 1, r["p0_eVc"]))
+    z0, dp0 = np.array([0.1, -0.3, 0.5]), np.array([1e-3, 0.0, -2e-3])
+    x0, xp0 = np.array([1e-3, 0.0, -2e-3]), np.array([1e-5, -2e-5, 0.0])
+    for scheme in ("euler_cromer", "leapfrog", "ruth4"):
+        a = O.track(d, scheme, z0, dp0, x0, xp0, x0, xp0, turns=N)
+        b = O.track_ramp(d, tc, scheme, z0, dp0, x0, xp0, x0, xp0)
+        for u, v in zip(a[:6], b[:6]):
+            assert np.array_equal(u, v), scheme
+
+
+def pin_ramp_synchronous_phase(O):
+    """Each turn's synchronous phase gives the synchronous particle the programme's energy
+    gain, q V sin(phi_s) = E(p0[n+1]) - E(p0[n]) (exact energies, so the momentum form
+    beta dp agrees to second order, ~1e-8), on the branch with eta cos(phi_s) > 0; eta C
+    and the kick slope are the textbook ones at the turn's starting momentum; the
+    synchronous particle (0, 0) stays there exactly; a voltage too low for the gain has no
+    bucket."""
+    for pa, pb, label in ((26e9, 30e9, "above"), (10e9, 11e9, "below")):
+        r = ring(voltage_V=4.5e6, p0_eVc=pa, phi_s_rad=0.0 if label == "above" else math.pi)
+        N = 4000
+        p0 = _linear_ramp(pa, pb, N)
+        tc = O.ramp_derive(r, np.full(N, 4.5e6), p0)
+        for n in (0, N // 2, N - 1):
+            a, eC, x = _ramp_textbook(r, p0[n], p0[n + 1], 4.5e6)
+            assert abs(tc[n, 3] / x - 1) < 1e-6, (label, n, tc[n, 3], x)
+            assert abs(tc[n, 0] / eC - 1) < 1e-12, (label, n)
+            # the kick slope A_n k cos(phi_s,n) of turn n is the textbook one at p0[n]
+            k = 2 * math.pi * r["harmonic"] / r["circumference_m"]
+            assert abs(tc[n, 1] * k * math.cos(tc[n, 2]) / a - 1) < 1e-7, (label, n)
+            assert eC * math.cos(tc[n, 2]) > 0, (label, n)
+            assert abs(tc[n, 4] * p0[n + 1] / p0[n] - 1) < 1e-15
+        d = O.derive(r)
+        z, dp, *_ = O.track_ramp(d, tc, "ruth4", [0.0], [0.0])
+        assert z[0] == 0.0 and dp[0] == 0.0
+    r = ring(voltage_V=4.5e6)
+    rc, _ = O.ramp_derive_rc(r, np.full(10, 1e5), _linear_ramp(26e9, 26.01e9, 10))
+    assert rc == -2
+
+
+def pin_ramp_adiabatic_invariant(O):
+    """Slow acceleration (rf_linear): the longitudinal action in (z, p0 delta) is an
+    adiabatic invariant.  With the textbook invariant of each turn's linear leap-frog
+    matrix, J = a z^2 + eta C (1 - K/4) delta^2 (K = eta C a), the action J / sqrt(a eta C
+    (1 - K/4)) times p0 stays constant to 2e-3 over a 4e3-turn ramp (about 35 synchrotron
+    periods), above and below transition, while the action without p0 changes by 9-13 %."""
+    for pa, pb, label in ((26e9, 30e9, "above"), (10e9, 11e9, "below")):
+        r = ring(voltage_V=4.5e6, rf_linear=1.0, p0_eVc=pa,
+                 phi_s_rad=0.0 if label == "above" else math.pi)
+        N = 4000
+        p0 = _linear_ramp(pa, pb, N)
+        tc = O.ramp_derive(r, np.full(N, 4.5e6), p0)
+        d = O.derive(r)
+        *_, mom = O.track_ramp(d, tc, "leapfrog", [0.05], [0.0], moments=True, stride=1)
+        z, dp = mom[:, 0], mom[:, 1]
+        I = np.empty(N + 1)
+        for n in range(N + 1):
+            pn1 = p0[n + 1] if n < N else p0[N] + (p0[N] - p0[N - 1])
+            a, eC, _ = _ramp_textbook(r, p0[n], pn1, 4.5e6)
+            b = eC * (1.0 - eC * a / 4.0)
+            I[n] = (a * z[n] ** 2 + b * dp[n] ** 2) / math.sqrt(a * b)
+        inv = I * p0
+        assert np.max(np.abs(inv / inv[0] - 1)) < 2e-3, (label, np.max(np.abs(inv / inv[0] - 1)))
+        assert abs(I[-1] / I[0] - 1) > 0.05, label
+
+
+def pin_ramp_normalised_emittance(O):
+    """Transverse adiabatic damping: the slopes follow the reference momentum, so the
+    normalised emittance beta gamma eps (Liouville) is conserved through the ramp to
+    rounding, while the geometric emittance shrinks as 1 / p0."""
+    r = ring(voltage_V=4.5e6)
+    N = 2000
+    p0 = _linear_ramp(26e9, 30e9, N)
+    tc = O.ramp_derive(r, np.full(N, 4.5e6), p0)
+    d = O.derive(r)
+    rng = np.random.default_rng(11)
+    n = 500
+    x, xp = rng.normal(0, 1.9e-3, n), rng.normal(0, 3.8e-5, n)
+    y, yp = rng.normal(0, 1.9e-3, n), rng.normal(0, 3.8e-5, n)
+    z, dp = rng.normal(0, 0.05, n), rng.normal(0, 4e-4, n)
+    *_, mom = O.track_ramp(d, tc, "leapfrog", z, dp, x, xp, y, yp, moments=True, stride=N)
+    for off in (9, 14):
+        e0, e1 = mom[0, off], mom[-1, off]
+        en0, en1 = e0 * p0[0] / r["mass_eV"], e1 * p0[N] / r["mass_eV"]
+        assert abs(en1 / en0 - 1) < 1e-11, (off, en1 / en0)
+        assert abs(e1 / e0 - p0[0] / p0[N]) < 1e-11
+
+
 ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_pendulum_detuning, pin_separatrix, pin_time_reversal, pin_inverse_map,
             pin_symplectic, pin_energy_order, pin_symmetry_and_fixed_point,
@@ -689,6 +803,7 @@ ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_nonlinear_slippage_fixed_points, pin_nonlinear_slippage_energy,
             pin_chromatic_phase_sum, pin_nonlinear_inverse_map, pin_nonlinear_symplectic,
             pin_rk4_linear_closed_form, pin_rk4_jacobian, pin_double_rf_linear,
-            pin_double_rf_energy)
+            pin_double_rf_energy, pin_ramp_constant_programme, pin_ramp_synchronous_phase,
+            pin_ramp_adiabatic_invariant, pin_ramp_normalised_emittance)
 # pins that need mpmath (skipped where it is missing)
 ALL_MPMATH = (pin_rk4_order,)

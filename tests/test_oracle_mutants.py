@@ -80,6 +80,15 @@ MUTANTS = {
                  "d->eta = 1.0 / (d->gamma * d->gamma) - 1.0 / (p->gamma_t * p->gamma_t);"),
     "gamma_from_p_over_m": ("d->gamma = sqrt(1.0 + d->betagamma * d->betagamma);",
                             "d->gamma = d->betagamma;"),
+    "ramp_no_rescale": ("            dp[i] = r * dp[i];\n", "            dp[i] = dp[i];\n"),
+    "ramp_rescale_inverted": ("        o[4] = pa / pb;", "        o[4] = pb / pa;"),
+    "ramp_slopes_not_damped": ("            if (dox) xp[i] = r * xp[i];", "            if (dox) xp[i] = xp[i];"),
+    "ramp_phis_branch": ("o[2] = eta > 0 ? asin(x) : REF_PI - asin(x);", "o[2] = asin(x);"),
+    "ramp_gain_without_beta": ("double x = b * (pb - pa) / (p->charge_e * V[t]);",
+                               "double x = (pb - pa) / (p->charge_e * V[t]);"),
+    "ramp_eta_from_end_momentum": ("double bg = pa / p->mass_eV;", "double bg = pb / p->mass_eV;"),
+    "ramp_A_from_end_momentum": ("o[1] = p->charge_e * V[t] / (b * pa);",
+                                 "o[1] = p->charge_e * V[t] / (b * pb);"),
 }
 
 
