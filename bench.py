@@ -48,6 +48,22 @@ WORKLOADS = {
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
         voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5,
         ring=dict(eta1=0.05, eta2=2.0, xi_x=5.0, xi_y=-3.0)),
+    # classic RK4 (four force evaluations per turn) on a double-RF ring: second system at
+    # h2 = 2h with V2 = 0.3 V in phase (bunch lengthening), 1e6 particles x 1e4 turns
+    "rk4_double_rf_1e6x1e4_f64": dict(
+        n=1_000_000, turns=10_000, schemes=("rk4",), dtype="f64", voltage=4.5e6,
+        transverse=True, stride=1, sep_frac=0.5,
+        ring=dict(harmonic2=2 * 4620, voltage2_V=0.3 * 4.5e6, phi2_rad=0.0)),
+    # the three symplectic schemes on the same double-RF ring
+    "double_rf_1e6x1e4_ec_lf_ruth4_f64": dict(
+        n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
+        voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5,
+        ring=dict(harmonic2=2 * 4620, voltage2_V=0.3 * 4.5e6, phi2_rad=0.0)),
+    # accelerating bucket: a linear momentum ramp 26 -> 30 GeV/c over the 1e4 turns at
+    # 4.5 MV (phi_s ~ 0.09 rad), per-turn constants from the programme table
+    "ramp_1e6x1e4_ec_lf_ruth4_f64": dict(
+        n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
+        voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5, ramp=dict(p0_end=30e9)),
     # small case for quick checks (not a bench line)
     "tiny": dict(n=20_000, turns=200, schemes=("euler_cromer", "leapfrog", "ruth4"),
                  dtype="f64", voltage=4.5e6, transverse=True, stride=1),
@@ -85,6 +101,17 @@ DRIFT_FLOPS = 2
 SCHEME_FLOPS = {"euler_cromer": DRIFT_FLOPS + KICK_FLOPS,
                 "leapfrog": 2 * DRIFT_FLOPS + KICK_FLOPS,
                 "ruth4": 4 * DRIFT_FLOPS + 3 * KICK_FLOPS}
+# Classic RK4 per particle-turn: four right-hand sides, each the slippage term
+# -(eta0 C + eta1 C d + eta2 C d^2) d (2 FMA + 1 MUL = 5) and the force A F1(z) (phase FMA,
+# sine, subtract, multiply = 24); the stage arguments z + c k, d + c k (2 x 2 FMA + 2 ADD =
+# 10) and the weighted sums (per coordinate 2 ADD + 2 FMA = 6, x 2 = 12).
+RK4_RHS_FLOPS = 5 + 2 + SINE_FLOPS + 1 + 1
+SCHEME_FLOPS["rk4"] = 4 * RK4_RHS_FLOPS + 10 + 12
+# the second RF system: each force evaluation adds phase FMA, sine, subtract and FMA
+RF2_FLOPS = 2 + SINE_FLOPS + 1 + 2
+KICKS = {"euler_cromer": 1, "leapfrog": 1, "ruth4": 3, "rk4": 4}
+# ramp programme: per particle-turn delta, x' and y' are multiplied by r_n
+RAMP_FLOPS = 3
 TRANSVERSE_FLOPS = 12
 MONITOR_FLOPS = 24
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
@@ -103,10 +130,14 @@ def alg_flops(scheme, transverse, monitor, ring=None):
     ring = ring or {}
     nl = ring.get("eta1", 0.0) != 0.0 or ring.get("eta2", 0.0) != 0.0
     chroma = [ring.get("xi_x", 0.0) != 0.0, ring.get("xi_y", 0.0) != 0.0]
+    dual = ring.get("voltage2_V", 0.0) != 0.0
     f = SCHEME_FLOPS[scheme]
-    if nl or any(chroma):   # the general kernel evaluates every drift with the expansion
+    if (nl or any(chroma) or dual) and scheme != "rk4":
+        # the general kernel evaluates every drift with the expansion
         ndrift = {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4}[scheme]
         f += ndrift * (DRIFT_FLOPS_NL - DRIFT_FLOPS)
+    if dual:
+        f += KICKS[scheme] * RF2_FLOPS
     if transverse:
         f += sum(CHROMA_PLANE_FLOPS if c else TRANSVERSE_FLOPS // 2 for c in chroma)
     return f
@@ -203,6 +234,19 @@ def make_inputs(wl, derived, seed):
     return out
 
 
+def ramp_programme(wl):
+    """(V[turns], p0[turns + 1]) of a ramp workload: a linear momentum ramp from the ring's
+    p0 to wl['ramp']['p0_end'] at the workload's voltage."""
+    import numpy as np
+
+    from paper_1610_05801_gb300 import synth
+
+    turns = wl["turns"]
+    pa = synth.ring(wl["voltage"])["p0_eVc"]
+    pb = wl["ramp"]["p0_end"]
+    return np.full(turns, wl["voltage"]), pa + (pb - pa) * np.arange(turns + 1) / turns
+
+
 def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the workload
     (n_sample particles x turns_sample turns x every scheme, with the same transverse
@@ -221,11 +265,19 @@ def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
         tr += list(synth.transverse_gaussian(2, n_sample, 50.0, 2e-6, d.betagamma))
         tr += list(synth.transverse_gaussian(3, n_sample, 50.0, 2e-6, d.betagamma))
     times = []
+    tc = None
+    if wl.get("ramp"):
+        V, p0 = ramp_programme(wl)
+        tc = O.ramp_derive(ring, V[:turns], p0[:turns + 1])
     for it in range(warmup + steps):
         t0 = time.perf_counter()
         for s in wl["schemes"]:
-            O.track(d, s, z, dp, *tr, turns=turns, moments=wl["stride"] > 0,
-                    stride=max(1, wl["stride"]))
+            if tc is not None:
+                O.track_ramp(d, tc, s, z, dp, *tr, turns=turns, moments=wl["stride"] > 0,
+                             stride=max(1, wl["stride"]))
+            else:
+                O.track(d, s, z, dp, *tr, turns=turns, moments=wl["stride"] > 0,
+                        stride=max(1, wl["stride"]))
         dt = time.perf_counter() - t0
         if it >= warmup:
             times.append(dt)
@@ -301,6 +353,12 @@ def run_ours(args, wl_name, wl):
     ev = {s: [] for s in wl["schemes"]}
     nlaunch = {s: 0 for s in wl["schemes"]}
     track = R.track_perturn if wl.get("perturn") else R.track
+    if wl.get("ramp"):
+        R.set_programme(*ramp_programme(wl))
+
+        def track(*b, turns, integrator, dtype, stream):
+            R.track_programme(*b, turn0=0, turns=turns, integrator=integrator, dtype=dtype,
+                              stream=stream)
 
     def step(record=False):
         for s in wl["schemes"]:
@@ -354,17 +412,22 @@ def run_ours(args, wl_name, wl):
     launches_per_call = max(1, nlaunch[dom] // args.steps)
     tpl = math.ceil(turns / launches_per_call)
     dur_s = per_scheme_ms[dom] / 1e3 / launches_per_call
-    flops = alg_flops(dom, wl["transverse"], wl["stride"] > 0, wl.get("ring")) * n * tpl
+    flops_pt = alg_flops(dom, wl["transverse"], wl["stride"] > 0, wl.get("ring"))
+    if wl.get("ramp"):
+        flops_pt += RAMP_FLOPS
+    flops = flops_pt * n * tpl
     achieved = flops / dur_s / 1e12
 
-    if args.no_e2e or wl.get("perturn"):
+    if args.no_e2e or wl.get("perturn") or wl.get("ramp"):
         e2e_value, h2d, d2h, e2e_steps = None, 0, 0, 0
     else:
         e2e_value, h2d, d2h, e2e_steps = e2e_host(R, host, wl, args, dist, dev, ws)
     roof = per_turn_roofline(wl, per_scheme_ms, n, turns, dt) if wl.get("perturn") else None
     kname = (f"k_track_{'f64' if dt == 'f64' else 'f32c'}<{dom}"
              f"{', transverse' if wl['transverse'] else ''}{', monitor' if wl['stride'] else ''}"
-             f"{', widened map' if wl.get('ring') else ''}>")
+             f"{', widened map' if wl.get('ring') else ''}{', ramp programme' if wl.get('ramp') else ''}>")
+    if wl.get("ramp"):
+        kname = kname.replace("k_track_", "k_ramp_")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -375,7 +438,9 @@ def run_ours(args, wl_name, wl):
                    "integrators": list(wl["schemes"]), "transverse": wl["transverse"],
                    "monitor_stride": wl["stride"], "ring": "C=6911.5 m h=4620 p0=26 GeV/c "
                    "gamma_t=22.77 V=4.5 MV phi_s=0" + "".join(
-                       f" {k}={v}" for k, v in (wl.get("ring") or {}).items()),
+                       f" {k}={v}" for k, v in (wl.get("ring") or {}).items()) + (
+                       f" ramp p0 26 -> {wl['ramp']['p0_end'] / 1e9:g} GeV/c linear over the "
+                       f"turns" if wl.get("ramp") else ""),
                    "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
@@ -386,8 +451,7 @@ def run_ours(args, wl_name, wl):
             "traffic": kernel_traffic(dt, dom, wl, n),
             "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
                            "counts and max clock); DFMA rate confirmed by a microbenchmark",
-            "alg_flops_per_particle_turn": alg_flops(dom, wl["transverse"], wl["stride"] > 0,
-                                                     wl.get("ring")),
+            "alg_flops_per_particle_turn": flops_pt,
             "moment_flops_per_particle_turn_fp32_pipe": MONITOR_FLOPS if wl["stride"] else 0,
             "launch_ms": dur_s * 1e3, "turns_per_launch": tpl},
         "gpu_launches": launches,

@@ -65,7 +65,11 @@ extern "C" {
 #define PHTL_E_TOOBIG (-9)    /* more jobs than phtl_batch_run_noalloc's fixed table   */
 
 /* ---- enums ------------------------------------------------------------------------- */
-enum { PHTL_EULER_CROMER = 0, PHTL_LEAPFROG = 1, PHTL_RUTH4 = 2 };
+/* PHTL_RK4: classic 4th-order Runge-Kutta on the smooth motion per turn, dz/dn = -eta(d) C d,
+ * dd/dn = A F1(z) + A2 F2(z) (Sec. 1.1.2's "Runge-Kutta" read literally): four force
+ * evaluations per turn, not symplectic, forward only.  It runs in the widened map's
+ * kernels (every dtype).                                                             */
+enum { PHTL_EULER_CROMER = 0, PHTL_LEAPFROG = 1, PHTL_RUTH4 = 2, PHTL_RK4 = 3 };
 
 /* Arithmetic of the particle state.
  *  PHTL_F64   : every coordinate buffer holds n doubles.
@@ -104,6 +108,14 @@ typedef struct phtl_params {
     double xi_x, xi_y;      /* chromaticities dQ/dd: per plane the phase advance is     */
                             /* 2 pi (frac(Q) + xi d), d after the turn's longitudinal  */
                             /* step                                                    */
+    /* Second RF system (double RF; voltage2_V = 0: none).  Each kick K(w) adds        */
+    /* w A2 (sin(phi2 + k2 z) - sin(phi2)), k2 = 2 pi harmonic2 / C,                   */
+    /* A2 = q voltage2_V / (beta p0); in rf_linear mode the bracket is cos(phi2) k2 z.  */
+    /* It belongs to the ring: batched and served jobs override voltage_V only.        */
+    double voltage2_V;      /* second system's voltage [V]                             */
+    double phi2_rad;        /* its phase at z = 0                                       */
+    int32_t harmonic2;      /* its harmonic number (> 0 when voltage2_V != 0)           */
+    int32_t pad2_;
 } phtl_params;
 
 /* Constants derived in FP64 on the host by phtl_create. */
@@ -114,7 +126,7 @@ typedef struct phtl_derived {
     double A;          /* kick amplitude q V / (beta p0)                           */
     double etaC;       /* eta * C [m]                                              */
     double sin_phis, cos_phis;
-    double K;          /* linear strength eta C A k cos(phi_s)                     */
+    double K;          /* linear strength eta C (A k cos(phi_s) + A2 k2 cos(phi2))  */
     double Qs;         /* sqrt(K) / (2 pi)                                         */
     double bucket_half_length_m; /* pi / k                                        */
     double bucket_half_height;   /* 2 sqrt(A / (k eta C)) (stationary bucket)      */
@@ -138,8 +150,9 @@ typedef struct phtl_handle phtl_handle; /* opaque, library-owned */
 /* Validate the parameters and derive the FP64 constants (Sec. 1.1.2 map, see above).
  * Pure host work: touches no GPU.  *out receives a new handle on PHTL_OK.
  * Errors: PHTL_E_INVALID (null, non-positive C/p0/mass/gamma_t/h/beta, a non-finite
- *         eta1/eta2/xi),
- *         PHTL_E_UNSTABLE (V != 0 and not 0 < K < 4).                               */
+ *         eta1/eta2/xi/voltage2/phi2, voltage2 != 0 with harmonic2 <= 0),
+ *         PHTL_E_UNSTABLE (single RF: V != 0 and not 0 < K < 4; double RF: not
+ *         0 <= K < 4, K = 0 being the flat-bottomed bucket).                          */
 int phtl_create(const phtl_params* params, phtl_handle** out);
 
 /* Stop the server if running, wait for the handle's streams, free everything the
@@ -178,7 +191,7 @@ int phtl_set_tuning(phtl_handle* h, int32_t block_threads, int64_t turns_per_lau
  * both NULL to leave that plane out.  Layout: PHTL_F64 -> n doubles per coordinate;
  * PHTL_F32C / PHTL_F32CD / PHTL_F32CS -> 2n floats per coordinate ([hi | comp]).  Pointers must be
  * aligned to the element size; 16-byte alignment enables 128-bit loads.
- * integrator: PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4.
+ * integrator: PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4 | PHTL_RK4.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Updates the buffers in place.  Errors: PHTL_E_BADHANDLE, PHTL_E_INVALID,
  * PHTL_E_NODEVICE, PHTL_E_CUDA (launch failure).                                   */
@@ -201,6 +214,45 @@ int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* 
                     int64_t n, int64_t turns, int integrator, int dtype, double* mon_rows,
                     int64_t mon_stride);
 
+/* ---- ramp programme (accelerating bucket) ---------------------------------------------- */
+
+/* Attach a machine programme to the handle: the RF voltage voltage_V[n] of every turn
+ * n = 0 .. nturns-1 and the reference momentum p0_eVc[n] at the start of turn n
+ * (nturns + 1 values; p0_eVc[nturns] is the momentum after the last turn).  Host arrays,
+ * read during the call.  The paper's runs change the machine parameters (hollow-bunch
+ * studies); it prints no formulas, so the per-turn reading is:
+ *   - turn n uses beta_n, gamma_n, eta_n from p0_eVc[n] and A_n = q V_n / (beta_n p0_n);
+ *   - a particle gains q V_n sin(phi) / beta_n of momentum per turn (dE = beta c dp) and
+ *     the synchronous one p0[n+1] - p0[n], so sin(phi_s,n) = beta_n (p0[n+1] - p0[n]) /
+ *     (q V_n), phi_s,n on the stable branch (asin above transition, pi - asin below);
+ *   - the turn runs the scheme's stages with eta_n C, A_n and phi_s,n (the synchronous
+ *     particle stays at (0, 0)), then the transverse rotation, then delta, x' and y' are
+ *     re-expressed against the next reference momentum: multiplied by
+ *     r_n = p0[n] / p0[n+1] (for a single kick exactly the momentum bookkeeping
+ *     p0[n] (1 + delta + A (sin phi - sin phi_s)) = p0[n+1] (1 + delta')).
+ * The ring's harmonic, gamma_t, transverse optics and rf_linear flag apply to every turn;
+ * the ring's own voltage_V, phi_s_rad and p0_eVc do not.  The constants of all turns are
+ * derived in FP64 on the host (the long-horizon reference bookkeeping) and kept in a
+ * library-owned device table of 96 bytes per turn (replacing any previous programme; freed
+ * by phtl_destroy or a call with nturns == 0).  Synchronous.
+ * Errors: PHTL_E_BADHANDLE; PHTL_E_INVALID (null arrays with nturns > 0, non-positive or
+ * non-finite momenta, V = 0 on a turn whose momentum changes, a ring with eta1, eta2,
+ * a chromaticity or a second RF system -- the programme runs the linear map only);
+ * PHTL_E_UNSTABLE (|sin phi_s,n| >= 1, or a turn's linear strength outside (0, 4));
+ * PHTL_E_NODEVICE; PHTL_E_NOMEM.                                                          */
+int phtl_set_programme(phtl_handle* h, const double* voltage_V, const double* p0_eVc,
+                       int64_t nturns);
+
+/* Track turns [turn0, turn0 + turns) of the attached programme with the persistent
+ * kernel (turn loop inside the kernel; each turn's constants read from the device table).
+ * Buffers, layout, dtypes, monitor and tuning as phtl_track; integrator PHTL_EULER_CROMER
+ * | PHTL_LEAPFROG | PHTL_RUTH4.  Stream-ordered.  Splitting a range into consecutive calls
+ * gives bitwise the same particles.  Errors: as phtl_track, plus PHTL_E_INVALID (no
+ * programme, a programme set on another device, turn0 + turns beyond it, PHTL_RK4).     */
+int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                         int64_t n, int64_t turn0, int64_t turns, int integrator, int dtype,
+                         void* cuda_stream);
+
 /* ---- batched launch (many independent bunches in one graph-captured launch) ------------ */
 
 /* One bunch of a batch.  Particles are independent and turns sequential (Sec. 2.3), so
@@ -216,7 +268,7 @@ typedef struct phtl_job {
     int64_t n;            /* macro-particles                                               */
     int64_t turns;        /* turns tracked by each run of the batch                        */
     double voltage_V;     /* RF voltage of this bunch                                      */
-    int32_t integrator;   /* PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4                 */
+    int32_t integrator;   /* PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4 | PHTL_RK4      */
     int32_t dtype;        /* PHTL_F64 | PHTL_F32C | PHTL_F32CD | PHTL_F32CS                 */
 } phtl_job;
 

@@ -49,15 +49,17 @@ void scheme_consts(const phtl_derived& d, int scheme, MapConsts& c)
     for (int j = 0; j < 3; ++j) split_df(c.kw[j], c.kw_hi[j], c.kw_lo[j]);
 }
 
-int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
+int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[4])
 {
     if (!finite_pos(p.circumference_m) || !finite_pos(p.gamma_t) || !finite_pos(p.p0_eVc) ||
         !finite_pos(p.mass_eV) || !finite_pos(p.beta_x_m) || !finite_pos(p.beta_y_m) ||
         p.harmonic <= 0 || !std::isfinite(p.charge_e) || !std::isfinite(p.voltage_V) ||
         !std::isfinite(p.phi_s_rad) || !std::isfinite(p.Qx) || !std::isfinite(p.Qy) ||
         !std::isfinite(p.eta1) || !std::isfinite(p.eta2) || !std::isfinite(p.xi_x) ||
-        !std::isfinite(p.xi_y))
+        !std::isfinite(p.xi_y) || !std::isfinite(p.voltage2_V) || !std::isfinite(p.phi2_rad))
         return PHTL_E_INVALID;
+    const bool dual = p.voltage2_V != 0.0;
+    if (dual && p.harmonic2 <= 0) return PHTL_E_INVALID;
     std::memset(&d, 0, sizeof(d));
     d.betagamma = p.p0_eVc / p.mass_eV;
     d.gamma = std::sqrt(1.0 + d.betagamma * d.betagamma);
@@ -68,7 +70,11 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
     d.etaC = d.eta * p.circumference_m;
     d.sin_phis = std::sin(p.phi_s_rad);
     d.cos_phis = std::cos(p.phi_s_rad);
-    d.K = d.etaC * d.A * d.k * d.cos_phis;
+    // second RF system (double RF): k2 = 2 pi h2 / C, A2 = q V2 / (beta p0)
+    const double k2 = dual ? 2.0 * kPi * static_cast<double>(p.harmonic2) / p.circumference_m : 0.0;
+    const double A2 = dual ? kick_amplitude(p, d, p.voltage2_V) : 0.0;
+    const double cos_phi2 = dual ? std::cos(p.phi2_rad) : 0.0;
+    d.K = d.etaC * (d.A * d.k * d.cos_phis + A2 * k2 * cos_phi2);
     d.Qs = d.K > 0.0 ? std::sqrt(d.K) / (2.0 * kPi) : 0.0;
     d.bucket_half_length_m = kPi / d.k;
     const double r = d.A / (d.k * d.etaC);
@@ -83,9 +89,12 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
     d.my[1] = p.beta_y_m * std::sin(muy);
     d.my[2] = -std::sin(muy) / p.beta_y_m;
     d.my[3] = std::cos(muy);
-    if (p.voltage_V != 0.0 && !(d.K > 0.0 && d.K < 4.0)) return PHTL_E_UNSTABLE;
+    // the linearised motion must oscillate (0 < K < 4); with a second RF system the
+    // flat-bottomed bucket K = 0 is allowed too
+    if (!dual && p.voltage_V != 0.0 && !(d.K > 0.0 && d.K < 4.0)) return PHTL_E_UNSTABLE;
+    if (dual && !(d.K >= 0.0 && d.K < 4.0)) return PHTL_E_UNSTABLE;
 
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < 4; ++s) {
         MapConsts& c = mc[s];
         std::memset(&c, 0, sizeof(c));
         scheme_consts(d, s, c);
@@ -121,7 +130,24 @@ int derive(const phtl_params& p, phtl_derived& d, MapConsts (&mc)[3])
         c.iby = 1.0 / p.beta_y_m;
         c.chroma_x = p.xi_x != 0.0 ? 1 : 0;
         c.chroma_y = p.xi_y != 0.0 ? 1 : 0;
-        c.general = (p.eta1 != 0.0 || p.eta2 != 0.0 || c.chroma_x || c.chroma_y) ? 1 : 0;
+        // second RF system
+        c.dual_rf = dual ? 1 : 0;
+        if (dual) {
+            double dc2[4];
+            scheme_weights(s, A2, d.etaC, dc2, c.kw2);
+            c.k2 = k2;
+            c.phi2 = p.phi2_rad;
+            c.sinphi2 = std::sin(p.phi2_rad);
+            c.lin2 = cos_phi2 * k2;
+        }
+        for (int j = 0; j < 3; ++j) split_df(c.kw2[j], c.kw2_hi[j], c.kw2_lo[j]);
+        split_df(c.k2, c.k2_hi, c.k2_lo);
+        split_df(c.phi2, c.phi2_hi, c.phi2_lo);
+        split_df(c.sinphi2, c.sinphi2_hi, c.sinphi2_lo);
+        split_df(c.lin2, c.lin2_hi, c.lin2_lo);
+        // the widened map's kernels: eta(delta), chromaticity, double RF, and RK4
+        c.general = (p.eta1 != 0.0 || p.eta2 != 0.0 || c.chroma_x || c.chroma_y || dual ||
+                     s == PHTL_RK4) ? 1 : 0;
         split_df(c.eta1C, c.eta1C_hi, c.eta1C_lo);
         split_df(c.eta2C, c.eta2C_hi, c.eta2C_lo);
         split_df(c.qx, c.qx_hi, c.qx_lo);
@@ -151,6 +177,10 @@ void scheme_weights(int scheme, double A, double etaC, double (&dc)[4], double (
         dc[0] = 0.5 * etaC;
         kw[0] = 1.0 * A;
         dc[1] = 0.5 * etaC;
+    } else if (scheme == PHTL_RK4) {
+        // classic RK4: the right-hand side uses eta C and A themselves
+        dc[0] = etaC;
+        kw[0] = A;
     } else {
         // Forest-Ruth: theta = 1 / (2 - 2^(1/3))
         const double th = 1.0 / (2.0 - std::cbrt(2.0));
@@ -169,6 +199,30 @@ double kick_amplitude(const phtl_params& p, const phtl_derived& d, double voltag
     return p.charge_e * voltage_V / (d.beta * p.p0_eVc);
 }
 
+void job_weights(const phtl_handle* h, int scheme, double voltage_V, JobDesc& J)
+{
+    const phtl_derived& d = h->derived;
+    scheme_weights(scheme, kick_amplitude(h->params, d, voltage_V), d.etaC, J.dc, J.kw);
+    for (int j = 0; j < 3; ++j) J.kw2[j] = h->mc[scheme].kw2[j];
+    fill_float_weights(J);
+}
+
+MapConsts batch_consts(const phtl_handle* h, bool has_rk4)
+{
+    MapConsts c = h->mc[0];
+    if (has_rk4) c.general = 1;
+    return c;
+}
+
+int voltage_check(const phtl_handle* h, double voltage_V)
+{
+    const phtl_derived& d = h->derived;
+    const double K = d.etaC * kick_amplitude(h->params, d, voltage_V) * d.k * d.cos_phis + h->K2;
+    if (h->mc[0].dual_rf) return K >= 0.0 && K < 4.0 ? PHTL_OK : PHTL_E_UNSTABLE;
+    if (voltage_V != 0.0 && !(K > 0.0 && K < 4.0)) return PHTL_E_UNSTABLE;
+    return PHTL_OK;
+}
+
 int handle_stream(phtl_handle* h, cudaStream_t* out)
 {
     if (!h->stream) {
@@ -182,9 +236,26 @@ int handle_stream(phtl_handle* h, cudaStream_t* out)
     return PHTL_OK;
 }
 
+void free_programme(phtl_handle* h)
+{
+    if (h->ramp) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (h->ramp_device >= 0 && cur != h->ramp_device) cudaSetDevice(h->ramp_device);
+        cudaDeviceSynchronize();
+        cudaFree(h->ramp);
+        if (cur >= 0 && cur != h->ramp_device) cudaSetDevice(cur);
+        h->ramp = nullptr;
+    }
+    h->ramp_turns = 0;
+    h->ramp_device = -1;
+    cudaGetLastError();
+}
+
 void release_handle_resources(phtl_handle* h)
 {
     stop_server(h);
+    free_programme(h);
     if (h->stream) {
         cudaStreamSynchronize(h->stream);
         cudaStreamDestroy(h->stream);
@@ -226,7 +297,7 @@ int ensure_device(phtl_handle* h)
 int64_t auto_turns_per_launch(int dtype, int scheme, int64_t n)
 {
     const double budget = dtype == PHTL_F64 ? 8e8 : 8e9;
-    const double w = scheme == PHTL_RUTH4 ? 3.0 : 1.0;
+    const double w = scheme == PHTL_RUTH4 ? 3.0 : scheme == PHTL_RK4 ? 4.0 : 1.0;
     double t = budget / (w * static_cast<double>(std::max<int64_t>(n, 1)));
     t = std::min(t, 1048576.0);
     return std::max<int64_t>(1, static_cast<int64_t>(t));
@@ -258,7 +329,7 @@ int check_track_args(const phtl_handle* h, void* const* c, int64_t n, int64_t tu
                      int integrator, int dtype)
 {
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
-    if (integrator < PHTL_EULER_CROMER || integrator > PHTL_RUTH4) return PHTL_E_INVALID;
+    if (integrator < PHTL_EULER_CROMER || integrator > PHTL_RK4) return PHTL_E_INVALID;
     if (dtype < PHTL_F64 || dtype > PHTL_F32CS) return PHTL_E_INVALID;
     if (n < 0 || turns < 0) return PHTL_E_INVALID;
     if (n > 0 && (!c[0] || !c[1])) return PHTL_E_INVALID;
@@ -367,6 +438,45 @@ int track_common(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, 
                          perturn, h->mon_rows, h->mon_cap, h->mon_stride);
 }
 
+// Per-turn constants of a ramp programme in FP64 (the reading stated at
+// phtl_set_programme in phtl.h), with their double-float splits.
+int derive_programme(const phtl_params& p, const double* V, const double* p0, int64_t nturns,
+                     RampTurn* out)
+{
+    const double k = 2.0 * kPi * static_cast<double>(p.harmonic) / p.circumference_m;
+    for (int64_t t = 0; t < nturns; ++t) {
+        const double pa = p0[t], pb = p0[t + 1];
+        if (!finite_pos(pa) || !finite_pos(pb) || !std::isfinite(V[t])) return PHTL_E_INVALID;
+        const double bg = pa / p.mass_eV;
+        const double g = std::sqrt(1.0 + bg * bg);
+        const double b = bg / g;
+        const double eta = 1.0 / (p.gamma_t * p.gamma_t) - 1.0 / (g * g);
+        RampTurn& T = out[t];
+        std::memset(&T, 0, sizeof(T));
+        T.etaC = eta * p.circumference_m;
+        T.A = p.charge_e * V[t] / (b * pa);
+        if (V[t] == 0.0) {
+            if (pb != pa) return PHTL_E_INVALID;
+        } else {
+            const double x = b * (pb - pa) / (p.charge_e * V[t]);
+            if (!(std::fabs(x) < 1.0)) return PHTL_E_UNSTABLE;
+            T.phis = eta > 0.0 ? std::asin(x) : kPi - std::asin(x);
+            T.sinphis = std::sin(T.phis);
+            const double K = T.etaC * T.A * k * std::cos(T.phis);
+            if (!(K > 0.0 && K < 4.0)) return PHTL_E_UNSTABLE;
+        }
+        T.lin = std::cos(T.phis) * k;
+        T.r = pa / pb;
+        split_df(T.etaC, T.etaC_h, T.etaC_l);
+        split_df(T.A, T.A_h, T.A_l);
+        split_df(T.phis, T.phis_h, T.phis_l);
+        split_df(T.sinphis, T.sinphis_h, T.sinphis_l);
+        split_df(T.lin, T.lin_h, T.lin_l);
+        split_df(T.r, T.r_h, T.r_l);
+    }
+    return PHTL_OK;
+}
+
 }  // namespace phtl
 
 using namespace phtl;
@@ -385,6 +495,8 @@ int phtl_create(const phtl_params* params, phtl_handle** out)
         delete h;
         return rc;
     }
+    // RK4's kw2[0] is A2 itself; lin2 = cos(phi2) k2
+    h->K2 = h->derived.etaC * h->mc[PHTL_RK4].kw2[0] * h->mc[PHTL_RK4].lin2;
     {
         std::lock_guard<std::mutex> g(g_registry_mu);
         g_registry.insert(h);
@@ -527,6 +639,134 @@ int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* 
     cudaGetLastError();
     cleanup();
     return rc;
+}
+
+int phtl_set_programme(phtl_handle* h, const double* voltage_V, const double* p0_eVc,
+                       int64_t nturns)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (nturns < 0 || (nturns > 0 && (!voltage_V || !p0_eVc))) return PHTL_E_INVALID;
+    if (nturns > (int64_t(1) << 32)) return PHTL_E_INVALID;
+    if (nturns == 0) {
+        free_programme(h);
+        return PHTL_OK;
+    }
+    const phtl_params& p = h->params;
+    if (p.eta1 != 0.0 || p.eta2 != 0.0 || p.xi_x != 0.0 || p.xi_y != 0.0 || p.voltage2_V != 0.0)
+        return PHTL_E_INVALID;  // the programme runs the linear map only
+    RampTurn* host = nullptr;
+    if (cudaMallocHost(reinterpret_cast<void**>(&host), sizeof(RampTurn) * nturns) != cudaSuccess) {
+        cudaGetLastError();
+        // no device (or no pinned memory): validate on the heap so argument errors still
+        // come first, then report the missing device
+        RampTurn* tmp = new (std::nothrow) RampTurn[static_cast<size_t>(std::min<int64_t>(nturns, 1 << 20))];
+        int rc = PHTL_E_NOMEM;
+        if (tmp) {
+            rc = PHTL_OK;
+            for (int64_t t0 = 0; t0 < nturns && rc == PHTL_OK; t0 += 1 << 20) {
+                const int64_t cnt = std::min<int64_t>(1 << 20, nturns - t0);
+                rc = derive_programme(p, voltage_V + t0, p0_eVc + t0, cnt, tmp);
+            }
+            delete[] tmp;
+        }
+        if (rc != PHTL_OK) return rc;
+        rc = ensure_device(h);
+        return rc != PHTL_OK ? rc : PHTL_E_NOMEM;
+    }
+    int rc = derive_programme(p, voltage_V, p0_eVc, nturns, host);
+    if (rc == PHTL_OK) rc = ensure_device(h);
+    if (rc == PHTL_OK) {
+        free_programme(h);
+        if (cudaMalloc(reinterpret_cast<void**>(&h->ramp), sizeof(RampTurn) * nturns) != cudaSuccess) {
+            cudaGetLastError();
+            h->ramp = nullptr;
+            rc = PHTL_E_NOMEM;
+        } else if (cudaMemcpy(h->ramp, host, sizeof(RampTurn) * nturns, cudaMemcpyHostToDevice) !=
+                   cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->ramp);
+            h->ramp = nullptr;
+            rc = PHTL_E_CUDA;
+        } else {
+            h->ramp_turns = nturns;
+            h->ramp_device = h->device;
+        }
+    }
+    cudaFreeHost(host);
+    return rc;
+}
+
+int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                         int64_t n, int64_t turn0, int64_t turns, int integrator, int dtype,
+                         void* cuda_stream)
+{
+    void* c[6] = {z, dp, x, xp, y, yp};
+    int rc = check_track_args(h, c, n, turns, integrator, dtype);
+    if (rc != PHTL_OK) return rc;
+    if (integrator == PHTL_RK4) return PHTL_E_INVALID;
+    if (turn0 < 0 || turns > h->ramp_turns - turn0) return PHTL_E_INVALID;
+    rc = ensure_device(h);
+    if (rc != PHTL_OK) return rc;
+    if (!h->ramp || h->ramp_device != h->device) return PHTL_E_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double* mon_rows = h->mon_rows;
+    if (mon_rows) {
+        const int64_t nrows = turns / h->mon_stride + 1;
+        if (nrows > h->mon_cap) return PHTL_E_INVALID;
+        if (cudaMemsetAsync(mon_rows, 0, static_cast<size_t>(nrows) * PHTL_MON_FIELDS * sizeof(double),
+                            s) != cudaSuccess) {
+            cudaGetLastError();
+            return PHTL_E_CUDA;
+        }
+    }
+    if (n == 0 || (turns == 0 && !mon_rows)) return PHTL_OK;
+    const int block = h->block > 0 ? h->block : 128;
+    const int ppt = particles_per_thread(dtype);
+    int64_t tpl = h->tpl > 0 ? h->tpl : auto_turns_per_launch(dtype, integrator, n);
+    tpl = std::min<int64_t>(tpl, 1 << 30);
+    bool vec = true;
+    for (int i = 0; i < 6; ++i)
+        if (c[i] && (reinterpret_cast<uintptr_t>(c[i]) % 16) != 0) vec = false;
+    if (dtype != PHTL_F64 && (n * 4) % 16 != 0) vec = false;
+    const int occ = occupancy_ramp(integrator, dtype, block);
+    if (occ <= 0) return PHTL_E_INVALID;
+    const int64_t chunk = static_cast<int64_t>(block) * ppt;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    int64_t cap = static_cast<int64_t>(occ) * h->nsm;
+    if (h->max_blocks > 0) cap = std::min<int64_t>(cap, h->max_blocks);
+    LaunchDesc L;
+    std::memset(&L, 0, sizeof(L));
+    for (int i = 0; i < 6; ++i) L.c[i] = c[i];
+    L.n = n;
+    L.scheme = integrator;
+    L.block = block;
+    L.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nchunks, cap)));
+    L.vec = vec ? 1 : 0;
+    int64_t t0 = 0;
+    bool first = true;
+    do {
+        const int64_t nt = std::min<int64_t>(tpl, turns - t0);
+        L.nturns = static_cast<int32_t>(nt);
+        MonitorArgs m;
+        std::memset(&m, 0, sizeof(m));
+        if (mon_rows) {
+            m.rows = mon_rows;
+            m.stride = h->mon_stride;
+            m.until = h->mon_stride - (t0 % h->mon_stride);
+            m.row = t0 / h->mon_stride + 1;
+            m.initial = first ? 1 : 0;
+        }
+        if (launch_ramp(L, h->mc[integrator], m, h->ramp, turn0 + t0, dtype, s) != cudaSuccess) {
+            cudaGetLastError();
+            return PHTL_E_CUDA;
+        }
+        t0 += nt;
+        first = false;
+        ++h->stats.launches;
+    } while (t0 < turns);
+    h->stats.particle_turns += n * turns;
+    ++h->stats.calls;
+    return PHTL_OK;
 }
 
 int phtl_get_stats(const phtl_handle* h, phtl_stats* out)

@@ -67,8 +67,7 @@ double probe_rate(phtl_handle* h, int dtype, int scheme, int block, int64_t m, i
                              reinterpret_cast<uintptr_t>(J.c[1]) % 16 == 0 &&
                              (dtype == PHTL_F64 || (m * 4) % 16 == 0);
         J.vec = aligned ? 1 : 0;
-        scheme_weights(scheme, h->derived.A, h->derived.etaC, J.dc, J.kw);
-        fill_float_weights(J);
+        job_weights(h, scheme, h->params.voltage_V, J);
         if (cudaMalloc(reinterpret_cast<void**>(&dj), sizeof(JobDesc)) != cudaSuccess) break;
         if (cudaMemcpyAsync(dj, &J, sizeof(J), cudaMemcpyHostToDevice, s) != cudaSuccess) break;
         const int ppt = particles_per_thread(dtype);
@@ -115,7 +114,7 @@ int autotune(phtl_handle* h, int dtype, int scheme, int64_t active, double targe
     int best_block = 0;
     double best_rate = 0.0;
     for (int b : candidates) {
-        const int occ = occupancy_batched(dtype, false, b, h->mc[0].general != 0);
+        const int occ = occupancy_batched(dtype, false, b, h->mc[scheme].general != 0);
         if (occ <= 0) continue;
         const int64_t cap = static_cast<int64_t>(occ) * h->nsm * b * ppt;  // one full wave
         const int64_t m = std::max<int64_t>(std::min<int64_t>(std::max<int64_t>(active, 1), cap), b * ppt);
@@ -151,6 +150,7 @@ struct phtl_batch {
         phtl::JobDesc* d_jobs = nullptr;
         int64_t tiles = 0;
         double rate = 0.0;
+        bool rk4 = false;                   // a job uses RK4: the widened map's kernels
     };
     std::vector<Group> groups;
     cudaStream_t cap_stream = nullptr;
@@ -194,7 +194,7 @@ int enqueue_batch(phtl_batch* b, cudaStream_t s, int64_t* launches)
             const int32_t T = static_cast<int32_t>(std::min<int64_t>(G.T, std::max<int64_t>(max_turns - t0, 0)));
             if (grid > 0) {
                 int rc = check_cuda(launch_batched(G.d_jobs, static_cast<int32_t>(G.jobs.size()),
-                                                   b->h->mc[0], G.dtype, G.mon, t0, T,
+                                                   batch_consts(b->h, G.rk4), G.dtype, G.mon, t0, T,
                                                    static_cast<int>(grid), G.block, s));
                 if (rc != PHTL_OK) return rc;
                 ++nl;
@@ -217,7 +217,7 @@ int phtl_autotune(phtl_handle* h, int dtype, int integrator, int64_t active_part
                   double target_launch_ms, phtl_tuning* out)
 {
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
-    if (!out || dtype < PHTL_F64 || dtype > PHTL_F32CS || integrator < 0 || integrator > 2 ||
+    if (!out || dtype < PHTL_F64 || dtype > PHTL_F32CS || integrator < 0 || integrator > PHTL_RK4 ||
         active_particles < 0 || !(target_launch_ms > 0.0))
         return PHTL_E_INVALID;
     return autotune(h, dtype, integrator, active_particles, target_launch_ms, out);
@@ -229,7 +229,6 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
     if (!out || njobs < 0 || (njobs > 0 && !jobs)) return PHTL_E_INVALID;
     *out = nullptr;
-    const phtl_derived& d = h->derived;
     // validate every job first
     for (int32_t i = 0; i < njobs; ++i) {
         const phtl_job& J = jobs[i];
@@ -240,9 +239,7 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
             if (J.mon_stride < 1 || J.turns / J.mon_stride + 1 > J.mon_capacity) return PHTL_E_INVALID;
             if (reinterpret_cast<uintptr_t>(J.mon_rows) % 8) return PHTL_E_INVALID;
         }
-        const double A = kick_amplitude(h->params, d, J.voltage_V);
-        const double K = d.etaC * A * d.k * d.cos_phis;
-        if (J.voltage_V != 0.0 && !(K > 0.0 && K < 4.0)) return PHTL_E_UNSTABLE;
+        if (voltage_check(h, J.voltage_V) != PHTL_OK) return PHTL_E_UNSTABLE;
         if (J.turns > (int64_t(1) << 40)) return PHTL_E_INVALID;
     }
     int rc = ensure_device(h);
@@ -264,14 +261,15 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
         phtl_batch::Group G;
         G.dtype = dt;
         int64_t active = 0, pt = 0;
-        int counts[3] = {0, 0, 0};
+        int counts[4] = {0, 0, 0, 0};
         for (int32_t i : idx) {
             active += jobs[i].n;
             pt += jobs[i].n * jobs[i].turns;
             counts[jobs[i].integrator]++;
             G.mon = G.mon || jobs[i].mon_rows != nullptr;
         }
-        const int dominant = static_cast<int>(std::max_element(counts, counts + 3) - counts);
+        G.rk4 = counts[PHTL_RK4] > 0;
+        const int dominant = static_cast<int>(std::max_element(counts, counts + 4) - counts);
         if (h->block > 0 && h->tpl > 0) {
             G.block = h->block;
             G.T = h->tpl;
@@ -286,7 +284,7 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
             G.T = h->tpl > 0 ? h->tpl : t.turns_per_launch;
             G.rate = t.particle_turns_per_s;
         }
-        if (occupancy_batched(dt, G.mon, G.block, h->mc[0].general != 0) <= 0) {
+        if (occupancy_batched(dt, G.mon, G.block, batch_consts(h, G.rk4).general != 0) <= 0) {
             delete b;
             return PHTL_E_INVALID;
         }
@@ -309,8 +307,7 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
             J.turns = U.turns;
             J.scheme = U.integrator;
             J.tile_begin = tiles;
-            scheme_weights(U.integrator, kick_amplitude(h->params, d, U.voltage_V), d.etaC, J.dc, J.kw);
-            fill_float_weights(J);
+            job_weights(h, U.integrator, U.voltage_V, J);
             tiles += (U.n + per_tile - 1) / per_tile;
             G.jobs.push_back(J);
             G.mon_bytes.push_back(U.mon_rows ? (U.turns / U.mon_stride + 1) * PHTL_MON_FIELDS * 8 : 0);

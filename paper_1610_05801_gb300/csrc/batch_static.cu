@@ -70,7 +70,6 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
     if (njobs < 0 || (njobs > 0 && !jobs)) return PHTL_E_INVALID;
     if (njobs > PHTL_NOALLOC_MAX_JOBS) return PHTL_E_TOOBIG;
-    const phtl_derived& d = h->derived;
     for (int32_t i = 0; i < njobs; ++i) {
         const phtl_job& J = jobs[i];
         int rc = check_track_args(h, J.c, J.n, J.turns, J.integrator, J.dtype);
@@ -80,8 +79,7 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
             if (J.mon_stride < 1 || J.turns / J.mon_stride + 1 > J.mon_capacity) return PHTL_E_INVALID;
             if (reinterpret_cast<uintptr_t>(J.mon_rows) % 8) return PHTL_E_INVALID;
         }
-        const double K = d.etaC * kick_amplitude(h->params, d, J.voltage_V) * d.k * d.cos_phis;
-        if (J.voltage_V != 0.0 && !(K > 0.0 && K < 4.0)) return PHTL_E_UNSTABLE;
+        if (voltage_check(h, J.voltage_V) != PHTL_OK) return PHTL_E_UNSTABLE;
         if (J.turns > (int64_t(1) << 40)) return PHTL_E_INVALID;
     }
     int rc = ensure_device(h);
@@ -104,13 +102,15 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
         std::stable_sort(order, order + cnt,
                          [&](int32_t a, int32_t b) { return jobs[a].turns > jobs[b].turns; });
         int64_t active = 0;
-        bool mon = false;
+        bool mon = false, rk4 = false;
         for (int32_t k = 0; k < cnt; ++k) {
             active += jobs[order[k]].n;
             mon = mon || jobs[order[k]].mon_rows != nullptr;
+            rk4 = rk4 || jobs[order[k]].integrator == PHTL_RK4;
         }
+        const MapConsts mc = batch_consts(h, rk4);
         const int block = h->block > 0 ? h->block : 128;
-        if (occupancy_batched(dt, mon, block, h->mc[0].general != 0) <= 0) return PHTL_E_INVALID;
+        if (occupancy_batched(dt, mon, block, mc.general != 0) <= 0) return PHTL_E_INVALID;
         const int64_t T = h->tpl > 0 ? h->tpl : auto_turns_per_launch(dt, jobs[order[0]].integrator, active);
         const int64_t per_tile = static_cast<int64_t>(block) * particles_per_thread(dt);
         JobDesc* G = host + used;
@@ -132,8 +132,7 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
             J.turns = U.turns;
             J.scheme = U.integrator;
             J.tile_begin = tiles;
-            scheme_weights(U.integrator, kick_amplitude(h->params, d, U.voltage_V), d.etaC, J.dc, J.kw);
-            fill_float_weights(J);
+            job_weights(h, U.integrator, U.voltage_V, J);
             tiles += (U.n + per_tile - 1) / per_tile;
             if (U.mon_rows) {
                 rc = cuda_rc(cudaMemsetAsync(U.mon_rows, 0,
@@ -156,7 +155,7 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
             const int64_t grid = k == cnt ? tiles : G[k].tile_begin;
             const int32_t nt = static_cast<int32_t>(std::min<int64_t>(T, std::max<int64_t>(max_turns - t0, 0)));
             if (grid > 0) {
-                rc = cuda_rc(launch_batched(table + used, cnt, h->mc[0], dt, mon, t0, nt,
+                rc = cuda_rc(launch_batched(table + used, cnt, mc, dt, mon, t0, nt,
                                             static_cast<int>(grid), block, s));
                 if (rc != PHTL_OK) return rc;
                 ++nl;

@@ -20,7 +20,8 @@ struct phtl_handle {
     uint64_t magic = phtl::kHandleMagic;
     phtl_params params{};
     phtl_derived derived{};
-    phtl::MapConsts mc[3]{};  // per integrator
+    phtl::MapConsts mc[4]{};  // per integrator
+    double K2 = 0.0;          // linear strength of the second RF system, eta C A2 k2 cos(phi2)
     // monitor attached by phtl_set_monitor
     double* mon_rows = nullptr;
     int64_t mon_cap = 0;
@@ -35,6 +36,10 @@ struct phtl_handle {
     int nsm = 0;
     cudaStream_t stream = nullptr;  // library-owned stream for the host-buffer path
     phtl::Server* server = nullptr;
+    // ramp programme (phtl_set_programme): per-turn table on device ramp_device
+    phtl::RampTurn* ramp = nullptr;
+    int64_t ramp_turns = 0;
+    int ramp_device = -1;
     phtl_stats stats{};
 };
 
@@ -53,5 +58,14 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
 int64_t auto_turns_per_launch(int dtype, int scheme, int64_t n);
 void scheme_weights(int scheme, double A, double etaC, double (&dc)[4], double (&kw)[3]);
 double kick_amplitude(const phtl_params& p, const phtl_derived& d, double voltage_V);
+// A batched job's stage weights: its scheme's drift weights, kick weights for its own
+// voltage, and the ring's second RF system (FP64 and the FP32 splits).
+void job_weights(const phtl_handle* h, int scheme, double voltage_V, JobDesc& J);
+// MapConsts of a batched launch: the handle's, with the widened map's kernels forced
+// when a job of the group uses RK4 (only those kernels hold it).
+MapConsts batch_consts(const phtl_handle* h, bool has_rk4);
+// PHTL_OK if a job's own voltage gives a stable bucket with the ring's second RF system
+// (the rule of phtl_create), else PHTL_E_UNSTABLE.
+int voltage_check(const phtl_handle* h, double voltage_V);
 
 }  // namespace phtl

@@ -49,17 +49,50 @@ struct MapConsts {
     float eta1C_hi, eta1C_lo, eta2C_hi, eta2C_lo;
     float qx_hi, qx_lo, qy_hi, qy_lo, xi_x_hi, xi_x_lo, xi_y_hi, xi_y_lo;
     float bx_hi, bx_lo, by_hi, by_lo, ibx_hi, ibx_lo, iby_hi, iby_lo;
+    // second RF system (double RF): stage j adds kw2[j] * (sin(phi2 + k2 z) - sin(phi2)),
+    // kw2[j] = w_j * A2 (lin2 z in rf_linear mode)
+    int32_t dual_rf;
+    int32_t pad3_;
+    double kw2[3];
+    double k2, phi2, sinphi2, lin2;
+    float kw2_hi[3], kw2_lo[3];
+    float k2_hi, k2_lo, phi2_hi, phi2_lo, sinphi2_hi, sinphi2_lo, lin2_hi, lin2_lo;
 };
 
 // Drift stage weights w_i of each scheme (the drift of stage i is w_i eta(d) C d); the
-// Ruth4 values are theta/2 and (1 - theta)/2 with theta = 1/(2 - 2^(1/3)).
+// Ruth4 values are theta/2 and (1 - theta)/2 with theta = 1/(2 - 2^(1/3)).  RK4 has one
+// "stage" of weight 1: its right-hand side uses eta(d) C itself.
 __host__ __device__ constexpr double drift_weight(int scheme, int i)
 {
     return scheme == PHTL_EULER_CROMER ? (i == 0 ? 1.0 : 0.0)
          : scheme == PHTL_LEAPFROG     ? (i < 2 ? 0.5 : 0.0)
+         : scheme == PHTL_RK4          ? (i == 0 ? 1.0 : 0.0)
          : (i == 0 || i == 3)          ? 0.6756035959798289
                                        : -0.17560359597982889;
 }
+
+// Kick stage weights w_j of each scheme (the kick of stage j is w_j A (sin phi - sin phi_s));
+// the Ruth4 values are theta, 1 - 2 theta, theta with theta = 1/(2 - 2^(1/3)).
+__host__ __device__ constexpr double kick_weight(int scheme, int j)
+{
+    return scheme != PHTL_RUTH4 ? (j == 0 ? 1.0 : 0.0)
+         : j == 1               ? -1.7024143839193155
+                                : 1.3512071919596578;
+}
+
+// One turn of a ramp programme (an accelerating bucket: the reference momentum and the RF
+// voltage change from turn to turn), derived in FP64 on the host by phtl_set_programme.
+struct RampTurn {
+    double etaC;     // eta_n C
+    double A;        // q V_n / (beta_n p0_n)
+    double phis;     // phi_s,n
+    double sinphis;  // sin(phi_s,n)
+    double lin;      // cos(phi_s,n) k (rf_linear mode)
+    double r;        // p0_n / p0_{n+1}: delta and the slopes are re-expressed after the turn
+    // double-float copies for the FP32 paths (value = hi + lo)
+    float etaC_h, etaC_l, A_h, A_l, phis_h, phis_l, sinphis_h, sinphis_l, lin_h, lin_l, r_h, r_l;
+};
+static_assert(sizeof(RampTurn) == 96, "RampTurn is 96 bytes");
 
 // Where and when a launch records monitor rows.
 struct MonitorArgs {
@@ -102,6 +135,9 @@ struct JobDesc {
     float dc_lo[4];
     float kw_hi[3];
     float kw_lo[3];
+    double kw2[3];       // second RF system's kick weights w_j * A2 (the ring's, not per job)
+    float kw2_hi[3];
+    float kw2_lo[3];
     int32_t scheme;      // integrator
     int32_t vec;         // nonzero: 16-byte aligned buffers (128-bit loads)
     int32_t pad_;
@@ -117,6 +153,8 @@ inline void fill_float_weights(JobDesc& J)
     for (int i = 0; i < 3; ++i) {
         J.kw_hi[i] = static_cast<float>(J.kw[i]);
         J.kw_lo[i] = static_cast<float>(J.kw[i] - static_cast<double>(J.kw_hi[i]));
+        J.kw2_hi[i] = static_cast<float>(J.kw2[i]);
+        J.kw2_lo[i] = static_cast<float>(J.kw2[i] - static_cast<double>(J.kw2_hi[i]));
     }
 }
 
@@ -141,8 +179,16 @@ int occupancy_f64(int scheme, bool trans, bool mon, int block, bool general);
 int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, bool general);
 int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, bool general);
 
+// Ramp programme kernels (track_ramp.cu): turns [turn0, turn0 + L.nturns) of the
+// programme table prog (device memory), linear map only.
+cudaError_t launch_ramp(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,
+                        const RampTurn* prog, int64_t turn0, int dtype, cudaStream_t s);
+int occupancy_ramp(int scheme, int dtype, int block);
+
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).
 const void* general_kernel_single(int scheme, int dtype);
+const void* general_kernel_single_rk4(int dtype);  // track_general_rk4.cu
 const void* general_kernel_batched(int dtype);
+const void* general_kernel_batched_f32(int dtype);  // PHTL_F32CD, PHTL_F32CS
 
 }  // namespace phtl

@@ -52,7 +52,7 @@ __device__ __forceinline__ void run_f64_zs(double (&z)[f64::P], double (&d)[f64:
     if (GEN) f64::slip_stages<SCHEME>(c, g1, g2);
     for (int t = 0; t < nt; ++t) {
         if (GEN) {
-            f64::long_turn_nl<SCHEME, ZS>(z, d, c, J.dc, J.kw, g1, g2);
+            f64::long_turn_nl<SCHEME, ZS>(z, d, c, J.dc, J.kw, J.kw2, g1, g2);
             f64::transverse_gen(x, xp, y, yp, d, hx, hy, c);
         } else {
             f64::long_turn<SCHEME, ZS>(z, d, c, J.dc, J.kw);
@@ -132,15 +132,19 @@ __global__ void __launch_bounds__(256, f64::kBatchedMinBlocks256) k_batched_f64(
             run_f64<PHTL_EULER_CROMER, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
         else if (J.scheme == PHTL_LEAPFROG)
             run_f64<PHTL_LEAPFROG, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
-        else
+        else if (!GEN || J.scheme == PHTL_RUTH4)
             run_f64<PHTL_RUTH4, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
+        else if constexpr (GEN)  // RK4 lives in the widened map's kernels only
+            run_f64<PHTL_RK4, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
     } else {
         if (J.scheme == PHTL_EULER_CROMER)
             run_f64<PHTL_EULER_CROMER, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
         else if (J.scheme == PHTL_LEAPFROG)
             run_f64<PHTL_LEAPFROG, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
-        else
+        else if (!GEN || J.scheme == PHTL_RUTH4)
             run_f64<PHTL_RUTH4, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
+        else if constexpr (GEN)  // RK4 lives in the widened map's kernels only
+            run_f64<PHTL_RK4, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
     }
     store2(gz, base, J.n, vec, z);
     store2(gd, base, J.n, vec, d);
@@ -171,8 +175,8 @@ __device__ __forceinline__ void run_f32c_zs(f32c::DF (&z)[f32c::P], f32c::DF (&d
     if (GEN) slip_stages<SCHEME>(c, g1h, g1l, g2h, g2l);
     for (int t = 0; t < nt; ++t) {
         if (GEN) {
-            long_turn_nl<SCHEME, DT, ZS>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo, g1h, g1l,
-                                         g2h, g2l);
+            long_turn_nl<SCHEME, DT, ZS>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo, J.kw2_hi,
+                                         J.kw2_lo, g1h, g1l, g2h, g2l);
             transverse_gen<DT>(x, xp, y, yp, d, hx, hy, c);
         } else {
             long_turn<SCHEME, DT, ZS>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo);
@@ -254,15 +258,19 @@ __global__ void PHTL_F32C_BOUNDS k_batched_f32c(const JobDesc* __restrict__ jobs
             run_f32c<PHTL_EULER_CROMER, DT, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
         else if (J.scheme == PHTL_LEAPFROG)
             run_f32c<PHTL_LEAPFROG, DT, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
-        else
+        else if (!GEN || J.scheme == PHTL_RUTH4)
             run_f32c<PHTL_RUTH4, DT, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
+        else if constexpr (GEN)  // RK4 lives in the widened map's kernels only
+            run_f32c<PHTL_RK4, DT, true, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
     } else {
         if (J.scheme == PHTL_EULER_CROMER)
             run_f32c<PHTL_EULER_CROMER, DT, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
         else if (J.scheme == PHTL_LEAPFROG)
             run_f32c<PHTL_LEAPFROG, DT, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
-        else
+        else if (!GEN || J.scheme == PHTL_RUTH4)
             run_f32c<PHTL_RUTH4, DT, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
+        else if constexpr (GEN)  // RK4 lives in the widened map's kernels only
+            run_f32c<PHTL_RK4, DT, false, GEN>(z, d, x, xp, y, yp, hx, hy, c, J, cnt, t0, nt, smem, parity);
     }
     store4(g[0], base, J.n, vec, z);
     store4(g[1], base, J.n, vec, d);

@@ -44,8 +44,8 @@ __device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&x
     if (GEN) slip_stages<SCHEME>(c, g1h, g1l, g2h, g2l);
     for (int t = 0; t < nturns; ++t) {
         if (GEN) {
-            long_turn_nl<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo, g1h, g1l,
-                                         g2h, g2l);
+            long_turn_nl<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo, c.kw2_hi,
+                                         c.kw2_lo, g1h, g1l, g2h, g2l);
             if (TRANS) transverse_gen<DT>(x, xp, y, yp, d, hx, hy, c);
         } else {
             long_turn<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo);

@@ -39,7 +39,7 @@ __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x
     if (GEN) slip_stages<SCHEME>(c, g1, g2);
     for (int t = 0; t < nturns; ++t) {
         if (GEN) {
-            long_turn_nl<SCHEME, ZS>(z, d, c, c.dc, c.kw, g1, g2);
+            long_turn_nl<SCHEME, ZS>(z, d, c, c.dc, c.kw, c.kw2, g1, g2);
             if (TRANS) transverse_gen(x, xp, y, yp, d, hx, hy, c);
         } else {
             long_turn<SCHEME, ZS>(z, d, c, c.dc, c.kw);

@@ -276,27 +276,161 @@ __device__ __forceinline__ void drift_nl(DF (&z)[P], const DF (&d)[P], float dh,
     }
 }
 
+// ---- second RF system (double RF) and classic RK4 ----------------------------------
+
+// Force of the second RF system per unit weight, sin(phi2 + k2 z) - sin(phi2) (rf_linear:
+// cos(phi2) k2 z), as a pair: the phase in FP64 for PHTL_F32C, in double-float for
+// PHTL_F32CD, and the double-float sine.
+template <int DT>
+__device__ __forceinline__ DF2 force2_df(const MapConsts& c, DF2 z)
+{
+    if (c.linear) return df_mul(DF2{c.lin2_hi, c.lin2_lo}, z);
+    DF2 ph;
+    if (DT == PHTL_F32C) {
+        const double zd = widen_bits(z.h) + widen_bits(z.l);
+        ph = split_bits(fma(c.k2, zd, c.phi2));
+    } else {
+        ph = df_add(df_mul(DF2{c.k2_hi, c.k2_lo}, z), DF2{c.phi2_hi, c.phi2_lo});
+    }
+    return df_add(sin_df(ph), DF2{-c.sinphi2_hi, -c.sinphi2_lo});
+}
+
+// The same for PHTL_F32CS: the phase rounded to FP32 and the SFU sine.
+__device__ __forceinline__ float force2_f(const MapConsts& c, DF2 z)
+{
+    if (c.linear) return c.lin2_hi * (z.h + z.l);
+    const DF2 ph = df_add(df_mul(DF2{c.k2_hi, c.k2_lo}, z), DF2{c.phi2_hi, c.phi2_lo});
+    return sin_sfu(__fadd_rn(ph.h, ph.l)) - c.sinphi2_hi;
+}
+
+// Force of the main RF system per unit weight at a pair z (the bracket of kick()).
+template <int DT, bool ZS>
+__device__ __forceinline__ DF2 force1_df(const MapConsts& c, DF2 z)
+{
+    if (c.linear) return df_mul(DF2{c.lin_hi, c.lin_lo}, z);
+    const DF2 f = sin_df(phase_df<DT, ZS>(c, DF{z.h, z.l}));
+    return ZS ? f : df_add(f, DF2{-c.sinphis_hi, -c.sinphis_lo});
+}
+
+template <bool ZS>
+__device__ __forceinline__ float force1_f(const MapConsts& c, DF2 z)
+{
+    if (c.linear) return c.lin_hi * (z.h + z.l);
+    const float f = sin_sfu(phase_f<ZS>(c, DF{z.h, z.l}));
+    return ZS ? f : f - c.sinphis_hi;
+}
+
+// Kick of the widened map: the main system (kick()), then the second one when it is on
+// (k2h + k2l: this stage's w_j A2), each increment added on its own.
+template <int DT, bool ZS>
+__device__ __forceinline__ void kick_gen(const DF (&z)[P], DF (&d)[P], float kh, float kl, float k2h,
+                                         float k2l, const MapConsts& c)
+{
+    kick<DT, ZS>(z, d, kh, kl, c);
+    if (!c.dual_rf) return;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (DT == PHTL_F32CS) {
+            const float f = force2_f(c, as2(z[p]));
+            acc(d[p], __fmaf_rn(k2h, f, __fmul_rn(k2l, f)));
+        } else {
+            acc2(d[p], df_mul(DF2{k2h, k2l}, force2_df<DT>(c, as2(z[p]))));
+        }
+    }
+}
+
+// Right-hand side of the smooth motion per turn as pairs: dz/dn = -(dc + g1 d + g2 d^2) d,
+// dd/dn = kw F1(z) + kw2 F2(z) (dc = eta0 C, g1 = eta1 C, g2 = eta2 C, kw = A, kw2 = A2).
+template <int DT, bool ZS>
+__device__ __forceinline__ void rk4_rhs_df(DF2 z, DF2 d, const MapConsts& c, DF2 dc, DF2 g1, DF2 g2,
+                                           DF2 kw, DF2 kw2, DF2& fz, DF2& fd)
+{
+    DF2 e = df_add(df_mul(g2, d), g1);
+    e = df_add(df_mul(e, d), dc);
+    fz = neg2(df_mul(e, d));
+    fd = df_mul(kw, force1_df<DT, ZS>(c, z));
+    if (c.dual_rf) fd = df_add(fd, df_mul(kw2, force2_df<DT>(c, z)));
+}
+
+__device__ __forceinline__ DF2 df_scale2(DF2 a, float s) { return DF2{s * a.h, s * a.l}; }  // s = 2^k: exact
+
+// One classic RK4 step of one turn.  PHTL_F32C / PHTL_F32CD: every stage in double-float,
+// the weighted sum (k1 + 2 k2 + 2 k3 + k4) / 6 added to the state with TwoSum.
+// PHTL_F32CS: the stages in FP32 (the state's comp folded into the stage arguments), the
+// weighted sum added with TwoSum.
+template <int DT, bool ZS>
+__device__ __forceinline__ void rk4_turn(DF (&z)[P], DF (&d)[P], const MapConsts& c, float dh,
+                                         float dl, float kh, float kl, float k2h, float k2l,
+                                         float g1h, float g1l, float g2h, float g2l)
+{
+    constexpr DFC sixth(1.0 / 6.0);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (DT == PHTL_F32CS) {
+            const float z0 = z[p].hi, d0 = d[p].hi, zc = z[p].c, dcmp = d[p].c;
+            float kz[4], kd[4];
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const float w = st == 0 ? 0.0f : (st == 3 ? 1.0f : 0.5f);
+                const float zs = st == 0 ? z0 : __fadd_rn(z0, __fmaf_rn(w, kz[st - 1], zc));
+                const float ds = st == 0 ? d0 : __fadd_rn(d0, __fmaf_rn(w, kd[st - 1], dcmp));
+                const float e = __fmaf_rn(__fmaf_rn(g2h, ds, g1h), ds, dh);
+                kz[st] = -__fmul_rn(e, ds);
+                const DF2 zz{zs, 0.0f};
+                const float f1 = force1_f<ZS>(c, zz);
+                float fd = __fmaf_rn(kh, f1, __fmul_rn(kl, f1));
+                if (c.dual_rf) fd = __fmaf_rn(k2h, force2_f(c, zz), fd);
+                kd[st] = fd;
+            }
+            const float sz = __fmaf_rn(2.0f, __fadd_rn(kz[1], kz[2]), __fadd_rn(kz[0], kz[3]));
+            const float sd = __fmaf_rn(2.0f, __fadd_rn(kd[1], kd[2]), __fadd_rn(kd[0], kd[3]));
+            acc(z[p], __fmul_rn(sz, 0.166666671633720398f));
+            acc(d[p], __fmul_rn(sd, 0.166666671633720398f));
+        } else {
+            const DF2 dc{dh, dl}, g1{g1h, g1l}, g2{g2h, g2l}, kw{kh, kl}, kw2{k2h, k2l};
+            const DF2 z0 = as2(z[p]), d0 = as2(d[p]);
+            DF2 k1z, k1d, k2z, k2d, k3z, k3d, k4z, k4d;
+            rk4_rhs_df<DT, ZS>(z0, d0, c, dc, g1, g2, kw, kw2, k1z, k1d);
+            rk4_rhs_df<DT, ZS>(df_add(z0, df_scale2(k1z, 0.5f)), df_add(d0, df_scale2(k1d, 0.5f)), c,
+                               dc, g1, g2, kw, kw2, k2z, k2d);
+            rk4_rhs_df<DT, ZS>(df_add(z0, df_scale2(k2z, 0.5f)), df_add(d0, df_scale2(k2d, 0.5f)), c,
+                               dc, g1, g2, kw, kw2, k3z, k3d);
+            rk4_rhs_df<DT, ZS>(df_add(z0, k3z), df_add(d0, k3d), c, dc, g1, g2, kw, kw2, k4z, k4d);
+            const DF2 sz = df_add(df_add(k1z, k4z), df_scale2(df_add(k2z, k3z), 2.0f));
+            const DF2 sd = df_add(df_add(k1d, k4d), df_scale2(df_add(k2d, k3d), 2.0f));
+            acc2(z[p], df_mul(sz, DF2{sixth.h, sixth.l}));
+            acc2(d[p], df_mul(sd, DF2{sixth.h, sixth.l}));
+        }
+    }
+}
+
+// One turn of the widened map: slippage expansion (g1*, g2*: stage i's w_i eta1 C,
+// w_i eta2 C), second RF system (k2h, k2l: stage j's w_j A2) and, for RK4, the classic
+// Runge-Kutta step.
 template <int SCHEME, int DT, bool ZS>
 __device__ __forceinline__ void long_turn_nl(DF (&z)[P], DF (&d)[P], const MapConsts& c,
                                              const float* dh, const float* dl, const float* kh,
-                                             const float* kl, const float (&g1h)[4],
-                                             const float (&g1l)[4], const float (&g2h)[4],
-                                             const float (&g2l)[4])
+                                             const float* kl, const float* k2h, const float* k2l,
+                                             const float (&g1h)[4], const float (&g1l)[4],
+                                             const float (&g2h)[4], const float (&g2l)[4])
 {
-    if (SCHEME == PHTL_EULER_CROMER) {
-        kick<DT, ZS>(z, d, kh[0], kl[0], c);
+    if (SCHEME == PHTL_RK4) {
+        rk4_turn<DT, ZS>(z, d, c, dh[0], dl[0], kh[0], kl[0], k2h[0], k2l[0], g1h[0], g1l[0],
+                         g2h[0], g2l[0]);
+    } else if (SCHEME == PHTL_EULER_CROMER) {
+        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c);
         drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
     } else if (SCHEME == PHTL_LEAPFROG) {
         drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
-        kick<DT, ZS>(z, d, kh[0], kl[0], c);
+        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c);
         drift_nl<DT>(z, d, dh[1], dl[1], g1h[1], g1l[1], g2h[1], g2l[1]);
     } else {
         drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
-        kick<DT, ZS>(z, d, kh[0], kl[0], c);
+        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c);
         drift_nl<DT>(z, d, dh[1], dl[1], g1h[1], g1l[1], g2h[1], g2l[1]);
-        kick<DT, ZS>(z, d, kh[1], kl[1], c);
+        kick_gen<DT, ZS>(z, d, kh[1], kl[1], k2h[1], k2l[1], c);
         drift_nl<DT>(z, d, dh[2], dl[2], g1h[2], g1l[2], g2h[2], g2l[2]);
-        kick<DT, ZS>(z, d, kh[2], kl[2], c);
+        kick_gen<DT, ZS>(z, d, kh[2], kl[2], k2h[2], k2l[2], c);
         drift_nl<DT>(z, d, dh[3], dl[3], g1h[3], g1l[3], g2h[3], g2l[3]);
     }
 }

@@ -148,7 +148,6 @@ public:
     int run_round(std::vector<sched::Job*>& act, std::vector<int64_t>& nt, int64_t* launches)
     {
         cudaSetDevice(h_->device);
-        const phtl_derived& d = h_->derived;
         int64_t nl = 0;
         bool used[2] = {false, false};
         for (int g = 0; g < kNumDtypes; ++g) {
@@ -172,6 +171,7 @@ public:
             const int block = block_[g];
             const int64_t per_tile = static_cast<int64_t>(block) * particles_per_thread(g);
             int64_t tiles = 0;
+            bool rk4 = false;
             for (size_t k = 0; k < idx.size(); ++k) {
                 const sched::Job& j = *act[idx[k]];
                 const DevJob* dj = static_cast<const DevJob*>(j.exec_state);
@@ -191,8 +191,8 @@ public:
                 J.turn_offset = j.turns_done;
                 J.tile_begin = tiles;
                 J.scheme = j.req.integrator;
-                scheme_weights(J.scheme, kick_amplitude(h_->params, d, j.req.voltage_V), d.etaC, J.dc, J.kw);
-                fill_float_weights(J);
+                job_weights(h_, J.scheme, j.req.voltage_V, J);
+                rk4 = rk4 || J.scheme == PHTL_RK4;
                 tiles += (j.req.n + per_tile - 1) / per_tile;
                 nt[idx[k]] = std::min<int64_t>(T, J.turns);
             }
@@ -202,7 +202,7 @@ public:
                                              cudaMemcpyHostToDevice, s));
             if (rc != PHTL_OK) return rc;
             if (tiles > 0) {
-                rc = cuda_rc(launch_batched(dtab_[g], static_cast<int32_t>(idx.size()), h_->mc[0], g,
+                rc = cuda_rc(launch_batched(dtab_[g], static_cast<int32_t>(idx.size()), batch_consts(h_, rk4), g,
                                             true, 0, static_cast<int32_t>(T), static_cast<int>(tiles), block, s));
                 if (rc != PHTL_OK) return rc;
                 ++nl;
@@ -292,7 +292,7 @@ namespace {
 int check_request(const phtl_handle* h, const phtl_request* r)
 {
     if (!r) return PHTL_E_INVALID;
-    if (r->integrator < PHTL_EULER_CROMER || r->integrator > PHTL_RUTH4) return PHTL_E_INVALID;
+    if (r->integrator < PHTL_EULER_CROMER || r->integrator > PHTL_RK4) return PHTL_E_INVALID;
     if (r->dtype < PHTL_F64 || r->dtype > PHTL_F32CS) return PHTL_E_INVALID;
     if (r->n < 0 || r->turns < 0 || !std::isfinite(r->voltage_V)) return PHTL_E_INVALID;
     if (r->n > 0) {
@@ -306,9 +306,7 @@ int check_request(const phtl_handle* h, const phtl_request* r)
         if (!r->resume_ticket && in_pair != (r->out[p] != nullptr)) return PHTL_E_INVALID;
     }
     if (r->mon_rows && r->mon_stride < 1) return PHTL_E_INVALID;
-    const phtl_derived& d = h->derived;
-    const double K = d.etaC * kick_amplitude(h->params, d, r->voltage_V) * d.k * d.cos_phis;
-    if (r->voltage_V != 0.0 && !(K > 0.0 && K < 4.0)) return PHTL_E_UNSTABLE;
+    if (voltage_check(h, r->voltage_V) != PHTL_OK) return PHTL_E_UNSTABLE;
     return PHTL_OK;
 }
 

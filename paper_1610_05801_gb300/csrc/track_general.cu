@@ -1,6 +1,6 @@
-// Single-bunch kernels of the widened map: the slippage expansion eta(delta) in the drift
-// and the chromatic transverse rotation (per-particle phase advance 2 pi (frac Q + xi
-// delta)).  The same kernel templates as the linear map (kernels_f64.cuh,
+// Single-bunch kernels of the widened map: the slippage expansion eta(delta) in the drift,
+// the chromatic transverse rotation (per-particle phase advance 2 pi (frac Q + xi
+// delta)), the second RF system and the classic RK4 integrator.  The same kernel templates as the linear map (kernels_f64.cuh,
 // kernels_f32c.cuh) with GEN = true, in a translation unit of their own so that neither
 // the linear kernels' registers nor their build time change.  Built with TRANS = MON =
 // true: the planes and the monitor are checked at run time.
@@ -29,6 +29,7 @@ const void* general_kernel_single(int scheme, int dtype)
     PHTL_GEN(PHTL_LEAPFROG)
     PHTL_GEN(PHTL_RUTH4)
 #undef PHTL_GEN
+    if (scheme == PHTL_RK4) return general_kernel_single_rk4(dtype);
     return nullptr;
 }
 

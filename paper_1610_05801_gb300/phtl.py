@@ -22,11 +22,11 @@ E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_TIMEOUT, E_CANCELLED, E_BADHANDLE, E_N
     -1, -2, -3, -4, -5, -6, -7, -8)
 E_TOOBIG = -9
 NOALLOC_MAX_JOBS = 256
-EULER_CROMER, LEAPFROG, RUTH4 = 0, 1, 2
+EULER_CROMER, LEAPFROG, RUTH4, RK4 = 0, 1, 2, 3
 F64, F32C, F32CD, F32CS = 0, 1, 2, 3
 MON_FIELDS = 16
 INTEGRATORS = {"euler_cromer": EULER_CROMER, "ec": EULER_CROMER, "leapfrog": LEAPFROG,
-               "lf": LEAPFROG, "ruth4": RUTH4}
+               "lf": LEAPFROG, "ruth4": RUTH4, "rk4": RK4}
 DTYPES = {"f64": F64, "f32c": F32C, "f32cd": F32CD, "f32cs": F32CS}
 MOMENT_NAMES = (
     "mean_z", "mean_dp", "rms_z", "rms_dp", "eps_z",
@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("phi_s_rad", C.c_double), ("beta_x_m", C.c_double), ("beta_y_m", C.c_double),
                 ("Qx", C.c_double), ("Qy", C.c_double), ("harmonic", C.c_int32),
                 ("rf_linear", C.c_int32), ("eta1", C.c_double), ("eta2", C.c_double),
-                ("xi_x", C.c_double), ("xi_y", C.c_double)]
+                ("xi_x", C.c_double), ("xi_y", C.c_double), ("voltage2_V", C.c_double),
+                ("phi2_rad", C.c_double), ("harmonic2", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class Derived(C.Structure):
@@ -129,6 +130,8 @@ SIGNATURES = {
     "phtl_get_stats": (_int, [_vp, C.POINTER(Stats)]),
     "phtl_eval_sin": (_int, [_vp, _vp, _i64, _int, _vp]),
     "phtl_eval_sin_kz": (_int, [C.c_double, _vp, _vp, _i64, _vp]),
+    "phtl_set_programme": (_int, [_vp, _vp, _vp, _i64]),
+    "phtl_track_programme": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _i64, _int, _int, _vp]),
     "phtl_autotune": (_int, [_vp, _int, _int, _i64, C.c_double, C.POINTER(Tuning)]),
     "phtl_batch_create": (_int, [_vp, C.POINTER(Job), C.c_int32, C.c_int32, C.POINTER(_vp)]),
     "phtl_batch_run": (_int, [_vp, _vp]),
@@ -180,7 +183,7 @@ def make_params(**kw) -> Params:
                     beta_y_m=1.0, Qx=0.0, Qy=0.0, rf_linear=0, voltage_V=0.0)
     defaults.update(kw)
     for k, v in defaults.items():
-        setattr(p, k, int(v) if k in ("harmonic", "rf_linear") else float(v))
+        setattr(p, k, int(v) if k in ("harmonic", "rf_linear", "harmonic2") else float(v))
     return p
 
 
@@ -303,6 +306,35 @@ class Ring:
         """One launch per turn (phtl_track_perturn); stream-ordered."""
         self._track(self._lib.phtl_track_perturn, z, dp, x, xp, y, yp, turns, integrator, dtype,
                     stream)
+
+    def set_programme(self, voltage_V=None, p0_eVc=None):
+        """Attach a ramp programme (phtl_set_programme): voltage_V[n] for turns 0..N-1 and
+        the reference momenta p0_eVc[0..N]; None detaches."""
+        if voltage_V is None:
+            _check(self._lib.phtl_set_programme(self._h, None, None, 0), "phtl_set_programme")
+            return
+        V = np.ascontiguousarray(voltage_V, dtype=np.float64)
+        p0 = np.ascontiguousarray(p0_eVc, dtype=np.float64)
+        if p0.shape[0] != V.shape[0] + 1:
+            raise ValueError("p0_eVc needs one more entry than voltage_V")
+        _check(self._lib.phtl_set_programme(self._h, V.ctypes.data, p0.ctypes.data, V.shape[0]),
+               "phtl_set_programme")
+
+    def track_programme(self, z, dp, x=None, xp=None, y=None, yp=None, turn0=0, turns=1,
+                        integrator="leapfrog", dtype="f64", stream=None):
+        """Track turns [turn0, turn0 + turns) of the attached programme
+        (phtl_track_programme)."""
+        dt = _dtype(dtype)
+        want = "float64" if dt == F64 else "float32"
+        bufs = (z, dp, x, xp, y, yp)
+        for name, b in zip(("z", "dp", "x", "xp", "y", "yp"), bufs):
+            if b is not None:
+                _check_tensor(b, want, name)
+        n = z.numel() if dt == F64 else z.numel() // 2
+        rc = self._lib.phtl_track_programme(self._h, *[_ptr(b) for b in bufs], n, int(turn0),
+                                            int(turns), _integrator(integrator), dt,
+                                            _stream_ptr(stream))
+        _check(rc, "phtl_track_programme")
 
     def track_host(self, z, dp, x=None, xp=None, y=None, yp=None, turns=1,
                    integrator="leapfrog", dtype="f64", mon_rows=None, mon_stride=1):

@@ -75,6 +75,73 @@ def test_create_validation():
     assert lib.phtl_create(None, None) == phtl.E_INVALID
 
 
+def test_double_rf_validation_and_strength():
+    """A second RF system: harmonic2 must be positive when voltage2 is set, the combined
+    linear strength K = eta C (A k cos phi_s + A2 k2 cos phi2) equals the oracle's, a
+    flat bottom (K = 0) is accepted and an over-cancelling system is unstable -- for the
+    handle and for a batched job's own voltage."""
+    base = dict(synth.ring(4.5e6), harmonic2=2 * 4620, voltage2_V=1.35e6, phi2_rad=0.0)
+    lib = phtl.load()
+    rc, _ = _create(**dict(base, harmonic2=0))
+    assert rc == phtl.E_INVALID
+    for bad in (dict(voltage2_V=float("nan")), dict(phi2_rad=float("inf"))):
+        rc, _ = _create(**dict(base, **bad))
+        assert rc == phtl.E_INVALID, bad
+    for ratio, phi2 in ((0.3, 0.0), (0.3, -0.4), (-0.5, 0.0)):
+        ring = dict(base, voltage2_V=ratio * 4.5e6, phi2_rad=phi2)
+        R = phtl.Ring(**ring)
+        a, b = R.derived(), oracle.derive(ring)
+        assert math.isclose(a.K, b.K, rel_tol=1e-13, abs_tol=1e-18), (ratio, a.K, b.K)
+        R.close()
+    rc, _ = _create(**dict(base, voltage2_V=-0.7 * 4.5e6))
+    assert rc == phtl.E_UNSTABLE
+    assert oracle.derive_rc(oracle.params(**dict(base, voltage2_V=-0.7 * 4.5e6))) == -2
+    # a batched job whose own voltage over-cancels against the ring's second system
+    R = phtl.Ring(**dict(base, voltage2_V=-0.3 * 4.5e6))
+    z = np.zeros(8)
+    J = (phtl.Job * 1)()
+    J[0].c[0] = J[0].c[1] = z.ctypes.data
+    J[0].n, J[0].turns, J[0].integrator, J[0].dtype = 8, 10, phtl.RK4, 0
+    h = C.c_void_p()
+    J[0].voltage_V = 1e6          # 1 MV - 1.35 MV at twice the harmonic: K < 0
+    assert lib.phtl_batch_create(R.handle, J, 1, 1, C.byref(h)) == phtl.E_UNSTABLE
+    J[0].integrator = 4
+    assert lib.phtl_batch_create(R.handle, J, 1, 1, C.byref(h)) == phtl.E_INVALID
+    R.close()
+
+
+def test_programme_validation_needs_no_gpu():
+    """phtl_set_programme checks the programme before it looks for a device: bad arrays
+    and unstable turns are reported here; a valid programme then needs the GPU."""
+    lib = phtl.load()
+    R = phtl.Ring(**synth.ring(4.5e6))
+    N = 100
+    V = np.full(N, 4.5e6)
+    p0 = 26e9 + 1e6 * np.arange(N + 1)
+
+    def setp(V, p0, n=N):
+        return lib.phtl_set_programme(R.handle, V.ctypes.data, p0.ctypes.data, n)
+
+    assert lib.phtl_set_programme(R.handle, None, None, 5) == phtl.E_INVALID
+    assert lib.phtl_set_programme(None, None, None, 0) == phtl.E_BADHANDLE
+    bad = p0.copy()
+    bad[7] = -1.0
+    assert setp(V, bad) == phtl.E_INVALID
+    bad = V.copy()
+    bad[3] = 0.0                                             # no voltage, momentum changes
+    assert setp(bad, p0) == phtl.E_INVALID
+    assert setp(np.full(N, 1e5), p0) == phtl.E_UNSTABLE      # too little voltage for the gain
+    assert lib.phtl_set_programme(R.handle, None, None, 0) == phtl.OK    # detach: no device needed
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert setp(V, p0) == phtl.E_NODEVICE
+    R.close()
+    # the programme runs the linear map only
+    R = phtl.Ring(**synth.ring(4.5e6, eta1=0.05))
+    assert lib.phtl_set_programme(R.handle, V.ctypes.data, p0.ctypes.data, N) == phtl.E_INVALID
+    R.close()
+
+
 def test_derived_constants_match_oracle():
     for V in (2e6, 4.5e6):
         ring = synth.ring(V, transverse=True)
@@ -120,7 +187,7 @@ def test_track_argument_validation_needs_no_gpu():
         return lib.phtl_track(h, a["z"], a["dp"], a["x"], a["xp"], a["y"], a["yp"], a["n"],
                               a["turns"], a["integ"], a["dt"], a["s"])
 
-    assert call(args(integ=3)) == phtl.E_INVALID
+    assert call(args(integ=4)) == phtl.E_INVALID
     assert call(args(integ=-1)) == phtl.E_INVALID
     assert call(args(dt=7)) == phtl.E_INVALID
     assert call(args(n=-1)) == phtl.E_INVALID
