@@ -115,6 +115,14 @@ class Oracle:
         L.ref_track_ramp.argtypes = [C.POINTER(RefDerived), dp, C.c_long, C.c_long, C.c_int,
                                      dp, dp, dp, dp, dp, dp, C.c_long, C.c_long, dp, C.c_long]
         L.ref_track_ramp.restype = C.c_int
+        lp = C.POINTER(C.c_long)
+        L.ref_collective_kick.argtypes = [dp, dp, C.c_long, C.c_double, C.c_double, C.c_long, dp,
+                                          C.c_double, lp, dp]
+        L.ref_collective_kick.restype = C.c_int
+        L.ref_track_collective.argtypes = [C.POINTER(RefDerived), C.c_int, dp, dp, dp, dp, dp, dp,
+                                           C.c_long, C.c_long, C.c_double, C.c_double, C.c_long,
+                                           dp, C.c_double, dp, C.c_long]
+        L.ref_track_collective.restype = C.c_int
         L.ref_num_threads.argtypes = []
         L.ref_num_threads.restype = C.c_int
         self.lib = L
@@ -207,6 +215,39 @@ class Oracle:
             raise ValueError(f"ref_track_ramp returned {rc}")
         return (*arrs, mom)
 
+    def collective_kick(self, z, dp, z_lo, inv_dz, w, alpha):
+        """One collective step on copies of (z, dp): returns (z, dp, counts, V)."""
+        z = np.array(z, dtype=np.float64, copy=True, order="C").reshape(-1)
+        dp = np.array(dp, dtype=np.float64, copy=True, order="C").reshape(-1)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        ns = w.shape[0]
+        counts = np.zeros(ns, dtype=np.int64)
+        V = np.zeros(ns)
+        rc = self.lib.ref_collective_kick(_ptr(z), _ptr(dp), z.shape[0], float(z_lo), float(inv_dz),
+                                          ns, _ptr(w), float(alpha),
+                                          counts.ctypes.data_as(C.POINTER(C.c_long)), _ptr(V))
+        if rc != 0:
+            raise ValueError(f"ref_collective_kick returned {rc}")
+        return z, dp, counts, V
+
+    def track_collective(self, d: RefDerived, scheme, z, dp, x=None, xp=None, y=None, yp=None,
+                         turns=1, z_lo=-1.0, inv_dz=1.0, w=(0.0,), alpha=0.0, moments=False,
+                         stride=1):
+        """Turns of map + collective step on copies of the inputs; returns like track()."""
+        if isinstance(scheme, str):
+            scheme = SCHEMES[scheme]
+        arrs = [None if a is None else np.array(a, dtype=np.float64, copy=True, order="C").reshape(-1)
+                for a in (z, dp, x, xp, y, yp)]
+        n = arrs[0].shape[0]
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        mom = np.zeros((turns // stride + 1, NMOM)) if moments else None
+        rc = self.lib.ref_track_collective(C.byref(d), int(scheme), *[_ptr(a) for a in arrs], n,
+                                           int(turns), float(z_lo), float(inv_dz), w.shape[0],
+                                           _ptr(w), float(alpha), _ptr(mom), int(stride))
+        if rc != 0:
+            raise ValueError(f"ref_track_collective returned {rc}")
+        return (*arrs, mom)
+
     def num_threads(self) -> int:
         return int(self.lib.ref_num_threads())
 
@@ -242,6 +283,14 @@ def jacobian(*a, **k):
 
 def num_threads() -> int:
     return load().num_threads()
+
+
+def collective_kick(*a, **k):
+    return load().collective_kick(*a, **k)
+
+
+def track_collective(*a, **k):
+    return load().track_collective(*a, **k)
 
 
 def ramp_derive(*a, **k):

@@ -33,6 +33,10 @@
  *           mu = 2 pi (frac(Q) + xi delta), alpha = 0, with the particle's delta after the
  *           turn's longitudinal step (xi = dQ/d delta, the chromaticity; xi = 0 gives the
  *           same matrix for every particle).
+ *   ramp (optional): per-turn eta_n, A_n, phi_s,n from a programme V_n, p0_n, with delta and
+ *           the slopes re-expressed by p0_n / p0_{n+1} after each turn
+ *   collective step (optional, after each turn): slice counts on a uniform grid, wake
+ *           potential V_k = sum_{j >= k} c_j w[j - k], kick delta += alpha V_k
  * Derived constants (all FP64, from the ring parameters):
  *   beta*gamma = p0/m; gamma = sqrt(1 + (beta gamma)^2); beta = beta gamma / gamma
  *   eta = 1/gamma_t^2 - 1/gamma^2;  k = 2 pi h / C;  A = q V / (beta p0)   [p0 in eV/c]
@@ -48,11 +52,15 @@
  * for the chromaticity: the summed-angle rotation; for RK4: the Taylor polynomial of
  * the linear flow, its determinant and the 5th-order local error against an
  * mpmath Taylor-series flow; for the second RF system: the combined linear slope and
- * the two-harmonic Hamiltonian's order); see the tests.
+ * the two-harmonic Hamiltonian's order; for the ramp: the textbook synchronous energy
+ * gain, the adiabatic invariant and the normalised emittance; for the collective step:
+ * counts of particles placed at slice centres, numpy's convolution, causality and the
+ * map-then-kick order); see the tests.
  */
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -464,6 +472,107 @@ int ref_track_ramp(const ref_derived* d, const double* tc, long nprog, long turn
             ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n,
                         moments + (t / stride) * REF_NMOM);
     }
+    return REF_OK;
+}
+
+/* ---- collective step: longitudinal slicing and a wake kick ------------- */
+
+/*
+ * The paper's conclusion names collective effects as the next workload after single-
+ * particle tracking; it prints no formulas.  The reading (a wake field acting through the
+ * bunch's own longitudinal line density):
+ *   - slicing: nslices uniform slices on [z_lo, z_hi); particle i lies in slice
+ *     k = floor((z_i - z_lo) * inv_dz), inv_dz = nslices / (z_hi - z_lo), when
+ *     0 <= k < nslices; c_k counts the particles of slice k;
+ *   - wake potential: V_k = sum over j >= k of c_j w[j - k] (z > 0 is ahead: a slice is
+ *     affected by the slices ahead of it and by itself, w[m] being the wake of one
+ *     macro-particle m slices ahead), summed in order of increasing j;
+ *   - kick: delta_i <- delta_i + alpha V_k(i) for the particles inside the range.
+ * inv_dz is passed in (computed once by the caller) so that both implementations decide
+ * the slice index from the same two operations.
+ */
+void ref_slice_counts(const double* z, long n, double z_lo, double inv_dz, long nslices,
+                      long* counts)
+{
+    long i, k;
+    for (k = 0; k < nslices; k++) counts[k] = 0;
+    for (i = 0; i < n; i++) {
+        double u = (z[i] - z_lo) * inv_dz;
+        if (u >= 0.0 && u < (double)nslices) {
+            k = (long)floor(u);
+            if (k < nslices) counts[k]++;
+        }
+    }
+}
+
+void ref_wake_potential(const long* counts, const double* w, long nslices, double* V)
+{
+    long j, k;
+    for (k = 0; k < nslices; k++) {
+        double s = 0.0;
+        for (j = k; j < nslices; j++) s = s + (double)counts[j] * w[j - k];
+        V[k] = s;
+    }
+}
+
+/* One collective step on (z, dp): slice, wake potential, kick.  counts / V (optional)
+ * receive the step's slice counts and potential. */
+int ref_collective_kick(double* z, double* dp, long n, double z_lo, double inv_dz, long nslices,
+                        const double* w, double alpha, long* counts, double* V)
+{
+    long i;
+    if (n < 0 || nslices < 1 || !w || (n > 0 && (!z || !dp))) return REF_E_INVALID;
+    long* c = counts ? counts : (long*)malloc(sizeof(long) * nslices);
+    double* v = V ? V : (double*)malloc(sizeof(double) * nslices);
+    if (!c || !v) return REF_E_INVALID;
+    ref_slice_counts(z, n, z_lo, inv_dz, nslices, c);
+    ref_wake_potential(c, w, nslices, v);
+    for (i = 0; i < n; i++) {
+        double u = (z[i] - z_lo) * inv_dz;
+        if (u >= 0.0 && u < (double)nslices) {
+            long k = (long)floor(u);
+            if (k < nslices) dp[i] = dp[i] + alpha * v[k];
+        }
+    }
+    if (!counts) free(c);
+    if (!V) free(v);
+    return REF_OK;
+}
+
+/* Track `turns` turns, each the scheme's one-turn map and the transverse rotation
+ * (as ref_track), then the collective step on the whole bunch.  Monitor rows after each
+ * full turn (collective kick included), as ref_track. */
+int ref_track_collective(const ref_derived* d, int scheme, double* z, double* dp, double* x,
+                         double* xp, double* y, double* yp, long n, long turns, double z_lo,
+                         double inv_dz, long nslices, const double* w, double alpha,
+                         double* moments, long stride)
+{
+    long t, i;
+    if (!d || n < 0 || turns < 0 || scheme < 0 || scheme > 3) return REF_E_INVALID;
+    if (n > 0 && (!z || !dp)) return REF_E_INVALID;
+    if (moments && stride <= 0) return REF_E_INVALID;
+    if (nslices < 1 || !w) return REF_E_INVALID;
+    int dox = x && xp, doy = y && yp;
+    long* c = (long*)malloc(sizeof(long) * nslices);
+    double* v = (double*)malloc(sizeof(double) * nslices);
+    if (!c || !v) { free(c); free(v); return REF_E_INVALID; }
+    if (moments) ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n, moments);
+    for (t = 1; t <= turns; t++) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+        for (i = 0; i < n; i++) {
+            ref_turn(d, scheme, 1.0, &z[i], &dp[i]);
+            ref_transverse(d, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                           doy ? &y[i] : 0, doy ? &yp[i] : 0);
+        }
+        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, c, v);
+        if (moments && t % stride == 0)
+            ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n,
+                        moments + (t / stride) * REF_NMOM);
+    }
+    free(c);
+    free(v);
     return REF_OK;
 }
 

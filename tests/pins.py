@@ -796,6 +796,97 @@ def pin_ramp_normalised_emittance(O):
         assert abs(e1 / e0 - p0[0] / p0[N]) < 1e-11
 
 
+# ---- collective step: slicing and a wake kick ------------------------------------------
+
+
+def _slices_setup(ns=64, lo=-0.8, hi=0.8):
+    return ns, lo, hi, ns / (hi - lo), (hi - lo) / ns
+
+
+def pin_collective_slicing(O):
+    """Particles at slice centres with a seeded count pattern are counted slice by slice;
+    z_lo belongs to the first slice, z_hi and beyond and below z_lo to none; the counts of
+    the inside particles add up to their number; z itself is untouched."""
+    ns, lo, hi, inv, dz = _slices_setup()
+    rng = np.random.default_rng(5)
+    pattern = rng.integers(0, 7, ns)
+    z = np.concatenate([np.full(c, lo + (k + 0.5) * dz) for k, c in enumerate(pattern)])
+    extra = np.array([lo, hi, hi + 0.3, lo - 1e-9, hi - 1e-9])
+    zall = np.concatenate([z, extra])
+    z1, dp1, counts, V = O.collective_kick(zall, np.zeros(zall.size), lo, inv, np.zeros(ns), 0.0)
+    want = pattern.copy()
+    want[0] += 1                     # z_lo
+    want[-1] += 1                    # just below z_hi
+    assert np.array_equal(counts, want), (counts, want)
+    assert counts.sum() == z.size + 2
+    assert np.array_equal(z1, zall) and np.all(dp1 == 0.0)
+
+
+def pin_collective_wake_library(O):
+    """The wake potential V_k = sum_{m >= 0} c_{k+m} w_m equals numpy's convolution of the
+    reversed counts with the wake table; a delta wake returns the counts, a constant wake
+    the number of particles at or ahead of each slice; the head slice feels only itself."""
+    ns, lo, hi, inv, dz = _slices_setup()
+    rng = np.random.default_rng(6)
+    pattern = rng.integers(0, 9, ns)
+    z = np.concatenate([np.full(c, lo + (k + 0.5) * dz) for k, c in enumerate(pattern)])
+    w = rng.normal(0.0, 1.0, ns)
+    _, _, counts, V = O.collective_kick(z, np.zeros(z.size), lo, inv, w, 1.0)
+    ref = np.convolve(counts[::-1].astype(float), w)[:ns][::-1]
+    assert np.max(np.abs(V - ref)) < 1e-12 * np.max(np.abs(ref)), np.max(np.abs(V - ref))
+    delta = np.zeros(ns)
+    delta[0] = 1.0
+    assert np.array_equal(O.collective_kick(z, np.zeros(z.size), lo, inv, delta, 1.0)[3],
+                          counts.astype(float))
+    const = O.collective_kick(z, np.zeros(z.size), lo, inv, np.ones(ns), 1.0)[3]
+    assert np.array_equal(const, np.cumsum(counts[::-1])[::-1].astype(float))
+    # causality: one particle at the head, many behind it; it feels only its own wake
+    zc = np.concatenate([np.full(50, lo + 0.5 * dz), [lo + (ns - 0.5) * dz]])
+    _, dpc, _, _ = O.collective_kick(zc, np.zeros(zc.size), lo, inv, np.ones(ns), 2.0)
+    assert dpc[-1] == 2.0 and np.all(dpc[:-1] == 2.0 * 51)
+
+
+def pin_collective_kick(O):
+    """The kick is alpha times the potential of the particle's own slice; particles outside
+    the range are not kicked; alpha = 0 leaves delta bitwise unchanged."""
+    ns, lo, hi, inv, dz = _slices_setup()
+    rng = np.random.default_rng(7)
+    z = rng.uniform(lo - 0.2, hi + 0.2, 3000)
+    dp = rng.normal(0, 1e-3, z.size)
+    w = np.exp(-np.arange(ns) / 10.0)
+    z1, dp1, counts, V = O.collective_kick(z, dp, lo, inv, w, -3e-7)
+    k = np.floor((z - lo) * inv).astype(int)
+    inside = (k >= 0) & (k < ns)
+    assert np.array_equal(dp1[~inside], dp[~inside])
+    assert np.max(np.abs(dp1[inside] - (dp[inside] + (-3e-7) * V[k[inside]]))) == 0.0
+    assert np.array_equal(O.collective_kick(z, dp, lo, inv, w, 0.0)[1], dp)
+
+
+def pin_collective_turn_order(O):
+    """A turn of the collective tracking is the one-turn map (and the transverse rotation)
+    followed by the collective step on the whole bunch; with alpha = 0 it is the plain
+    tracking, bitwise, every scheme."""
+    ns, lo, hi, inv, dz = _slices_setup()
+    r = ring(voltage_V=4.5e6)
+    d = O.derive(r)
+    rng = np.random.default_rng(8)
+    z, dp = rng.normal(0, 0.1, 400), rng.normal(0, 5e-4, 400)
+    x, xp = rng.normal(0, 1e-3, 400), rng.normal(0, 2e-5, 400)
+    w = 1.0 / (1.0 + np.arange(ns))
+    for scheme in ("euler_cromer", "leapfrog", "ruth4", "rk4"):
+        a = O.track_collective(d, scheme, z, dp, x, xp, turns=1, z_lo=lo, inv_dz=inv, w=w,
+                               alpha=1e-7)
+        b = O.track(d, scheme, z, dp, x, xp, turns=1)
+        c = O.collective_kick(b[0], b[1], lo, inv, w, 1e-7)
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]), scheme
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3]), scheme
+        e = O.track_collective(d, scheme, z, dp, x, xp, turns=50, z_lo=lo, inv_dz=inv, w=w,
+                               alpha=0.0)
+        f = O.track(d, scheme, z, dp, x, xp, turns=50)
+        for u, v in zip(e[:4], f[:4]):
+            assert np.array_equal(u, v), scheme
+
+
 ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_pendulum_detuning, pin_separatrix, pin_time_reversal, pin_inverse_map,
             pin_symplectic, pin_energy_order, pin_symmetry_and_fixed_point,
@@ -804,6 +895,8 @@ ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_chromatic_phase_sum, pin_nonlinear_inverse_map, pin_nonlinear_symplectic,
             pin_rk4_linear_closed_form, pin_rk4_jacobian, pin_double_rf_linear,
             pin_double_rf_energy, pin_ramp_constant_programme, pin_ramp_synchronous_phase,
-            pin_ramp_adiabatic_invariant, pin_ramp_normalised_emittance)
+            pin_ramp_adiabatic_invariant, pin_ramp_normalised_emittance,
+            pin_collective_slicing, pin_collective_wake_library, pin_collective_kick,
+            pin_collective_turn_order)
 # pins that need mpmath (skipped where it is missing)
 ALL_MPMATH = (pin_rk4_order,)

@@ -87,6 +87,28 @@ MUTANTS = {
     "ramp_gain_without_beta": ("double x = b * (pb - pa) / (p->charge_e * V[t]);",
                                "double x = (pb - pa) / (p->charge_e * V[t]);"),
     "ramp_eta_from_end_momentum": ("double bg = pa / p->mass_eV;", "double bg = pb / p->mass_eV;"),
+    "wake_direction_reversed": ("for (j = k; j < nslices; j++) s = s + (double)counts[j] * w[j - k];",
+                                "for (j = 0; j <= k; j++) s = s + (double)counts[j] * w[k - j];"),
+    "wake_index_off_by_one": ("s = s + (double)counts[j] * w[j - k];",
+                              "s = s + (double)counts[j] * w[j - k + (j + 1 < nslices)];"),
+    "slice_round_not_floor": ("            k = (long)floor(u);\n            if (k < nslices) counts[k]++;",
+                              "            k = (long)floor(u + 0.5);\n            if (k < nslices) counts[k]++;"),
+    "slice_includes_z_hi": ("        if (u >= 0.0 && u < (double)nslices) {\n            k = (long)floor(u);",
+                            "        if (u >= 0.0 && u <= (double)nslices) {\n            k = (long)floor(u) - (u == (double)nslices);"),
+    "collective_kick_sign": ("if (k < nslices) dp[i] = dp[i] + alpha * v[k];",
+                             "if (k < nslices) dp[i] = dp[i] - alpha * v[k];"),
+    "collective_before_map": ("""        for (i = 0; i < n; i++) {
+            ref_turn(d, scheme, 1.0, &z[i], &dp[i]);
+            ref_transverse(d, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                           doy ? &y[i] : 0, doy ? &yp[i] : 0);
+        }
+        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, c, v);""",
+                              """        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, c, v);
+        for (i = 0; i < n; i++) {
+            ref_turn(d, scheme, 1.0, &z[i], &dp[i]);
+            ref_transverse(d, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
+                           doy ? &y[i] : 0, doy ? &yp[i] : 0);
+        }"""),
     "ramp_A_from_end_momentum": ("o[1] = p->charge_e * V[t] / (b * pa);",
                                  "o[1] = p->charge_e * V[t] / (b * pb);"),
 }
