@@ -64,6 +64,12 @@ WORKLOADS = {
     "ramp_1e6x1e4_ec_lf_ruth4_f64": dict(
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
         voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5, ramp=dict(p0_end=30e9)),
+    # collective step after every turn: 512 uniform slices on [-0.75, 0.75) m, a decaying
+    # oscillating (resonator-like) wake table, kick -5e-11 x V; leap-frog, 1e6 x 1e4 turns
+    "collective_wake_1e6x1e4_lf_f64": dict(
+        n=1_000_000, turns=10_000, schemes=("leapfrog",), dtype="f64", voltage=4.5e6,
+        transverse=True, stride=1, sep_frac=0.5,
+        wake=dict(nslices=512, z_lo=-0.75, z_hi=0.75, alpha=-5e-11)),
     # small case for quick checks (not a bench line)
     "tiny": dict(n=20_000, turns=200, schemes=("euler_cromer", "leapfrog", "ruth4"),
                  dtype="f64", voltage=4.5e6, transverse=True, stride=1),
@@ -112,6 +118,8 @@ RF2_FLOPS = 2 + SINE_FLOPS + 1 + 2
 KICKS = {"euler_cromer": 1, "leapfrog": 1, "ruth4": 3, "rk4": 4}
 # ramp programme: per particle-turn delta, x' and y' are multiplied by r_n
 RAMP_FLOPS = 3
+# collective step per particle-turn: the slice index twice (2 flops each) and the kick FMA
+COLLECTIVE_FLOPS = 6
 TRANSVERSE_FLOPS = 12
 MONITOR_FLOPS = 24
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
@@ -247,6 +255,15 @@ def ramp_programme(wl):
     return np.full(turns, wl["voltage"]), pa + (pb - pa) * np.arange(turns + 1) / turns
 
 
+def wake_table(wl):
+    """The workload's wake samples w[m] = exp(-m / 51.2) cos(m / 25.6) (512 slices)."""
+    import numpy as np
+
+    ns = wl["wake"]["nslices"]
+    m = np.arange(ns)
+    return np.exp(-m / (0.1 * ns)) * np.cos(m / (0.05 * ns))
+
+
 def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the workload
     (n_sample particles x turns_sample turns x every scheme, with the same transverse
@@ -275,6 +292,12 @@ def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
             if tc is not None:
                 O.track_ramp(d, tc, s, z, dp, *tr, turns=turns, moments=wl["stride"] > 0,
                              stride=max(1, wl["stride"]))
+            elif wl.get("wake"):
+                wk = wl["wake"]
+                O.track_collective(d, s, z, dp, *tr, turns=turns, z_lo=wk["z_lo"],
+                                   inv_dz=wk["nslices"] / (wk["z_hi"] - wk["z_lo"]),
+                                   w=wake_table(wl), alpha=wk["alpha"],
+                                   moments=wl["stride"] > 0, stride=max(1, wl["stride"]))
             else:
                 O.track(d, s, z, dp, *tr, turns=turns, moments=wl["stride"] > 0,
                         stride=max(1, wl["stride"]))
@@ -353,6 +376,10 @@ def run_ours(args, wl_name, wl):
     ev = {s: [] for s in wl["schemes"]}
     nlaunch = {s: 0 for s in wl["schemes"]}
     track = R.track_perturn if wl.get("perturn") else R.track
+    if wl.get("wake"):
+        wk = wl["wake"]
+        R.set_wake(wake_table(wl), wk["z_lo"], wk["z_hi"], wk["alpha"])
+        track = R.track_collective
     if wl.get("ramp"):
         R.set_programme(*ramp_programme(wl))
 
@@ -410,15 +437,25 @@ def run_ours(args, wl_name, wl):
     per_scheme_ms = {s: sum(a.elapsed_time(b) for a, b in ev[s]) / len(ev[s]) for s in ev}
     dom = max(per_scheme_ms, key=per_scheme_ms.get)
     launches_per_call = max(1, nlaunch[dom] // args.steps)
+    if wl.get("wake"):
+        # two launches per turn (turn + slicing, potential): the turn kernel's duration is
+        # bounded above by the call's time per turn (the potential kernel and the gaps
+        # included), so the achieved rate below is a lower bound
+        launches_per_call = turns
     tpl = math.ceil(turns / launches_per_call)
     dur_s = per_scheme_ms[dom] / 1e3 / launches_per_call
     flops_pt = alg_flops(dom, wl["transverse"], wl["stride"] > 0, wl.get("ring"))
     if wl.get("ramp"):
         flops_pt += RAMP_FLOPS
+    if wl.get("wake"):
+        # the general kernel's drifts, and per particle the slice index twice (subtract,
+        # multiply) and the kick FMA
+        flops_pt += {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4, "rk4": 0}[dom] * (
+            DRIFT_FLOPS_NL - DRIFT_FLOPS) + COLLECTIVE_FLOPS
     flops = flops_pt * n * tpl
     achieved = flops / dur_s / 1e12
 
-    if args.no_e2e or wl.get("perturn") or wl.get("ramp"):
+    if args.no_e2e or wl.get("perturn") or wl.get("ramp") or wl.get("wake"):
         e2e_value, h2d, d2h, e2e_steps = None, 0, 0, 0
     else:
         e2e_value, h2d, d2h, e2e_steps = e2e_host(R, host, wl, args, dist, dev, ws)
@@ -428,6 +465,8 @@ def run_ours(args, wl_name, wl):
              f"{', widened map' if wl.get('ring') else ''}{', ramp programme' if wl.get('ramp') else ''}>")
     if wl.get("ramp"):
         kname = kname.replace("k_track_", "k_ramp_")
+    if wl.get("wake"):
+        kname = f"k_coll_turn<{dom}> (one turn + slicing + previous turn's wake kick)"
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

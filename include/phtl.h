@@ -253,6 +253,52 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
                          int64_t n, int64_t turn0, int64_t turns, int integrator, int dtype,
                          void* cuda_stream);
 
+/* ---- collective step: slicing and a wake kick ------------------------------------------- */
+
+#define PHTL_MAX_SLICES 4096
+
+/* A wake acting through the bunch's own longitudinal line density.  The paper's
+ * conclusion names collective effects as the next workload after single-particle tracking
+ * and prints no formulas; the reading:
+ *   - slicing: nslices uniform slices on [z_lo, z_hi); particle i lies in slice
+ *     k = floor((z_i - z_lo) * inv_dz), inv_dz = nslices / (z_hi - z_lo) (both FP64,
+ *     subtract then multiply), when 0 <= k < nslices; c_k counts slice k's particles;
+ *   - wake potential: V_k = sum over j >= k of c_j w[j - k] (z > 0 is ahead: a slice feels
+ *     the slices ahead of it and itself; w[m] is the wake of one macro-particle m slices
+ *     ahead, in units chosen with alpha);
+ *   - kick: delta_i += alpha V_k(i) for the particles inside the grid (others unchanged). */
+typedef struct phtl_wake {
+    double z_lo, z_hi;  /* slicing range [z_lo, z_hi), z_hi > z_lo                     */
+    double alpha;       /* kick per unit wake potential                              */
+    const double* w;    /* host array of nslices wake samples w[0 .. nslices-1]       */
+    int32_t nslices;    /* 1 .. PHTL_MAX_SLICES                                       */
+    int32_t pad_;
+} phtl_wake;
+
+/* Attach a wake to the handle (NULL detaches).  The table is copied into library-owned
+ * device memory together with the slice counts (two buffers) and the potential: 24 bytes
+ * per slice, freed by phtl_destroy or a detaching call.  Synchronous.
+ * Errors: PHTL_E_BADHANDLE; PHTL_E_INVALID (nslices out of range, z_hi <= z_lo,
+ * non-finite values, w NULL); PHTL_E_NODEVICE; PHTL_E_NOMEM.                           */
+int phtl_set_wake(phtl_handle* h, const phtl_wake* wake);
+
+/* One collective step on (z, dp) without the map: slice the bunch, form the potential,
+ * kick.  FP64 buffers of n doubles (dtype must be PHTL_F64).  counts_out (nslices
+ * uint32) and V_out (nslices doubles): device pointers or NULL, receive the step's
+ * counts and potential.  Stream-ordered.  Errors: as phtl_track, plus PHTL_E_INVALID
+ * (no wake attached, or attached on another device, or dtype other than PHTL_F64).     */
+int phtl_collective_kick(phtl_handle* h, void* z, void* dp, int64_t n, int dtype,
+                         uint32_t* counts_out, double* V_out, void* cuda_stream);
+
+/* Track `turns` turns, each the scheme's one-turn map and the transverse rotation (as
+ * phtl_track, widened map included) followed by the collective step on the whole bunch.
+ * FP64 only; every integrator (RK4 included); the monitor (phtl_set_monitor) records
+ * after each full turn, collective kick included.  Each turn is two kernel launches
+ * (turn + slicing, potential), the state making one HBM round trip per turn.
+ * Stream-ordered.  Errors: as phtl_collective_kick.                                     */
+int phtl_track_collective(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                          int64_t n, int64_t turns, int integrator, int dtype, void* cuda_stream);
+
 /* ---- batched launch (many independent bunches in one graph-captured launch) ------------ */
 
 /* One bunch of a batch.  Particles are independent and turns sequential (Sec. 2.3), so

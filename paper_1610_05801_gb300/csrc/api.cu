@@ -252,10 +252,29 @@ void free_programme(phtl_handle* h)
     cudaGetLastError();
 }
 
+void free_wake(phtl_handle* h)
+{
+    if (h->wake_mem) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (h->wake_device >= 0 && cur != h->wake_device) cudaSetDevice(h->wake_device);
+        cudaDeviceSynchronize();
+        cudaFree(h->wake_mem);
+        if (cur >= 0 && cur != h->wake_device) cudaSetDevice(cur);
+    }
+    h->wake_mem = nullptr;
+    h->wake_w = h->wake_V = nullptr;
+    h->wake_counts = nullptr;
+    h->wake_device = -1;
+    std::memset(&h->coll, 0, sizeof(h->coll));
+    cudaGetLastError();
+}
+
 void release_handle_resources(phtl_handle* h)
 {
     stop_server(h);
     free_programme(h);
+    free_wake(h);
     if (h->stream) {
         cudaStreamSynchronize(h->stream);
         cudaStreamDestroy(h->stream);
@@ -764,6 +783,170 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
         first = false;
         ++h->stats.launches;
     } while (t0 < turns);
+    h->stats.particle_turns += n * turns;
+    ++h->stats.calls;
+    return PHTL_OK;
+}
+
+int phtl_set_wake(phtl_handle* h, const phtl_wake* wk)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (!wk) {
+        free_wake(h);
+        return PHTL_OK;
+    }
+    const int ns = wk->nslices;
+    if (ns < 1 || ns > PHTL_MAX_SLICES || !wk->w || !std::isfinite(wk->z_lo) ||
+        !std::isfinite(wk->z_hi) || !(wk->z_hi > wk->z_lo) || !std::isfinite(wk->alpha))
+        return PHTL_E_INVALID;
+    for (int m = 0; m < ns; ++m)
+        if (!std::isfinite(wk->w[m])) return PHTL_E_INVALID;
+    const double inv_dz = static_cast<double>(ns) / (wk->z_hi - wk->z_lo);
+    if (!std::isfinite(inv_dz)) return PHTL_E_INVALID;
+    int rc = ensure_device(h);
+    if (rc != PHTL_OK) return rc;
+    free_wake(h);
+    const size_t bytes = static_cast<size_t>(ns) * (2 * sizeof(double) + 2 * sizeof(unsigned));
+    if (cudaMalloc(&h->wake_mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h->wake_mem = nullptr;
+        return PHTL_E_NOMEM;
+    }
+    h->wake_w = static_cast<double*>(h->wake_mem);
+    h->wake_V = h->wake_w + ns;
+    h->wake_counts = reinterpret_cast<unsigned*>(h->wake_V + ns);
+    if (cudaMemcpy(h->wake_w, wk->w, sizeof(double) * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->wake_V, 0, sizeof(double) * ns + 2 * sizeof(unsigned) * ns) != cudaSuccess) {
+        cudaGetLastError();
+        free_wake(h);
+        return PHTL_E_CUDA;
+    }
+    h->wake_device = h->device;
+    h->coll.z_lo = wk->z_lo;
+    h->coll.inv_dz = inv_dz;
+    h->coll.alpha = wk->alpha;
+    h->coll.nslices = ns;
+    return PHTL_OK;
+}
+
+namespace {
+
+// Launch shape of the collective kernels for n particles (grid = resident capacity).
+int coll_launch(phtl_handle* h, void* const* c, int64_t n, int integrator, LaunchDesc& L)
+{
+    const int block = h->block > 0 ? h->block : 128;
+    const int occ = occupancy_coll(integrator, block, h->coll.nslices);
+    if (occ <= 0) return PHTL_E_INVALID;
+    const int64_t chunk = static_cast<int64_t>(block) * particles_per_thread(PHTL_F64);
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    int64_t cap = static_cast<int64_t>(occ) * h->nsm;
+    if (h->max_blocks > 0) cap = std::min<int64_t>(cap, h->max_blocks);
+    std::memset(&L, 0, sizeof(L));
+    bool vec = true;
+    for (int i = 0; i < 6; ++i) {
+        L.c[i] = c[i];
+        if (c[i] && (reinterpret_cast<uintptr_t>(c[i]) % 16) != 0) vec = false;
+    }
+    L.n = n;
+    L.scheme = integrator;
+    L.block = block;
+    L.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nchunks, cap)));
+    L.vec = vec ? 1 : 0;
+    L.nturns = 1;
+    return PHTL_OK;
+}
+
+int coll_ready(phtl_handle* h, int dtype)
+{
+    if (dtype != PHTL_F64) return PHTL_E_INVALID;  // the collective step runs in FP64
+    int rc = ensure_device(h);
+    if (rc != PHTL_OK) return rc;
+    if (!h->wake_mem || h->wake_device != h->device) return PHTL_E_INVALID;
+    return PHTL_OK;
+}
+
+int cuda_ok(cudaError_t e)
+{
+    if (e == cudaSuccess) return PHTL_OK;
+    cudaGetLastError();
+    return PHTL_E_CUDA;
+}
+
+}  // namespace
+
+int phtl_collective_kick(phtl_handle* h, void* z, void* dp, int64_t n, int dtype,
+                         uint32_t* counts_out, double* V_out, void* cuda_stream)
+{
+    void* c[6] = {z, dp, nullptr, nullptr, nullptr, nullptr};
+    int rc = check_track_args(h, c, n, 0, PHTL_LEAPFROG, dtype);
+    if (rc != PHTL_OK) return rc;
+    rc = coll_ready(h, dtype);
+    if (rc != PHTL_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int ns = h->coll.nslices;
+    unsigned* cnt = h->wake_counts;
+    rc = cuda_ok(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * ns, s));
+    if (rc == PHTL_OK && n > 0) {
+        LaunchDesc L;
+        rc = coll_launch(h, c, n, PHTL_LEAPFROG, L);
+        if (rc == PHTL_OK)
+            rc = cuda_ok(launch_coll_turn(L, h->mc[PHTL_LEAPFROG], h->coll, h->wake_V, cnt, nullptr,
+                                          -1, false, false, s));
+        if (rc == PHTL_OK) rc = cuda_ok(launch_wake_potential(cnt, h->wake_w, ns, h->wake_V, nullptr, s));
+        if (rc == PHTL_OK)
+            rc = cuda_ok(launch_coll_turn(L, h->mc[PHTL_LEAPFROG], h->coll, h->wake_V, nullptr, nullptr,
+                                          -1, true, false, s));
+        if (rc == PHTL_OK) h->stats.launches += 3;
+    } else if (rc == PHTL_OK) {
+        rc = cuda_ok(cudaMemsetAsync(h->wake_V, 0, sizeof(double) * ns, s));
+    }
+    if (rc == PHTL_OK && counts_out)
+        rc = cuda_ok(cudaMemcpyAsync(counts_out, cnt, sizeof(unsigned) * ns, cudaMemcpyDeviceToDevice, s));
+    if (rc == PHTL_OK && V_out)
+        rc = cuda_ok(cudaMemcpyAsync(V_out, h->wake_V, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s));
+    return rc;
+}
+
+int phtl_track_collective(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
+                          int64_t n, int64_t turns, int integrator, int dtype, void* cuda_stream)
+{
+    void* c[6] = {z, dp, x, xp, y, yp};
+    int rc = check_track_args(h, c, n, turns, integrator, dtype);
+    if (rc != PHTL_OK) return rc;
+    rc = coll_ready(h, dtype);
+    if (rc != PHTL_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double* mon = h->mon_rows;
+    const int64_t stride = h->mon_stride;
+    if (mon) {
+        const int64_t nrows = turns / stride + 1;
+        if (nrows > h->mon_cap) return PHTL_E_INVALID;
+        rc = cuda_ok(cudaMemsetAsync(mon, 0, static_cast<size_t>(nrows) * PHTL_MON_FIELDS * sizeof(double), s));
+        if (rc != PHTL_OK) return rc;
+    }
+    if (n == 0 || (turns == 0 && !mon)) return PHTL_OK;
+    LaunchDesc L;
+    rc = coll_launch(h, c, n, integrator, L);
+    if (rc != PHTL_OK) return rc;
+    const int ns = h->coll.nslices;
+    unsigned* cnt[2] = {h->wake_counts, h->wake_counts + ns};
+    const MapConsts& mc = h->mc[integrator];
+    rc = cuda_ok(cudaMemsetAsync(h->wake_counts, 0, 2 * sizeof(unsigned) * ns, s));
+    // turn t: the previous turn's kick (t > 1), its monitor row, the map, the slicing; then
+    // the potential of the new counts (clearing the other buffer for the next turn)
+    for (int64_t t = 1; t <= turns && rc == PHTL_OK; ++t) {
+        const int64_t rec = (mon && (t - 1) % stride == 0) ? (t - 1) / stride : -1;
+        rc = cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_V, cnt[t & 1], mon, rec, t > 1, true, s));
+        if (rc == PHTL_OK)
+            rc = cuda_ok(launch_wake_potential(cnt[t & 1], h->wake_w, ns, h->wake_V, cnt[(t + 1) & 1], s));
+    }
+    // the last turn's kick and monitor row
+    if (rc == PHTL_OK) {
+        const int64_t rec = (mon && turns % stride == 0) ? turns / stride : -1;
+        rc = cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_V, nullptr, mon, rec, turns > 0, false, s));
+    }
+    if (rc != PHTL_OK) return rc;
+    h->stats.launches += 2 * turns + 1;
     h->stats.particle_turns += n * turns;
     ++h->stats.calls;
     return PHTL_OK;

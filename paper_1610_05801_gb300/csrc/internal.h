@@ -94,6 +94,15 @@ struct RampTurn {
 };
 static_assert(sizeof(RampTurn) == 96, "RampTurn is 96 bytes");
 
+// Slicing grid and strength of the collective (wake) step.
+struct CollArgs {
+    double z_lo;     // first slice edge
+    double inv_dz;   // nslices / (z_hi - z_lo)
+    double alpha;    // kick per unit wake potential
+    int32_t nslices;
+    int32_t pad_;
+};
+
 // Where and when a launch records monitor rows.
 struct MonitorArgs {
     double* rows;      // device rows (PHTL_MON_FIELDS doubles each) or nullptr
@@ -184,6 +193,15 @@ int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, bo
 cudaError_t launch_ramp(const LaunchDesc& L, const MapConsts& c, const MonitorArgs& m,
                         const RampTurn* prog, int64_t turn0, int dtype, cudaStream_t s);
 int occupancy_ramp(int scheme, int dtype, int block);
+
+// Collective step kernels (track_collective.cu): one turn (optionally the previous turn's
+// kick first, a monitor row, the map, the slicing of the new z), and the wake potential.
+cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
+                             const double* V, unsigned* counts, double* mon_rows, int64_t rec_row,
+                             bool kick, bool map, cudaStream_t s);
+cudaError_t launch_wake_potential(const unsigned* counts, const double* w, int ns, double* V,
+                                  unsigned* clear, cudaStream_t s);
+int occupancy_coll(int scheme, int block, int nslices);
 
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).
 const void* general_kernel_single(int scheme, int dtype);

@@ -1,0 +1,241 @@
+// Collective step kernels: longitudinal slicing of the bunch, the wake potential of the
+// slice counts and the wake kick, interleaved with the one-turn map (FP64).
+//
+// The paper's conclusion names collective effects as the next workload after tracking; the
+// reading is stated in phtl.h at phtl_set_wake: after each turn's map, the particles are
+// counted on a uniform grid of slices, V_k = sum_{j >= k} c_j w[j - k] is formed, and each
+// particle inside the grid gets delta += alpha V_k of its own slice.
+//
+// The step needs the whole bunch's histogram between two turns, so the state cannot stay
+// in registers across turns as in the persistent kernels: each turn is one launch of
+// k_coll_turn (apply the previous turn's kick, record the monitor row, run the turn's map,
+// count the new z into a block-private shared-memory histogram that is flushed to the
+// global counts with one atomic per non-empty slice), then one launch of k_wake_potential
+// (counts and table staged in shared memory, one warp per slice, lane-strided partial sums
+// and a shuffle reduction; it also clears the other counts buffer for the next turn).  The state makes one HBM round trip per
+// turn (96 bytes per particle with both transverse planes), well under the FP64 work of
+// the turn on GB300.  Integer counts make the histogram exact and independent of the
+// order of the atomics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "monitor.cuh"
+#include "ops_f64.cuh"
+
+namespace phtl {
+namespace {
+
+using namespace f64;
+
+// Slice of z on the uniform grid [z_lo, z_lo + ns / inv_dz), or -1 outside: the same two
+// FP64 operations (subtract, multiply) as the definition give u, and the decision
+// 0 <= u < ns, k = floor(u) is taken exactly, on u's bit pattern: non-negative doubles
+// order like their bits (-0.0 counts as 0; NaN and +Inf lie above every finite bound),
+// and adding 2^52 rounded down leaves floor(u) in the low mantissa bits.  Three FP64
+// operations instead of the compare, floor and conversion instructions, which also run
+// on the FP64 pipe.  ns_bits: the bit pattern of (double)ns.
+__device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, long long ns_bits)
+{
+    const double u = __dmul_rn(__dsub_rn(z, z_lo), inv_dz);
+    long long b = __double_as_longlong(u);
+    if (b == static_cast<long long>(0x8000000000000000ull)) b = 0;  // -0.0
+    if (b < 0 || b >= ns_bits) return -1;
+    return __double2loint(__dadd_rd(u, 4503599627370496.0));      // floor(u) < ns <= 4096
+}
+
+// One turn of the collective tracking for one particle chunk per loop iteration.
+//   kick:  apply delta += alpha V[k] with the previous turn's potential V
+//   rec:   monitor row to record after the kick (-1: none)
+//   map:   run the turn's map and the transverse rotation
+//   cnt:   counts buffer for the new z (nullptr: no slicing)
+// Shared memory: ns uint32 histogram bins, then the monitor's 2 * warps * 16 DF2.
+template <int S>
+__global__ void __launch_bounds__(256, 2)
+    k_coll_turn(LaunchDesc L, MapConsts c, CollArgs A, const double* __restrict__ V,
+                unsigned* __restrict__ counts, double* __restrict__ mon_rows, int64_t rec_row,
+                int kick, int map)
+{
+    extern __shared__ double smem_d[];
+    unsigned* hist = reinterpret_cast<unsigned*>(smem_d);
+    double* msm = smem_d + (A.nslices + 1) / 2;  // 8-byte aligned after the bins
+    double* g[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) g[i] = static_cast<double*>(L.c[i]);
+    const bool hx = g[2] != nullptr, hy = g[4] != nullptr;
+    const bool vec = L.vec != 0;
+    if (counts)
+        for (int k = threadIdx.x; k < A.nslices; k += blockDim.x) hist[k] = 0u;
+    __syncthreads();
+    const int64_t chunk = static_cast<int64_t>(blockDim.x) * P;
+    const int64_t nchunks = (L.n + chunk - 1) / chunk;
+    int parity = 0;
+    double g1[4], g2[4];
+    slip_stages<S>(c, g1, g2);
+    const long long ns_bits = __double_as_longlong(static_cast<double>(A.nslices));
+    for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+        const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
+        double z[P], d[P], x[P], xp[P], y[P], yp[P];
+        load2(g[0], base, L.n, vec, z);
+        load2(g[1], base, L.n, vec, d);
+#pragma unroll
+        for (int p = 0; p < P; ++p) x[p] = xp[p] = y[p] = yp[p] = 0.0;
+        if (hx) {
+            load2(g[2], base, L.n, vec, x);
+            load2(g[3], base, L.n, vec, xp);
+        }
+        if (hy) {
+            load2(g[4], base, L.n, vec, y);
+            load2(g[5], base, L.n, vec, yp);
+        }
+        const int64_t left = L.n - base;
+        const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
+        if (kick) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int k = base + p < L.n ? slice_of(z[p], A.z_lo, A.inv_dz, ns_bits) : -1;
+                if (k >= 0) d[p] = fma(A.alpha, __ldg(V + k), d[p]);
+            }
+        }
+        if (mon_rows && rec_row >= 0) {
+            record<true>(z, d, x, xp, y, yp, cnt, hx, hy, msm, parity, mon_rows, rec_row);
+            parity ^= 1;
+        }
+        if (map) {
+            if (c.phis_zero) long_turn_nl<S, true>(z, d, c, c.dc, c.kw, c.kw2, g1, g2);
+            else long_turn_nl<S, false>(z, d, c, c.dc, c.kw, c.kw2, g1, g2);
+            transverse_gen(x, xp, y, yp, d, hx, hy, c);
+        }
+        if (counts) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int k = base + p < L.n ? slice_of(z[p], A.z_lo, A.inv_dz, ns_bits) : -1;
+                if (k >= 0) atomicAdd(hist + k, 1u);
+            }
+        }
+        store2(g[0], base, L.n, vec, z);
+        store2(g[1], base, L.n, vec, d);
+        if (hx) {
+            store2(g[2], base, L.n, vec, x);
+            store2(g[3], base, L.n, vec, xp);
+        }
+        if (hy) {
+            store2(g[4], base, L.n, vec, y);
+            store2(g[5], base, L.n, vec, yp);
+        }
+    }
+    if (counts) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < A.nslices; k += blockDim.x) {
+            const unsigned h = hist[k];
+            if (h) atomicAdd(counts + k, h);
+        }
+    }
+}
+
+// V_k = sum_{j >= k} c_j w[j - k].  Every block stages the counts (as doubles) and the wake
+// table in shared memory with one coalesced pass, then each of its warps forms the
+// potential of one slice at a time: lane-strided partial sums, then a butterfly
+// reduction (a fixed order, so the result does not depend on the launch).  Block 0 also
+// clears `clear` (the other counts buffer) for the next turn.  Shared memory: 2 ns doubles.
+__global__ void __launch_bounds__(256)
+    k_wake_potential(const unsigned* __restrict__ counts, const double* __restrict__ w, int ns,
+                     double* __restrict__ V, unsigned* __restrict__ clear)
+{
+    extern __shared__ double sm[];
+    double* c = sm;
+    double* ws = sm + ns;
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+        c[k] = static_cast<double>(counts[k]);
+        ws[k] = w[k];
+    }
+    __syncthreads();
+    if (clear && blockIdx.x == 0)
+        for (int k = threadIdx.x; k < ns; k += blockDim.x) clear[k] = 0u;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int k = blockIdx.x * wpb + (threadIdx.x >> 5); k < ns; k += gridDim.x * wpb) {
+        double s = 0.0;
+        for (int j = k + lane; j < ns; j += 32) s = fma(c[j], ws[j - k], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullMask, s, o);
+        if (lane == 0) V[k] = s;
+    }
+}
+
+template <int S>
+const void* coll_kernel_s()
+{
+    return reinterpret_cast<const void*>(&k_coll_turn<S>);
+}
+
+const void* coll_kernel(int scheme)
+{
+    if (scheme == PHTL_EULER_CROMER) return coll_kernel_s<PHTL_EULER_CROMER>();
+    if (scheme == PHTL_LEAPFROG) return coll_kernel_s<PHTL_LEAPFROG>();
+    if (scheme == PHTL_RUTH4) return coll_kernel_s<PHTL_RUTH4>();
+    if (scheme == PHTL_RK4) return coll_kernel_s<PHTL_RK4>();
+    return nullptr;
+}
+
+size_t coll_smem(int block, int ns)
+{
+    return static_cast<size_t>((ns + 1) / 2) * sizeof(double) + 2u * (block / 32) * 16 * sizeof(double);
+}
+
+}  // namespace
+
+int occupancy_coll(int scheme, int block, int nslices)
+{
+    const void* k = coll_kernel(scheme);
+    if (!k) return 0;
+    const size_t sm = coll_smem(block, nslices);
+    if (sm > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, sm) != cudaSuccess) return 0;
+    return nb;
+}
+
+cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
+                             const double* V, unsigned* counts, double* mon_rows, int64_t rec_row,
+                             bool kick, bool map, cudaStream_t s)
+{
+    const void* k = coll_kernel(L.scheme);
+    if (!k) return cudaErrorInvalidValue;
+    LaunchDesc Lc = L;
+    MapConsts cc = c;
+    CollArgs aa = A;
+    const double* vv = V;
+    unsigned* cn = counts;
+    double* mr = mon_rows;
+    int64_t rr = rec_row;
+    int kk = kick ? 1 : 0, mm = map ? 1 : 0;
+    void* args[] = {&Lc, &cc, &aa, &vv, &cn, &mr, &rr, &kk, &mm};
+    return cudaLaunchKernel(k, dim3(L.grid), dim3(L.block), args, coll_smem(L.block, A.nslices), s);
+}
+
+cudaError_t launch_wake_potential(const unsigned* counts, const double* w, int ns, double* V,
+                                  unsigned* clear, cudaStream_t s)
+{
+    const int block = 256;
+    // one slice per warp, at most 152 blocks: few enough that staging the table in every
+    // block stays cheap, enough to spread 4096 slices
+    const int grid = std::min((ns + 7) / 8, 152);
+    const size_t sm = 2u * static_cast<size_t>(ns) * sizeof(double);
+    // above 48 KB (more than 3072 slices; 64 KB at most) the launch must opt in, on the
+    // current device
+    if (sm > 48u * 1024u &&
+        cudaFuncSetAttribute(k_wake_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sm)) != cudaSuccess)
+        return cudaGetLastError();
+    k_wake_potential<<<grid, block, sm, s>>>(counts, w, ns, V, clear);
+    return cudaGetLastError();
+}
+
+}  // namespace phtl

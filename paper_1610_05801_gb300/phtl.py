@@ -58,6 +58,14 @@ class Derived(C.Structure):
                                                           ("my", C.c_double * 4)]
 
 
+class Wake(C.Structure):
+    _fields_ = [("z_lo", C.c_double), ("z_hi", C.c_double), ("alpha", C.c_double),
+                ("w", C.c_void_p), ("nslices", C.c_int32), ("pad_", C.c_int32)]
+
+
+MAX_SLICES = 4096
+
+
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("particle_turns", C.c_int64), ("calls", C.c_int64)]
 
@@ -132,6 +140,9 @@ SIGNATURES = {
     "phtl_eval_sin_kz": (_int, [C.c_double, _vp, _vp, _i64, _vp]),
     "phtl_set_programme": (_int, [_vp, _vp, _vp, _i64]),
     "phtl_track_programme": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _i64, _int, _int, _vp]),
+    "phtl_set_wake": (_int, [_vp, C.POINTER(Wake)]),
+    "phtl_collective_kick": (_int, [_vp, _vp, _vp, _i64, _int, _vp, _vp, _vp]),
+    "phtl_track_collective": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _int, _int, _vp]),
     "phtl_autotune": (_int, [_vp, _int, _int, _i64, C.c_double, C.POINTER(Tuning)]),
     "phtl_batch_create": (_int, [_vp, C.POINTER(Job), C.c_int32, C.c_int32, C.POINTER(_vp)]),
     "phtl_batch_run": (_int, [_vp, _vp]),
@@ -335,6 +346,32 @@ class Ring:
                                             int(turns), _integrator(integrator), dt,
                                             _stream_ptr(stream))
         _check(rc, "phtl_track_programme")
+
+    def set_wake(self, w=None, z_lo=0.0, z_hi=1.0, alpha=0.0):
+        """Attach a wake (phtl_set_wake): w[m] for m = 0..nslices-1 on the uniform slicing
+        [z_lo, z_hi), kick alpha * V; None detaches."""
+        if w is None:
+            _check(self._lib.phtl_set_wake(self._h, None), "phtl_set_wake")
+            return
+        wa = np.ascontiguousarray(w, dtype=np.float64)
+        wk = Wake(float(z_lo), float(z_hi), float(alpha), wa.ctypes.data, wa.shape[0], 0)
+        _check(self._lib.phtl_set_wake(self._h, C.byref(wk)), "phtl_set_wake")
+
+    def collective_kick(self, z, dp, counts_out=None, V_out=None, stream=None):
+        """One collective step (slice, potential, kick) on FP64 device tensors z, dp;
+        counts_out (int32/uint32 tensor) and V_out (float64 tensor) receive the step's
+        counts and potential when given."""
+        _check_tensor(z, "float64", "z")
+        _check_tensor(dp, "float64", "dp")
+        rc = self._lib.phtl_collective_kick(self._h, _ptr(z), _ptr(dp), z.numel(), F64,
+                                            _ptr(counts_out), _ptr(V_out), _stream_ptr(stream))
+        _check(rc, "phtl_collective_kick")
+
+    def track_collective(self, z, dp, x=None, xp=None, y=None, yp=None, turns=1,
+                         integrator="leapfrog", dtype="f64", stream=None):
+        """Turns of map + collective step (phtl_track_collective)."""
+        self._track(self._lib.phtl_track_collective, z, dp, x, xp, y, yp, turns, integrator,
+                    dtype, stream)
 
     def track_host(self, z, dp, x=None, xp=None, y=None, yp=None, turns=1,
                    integrator="leapfrog", dtype="f64", mon_rows=None, mon_stride=1):

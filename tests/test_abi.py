@@ -142,6 +142,37 @@ def test_programme_validation_needs_no_gpu():
     R.close()
 
 
+def test_wake_validation_needs_no_gpu():
+    """phtl_set_wake checks its arguments before it looks for a device."""
+    lib = phtl.load()
+    R = phtl.Ring(**synth.ring(4.5e6))
+    w = np.ones(16)
+
+    def setw(**over):
+        kw = dict(z_lo=-0.5, z_hi=0.5, alpha=1e-6, w=w.ctypes.data, nslices=16, pad_=0)
+        kw.update(over)
+        wk = phtl.Wake(**kw)
+        return lib.phtl_set_wake(R.handle, C.byref(wk))
+
+    assert setw(nslices=0) == phtl.E_INVALID
+    assert setw(nslices=phtl.MAX_SLICES + 1) == phtl.E_INVALID
+    assert setw(z_hi=-0.5) == phtl.E_INVALID
+    assert setw(alpha=float("nan")) == phtl.E_INVALID
+    assert setw(w=None) == phtl.E_INVALID
+    bad = w.copy()
+    bad[3] = float("inf")
+    assert setw(w=bad.ctypes.data) == phtl.E_INVALID
+    assert lib.phtl_set_wake(R.handle, None) == phtl.OK          # detach: nothing attached
+    assert lib.phtl_set_wake(None, None) == phtl.E_BADHANDLE
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert setw() == phtl.E_NODEVICE
+        z = np.zeros(8)
+        assert lib.phtl_track_collective(R.handle, z.ctypes.data, z.ctypes.data, None, None, None,
+                                         None, 8, 1, 1, 0, None) == phtl.E_NODEVICE
+    R.close()
+
+
 def test_derived_constants_match_oracle():
     for V in (2e6, 4.5e6):
         ring = synth.ring(V, transverse=True)

@@ -1,0 +1,226 @@
+"""GPU parity of the collective step (uniform slicing, wake potential, wake kick) against
+the oracle: one step on identical inputs, and turns of map + collective step.
+
+The reading (phtl.h at phtl_set_wake, and the oracle): after each turn's map the particles
+are counted on nslices uniform slices of [z_lo, z_hi), V_k = sum_{j >= k} c_j w[j - k],
+and delta += alpha V_k of the particle's own slice.
+
+Tolerances:
+  counts      bit-exact on identical z (the slice index is the same two FP64 operations on
+              both sides, so the integer decision is taken in the same precision);
+  V           <= 1e-13 of max |V| (the GPU sums each slice's terms in 32 lane-strided
+              partial sums, the oracle in order: rounding only);
+  one step    delta within 1e-15 absolute plus |alpha| times the V tolerance;
+  many turns  per particle <= 1e-10 of the bucket / transverse amplitude after 1000 turns,
+              moments <= 1e-9 (the map's tolerances; the kick adds a deterministic force
+              computed from identical counts on both sides as long as no particle sits
+              within rounding of a slice edge, a ~1e-4 chance at these sizes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1610_05801_gb300 import phtl  # noqa: E402
+from test_parity_gpu import moment_errors  # noqa: E402
+from test_widened_gpu import widened_inputs  # noqa: E402
+
+DEV = "cuda:0"
+SCHEMES4 = ("euler_cromer", "leapfrog", "ruth4", "rk4")
+
+
+def wake_table(ns, seed=3):
+    """A decaying oscillating wake (resonator-like), seeded amplitude jitter."""
+    m = np.arange(ns)
+    rng = np.random.default_rng(seed)
+    return np.exp(-m / (0.1 * ns + 1.0)) * np.cos(m / (0.05 * ns + 1.0)) * (1 + 0.1 * rng.normal(size=ns))
+
+
+def grid(ns, lo=-0.75, hi=0.75):
+    return dict(z_lo=lo, z_hi=hi, inv_dz=ns / (hi - lo))
+
+
+def _t(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device=DEV)
+
+
+@pytest.mark.parametrize("ns", [1, 7, 256, 4096])
+def test_one_step_matches_oracle(ns):
+    inp = widened_inputs(100_003, seed=31)
+    z, dp = inp["z"], inp["dp"]
+    g = grid(ns)
+    w = wake_table(ns)
+    alpha = -2e-9
+    R = phtl.Ring(**inp["ring"])
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha)
+    zt, dt = _t(z), _t(dp)
+    cnt = torch.zeros(ns, dtype=torch.int32, device=DEV)
+    V = torch.zeros(ns, dtype=torch.float64, device=DEV)
+    R.collective_kick(zt, dt, counts_out=cnt, V_out=V)
+    torch.cuda.synchronize()
+    z1, d1, c_ref, V_ref = oracle.collective_kick(z, dp, g["z_lo"], g["inv_dz"], w, alpha)
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), c_ref)
+    assert np.array_equal(zt.cpu().numpy(), z)
+    vs = np.max(np.abs(V_ref))
+    assert np.max(np.abs(V.cpu().numpy() - V_ref)) <= 1e-13 * vs
+    assert np.max(np.abs(dt.cpu().numpy() - d1)) <= 1e-15 + abs(alpha) * 1e-13 * vs
+    R.close()
+
+
+def test_range_edges_and_outside_particles():
+    """z_lo is in the first slice; z_hi, beyond, below and NaN-free outliers are neither
+    counted nor kicked."""
+    ns = 64
+    g = grid(ns)
+    dz = 1.5 / ns
+    z = np.array([g["z_lo"], g["z_hi"], 5.0, -5.0, g["z_lo"] + 0.5 * dz, g["z_hi"] - 1e-9])
+    dp = np.zeros(z.size)
+    R = phtl.Ring(**widened_inputs(1, seed=1)["ring"])
+    R.set_wake(np.ones(ns), g["z_lo"], g["z_hi"], 1.0)
+    zt, dt = _t(z), _t(dp)
+    cnt = torch.zeros(ns, dtype=torch.int32, device=DEV)
+    R.collective_kick(zt, dt, counts_out=cnt)
+    torch.cuda.synchronize()
+    _, d1, c_ref, _ = oracle.collective_kick(z, dp, g["z_lo"], g["inv_dz"], np.ones(ns), 1.0)
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), c_ref)
+    assert np.array_equal(dt.cpu().numpy(), d1)
+    assert d1[1] == 0.0 and d1[2] == 0.0 and d1[3] == 0.0
+    R.close()
+
+
+def run_gpu(inp, scheme, turns, w, g, alpha, stride=None, tuning=None):
+    R = phtl.Ring(**inp["ring"])
+    if tuning:
+        R.set_tuning(**tuning)
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha)
+    bufs = [_t(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    mon = None
+    if stride:
+        mon = torch.full((turns // stride + 1, phtl.MON_FIELDS), float("nan"), dtype=torch.float64,
+                         device=DEV)
+        R.set_monitor(mon, stride=stride)
+    R.track_collective(*bufs, turns=turns, integrator=scheme)
+    torch.cuda.synchronize()
+    out = [b.cpu().numpy() for b in bufs]
+    moms = phtl.moments_from_sums(mon.cpu().numpy()) if stride else None
+    R.close()
+    return out, moms
+
+
+def run_ref(inp, scheme, turns, w, g, alpha, stride=None):
+    r = oracle.track_collective(inp["d"], scheme, inp["z"], inp["dp"], inp["x"], inp["xp"],
+                                inp["y"], inp["yp"], turns=turns, z_lo=g["z_lo"],
+                                inv_dz=g["inv_dz"], w=w, alpha=alpha, moments=bool(stride),
+                                stride=stride or 1)
+    return list(r[:6]), r[6]
+
+
+def errors(inp, got, ref):
+    d = inp["d"]
+    zb, db = math.pi / d.k, 2 * math.sqrt(d.A / (d.k * d.etaC))
+    e = [np.max(np.abs(got[0] - ref[0])) / zb, np.max(np.abs(got[1] - ref[1])) / db]
+    for i in (2, 4):
+        amp = np.max(np.hypot(ref[i], 50.0 * ref[i + 1]))
+        e += [np.max(np.abs(got[i] - ref[i])) / amp, np.max(np.abs(got[i + 1] - ref[i + 1])) * 50.0 / amp]
+    return max(e)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES4)
+def test_turns_match_oracle(scheme):
+    inp = widened_inputs(4099, seed=33)
+    ns = 128
+    g, w = grid(ns), wake_table(ns)
+    alpha = -5e-9       # the wake's kick ~1e-3 of the RF kick at the bunch centre
+    got, mg = run_gpu(inp, scheme, 1000, w, g, alpha, stride=7,
+                      tuning=dict(block_threads=64))
+    ref, mr = run_ref(inp, scheme, 1000, w, g, alpha, stride=7)
+    assert errors(inp, got, ref) < 1e-10, errors(inp, got, ref)
+    assert moment_errors(inp["d"], mg, mr) < 1e-9
+    # the wake does act: without it the bunch ends elsewhere
+    plain, _ = run_ref(inp, scheme, 1000, w, g, 0.0)
+    assert np.max(np.abs(plain[1] - ref[1])) > 1e3 * np.max(np.abs(got[1] - ref[1]))
+
+
+def test_turns_widened_double_rf():
+    inp = widened_inputs(2049, seed=35, eta1=0.05, eta2=2.0, xi_x=5.0, xi_y=-3.0,
+                         harmonic2=2 * 4620, voltage2_V=1.35e6, phi2_rad=0.0)
+    ns = 200
+    g, w = grid(ns), wake_table(ns, seed=4)
+    got, mg = run_gpu(inp, "ruth4", 500, w, g, 3e-9, stride=50)
+    ref, mr = run_ref(inp, "ruth4", 500, w, g, 3e-9, stride=50)
+    assert errors(inp, got, ref) < 1e-10
+    assert moment_errors(inp["d"], mg, mr) < 1e-9
+
+
+@pytest.mark.parametrize("scheme", ["euler_cromer", "ruth4"])
+def test_zero_strength_equals_plain_tracking(scheme):
+    """alpha = 0: bitwise the particles of phtl_track (the turn's map is the same code; the
+    state's HBM round trip per turn is exact)."""
+    inp = widened_inputs(3001, seed=37)
+    g, w = grid(64), wake_table(64)
+    a, _ = run_gpu(inp, scheme, 300, w, g, 0.0)
+    R = phtl.Ring(**inp["ring"])
+    bufs = [_t(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    R.track(*bufs, turns=300, integrator=scheme)
+    torch.cuda.synchronize()
+    for u, b in zip(a, bufs):
+        assert np.array_equal(u, b.cpu().numpy())
+    R.close()
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_ragged_small(n):
+    inp = widened_inputs(n, seed=39 + n)
+    g, w = grid(16), wake_table(16)
+    got, mg = run_gpu(inp, "leapfrog", 300, w, g, -1e-6, stride=100, tuning=dict(block_threads=32))
+    ref, mr = run_ref(inp, "leapfrog", 300, w, g, -1e-6, stride=100)
+    assert errors(inp, got, ref) < 1e-10
+    assert np.allclose(mg[:, :4], mr[:, :4], rtol=1e-9, atol=1e-18)
+
+
+def test_zero_turns_records_row_zero_only():
+    inp = widened_inputs(1001, seed=41)
+    g, w = grid(32), wake_table(32)
+    got, mg = run_gpu(inp, "leapfrog", 0, w, g, 1e-6, stride=1)
+    for k, u in zip(("z", "dp", "x", "xp", "y", "yp"), got):
+        assert np.array_equal(u, inp[k])
+    ref = oracle.moments(*[inp[k] for k in ("z", "dp", "x", "xp", "y", "yp")])
+    assert mg.shape[0] == 1 and np.allclose(mg[0], ref, rtol=1e-9, atol=1e-18)
+
+
+def test_argument_errors():
+    inp = widened_inputs(64, seed=43)
+    R = phtl.Ring(**inp["ring"])
+    bufs = [_t(inp[k]) for k in ("z", "dp")]
+    with pytest.raises(phtl.PhtlError) as e:
+        R.track_collective(*bufs, turns=1)              # no wake attached
+    assert e.value.code == phtl.E_INVALID
+    R.set_wake(np.ones(8), -0.5, 0.5, 1e-6)
+    f32 = [torch.zeros(128, dtype=torch.float32, device=DEV) for _ in range(2)]
+    with pytest.raises(phtl.PhtlError) as e:
+        R.track_collective(*f32, turns=1, dtype="f32cd")
+    assert e.value.code == phtl.E_INVALID
+    R.set_wake(None)
+    with pytest.raises(phtl.PhtlError):
+        R.collective_kick(*bufs)
+    R.close()
+
+
+def test_full_size_sampled():
+    """1e6 particles x 100 turns in the default launch shape against the oracle run on the
+    whole bunch (the step couples every particle): a 512-particle sample and the moments."""
+    n = 1_000_000
+    inp = widened_inputs(n, seed=45)
+    ns = 512
+    g, w = grid(ns), wake_table(ns)
+    got, mg = run_gpu(inp, "leapfrog", 100, w, g, -5e-11, stride=50)
+    ref, mr = run_ref(inp, "leapfrog", 100, w, g, -5e-11, stride=50)
+    idx = np.random.default_rng(9).choice(n, 512, replace=False)
+    sub = dict(inp)
+    assert errors(sub, [u[idx] for u in got], [v[idx] for v in ref]) < 1e-10
+    assert moment_errors(inp["d"], mg, mr) < 1e-9
