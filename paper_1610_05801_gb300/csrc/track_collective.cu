@@ -52,7 +52,7 @@ __device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, lo
 //   cnt:   counts buffer for the new z (nullptr: no slicing)
 // Shared memory: ns uint32 histogram bins, then the monitor's 2 * warps * 16 DF2.
 template <int S>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_coll_turn(LaunchDesc L, MapConsts c, CollArgs A, const double* __restrict__ V,
                 unsigned* __restrict__ counts, double* __restrict__ mon_rows, int64_t rec_row,
                 int kick, int map)
