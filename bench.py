@@ -65,11 +65,12 @@ WORKLOADS = {
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
         voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5, ramp=dict(p0_end=30e9)),
     # collective step after every turn: 512 uniform slices on [-0.75, 0.75) m, a decaying
-    # oscillating (resonator-like) wake table, kick -5e-11 x V; leap-frog, 1e6 x 1e4 turns
+    # oscillating (resonator-like) wake table, kick -5e-11 x V plus space charge 1e-9 x the
+    # line-density slope; leap-frog, 1e6 x 1e4 turns
     "collective_wake_1e6x1e4_lf_f64": dict(
         n=1_000_000, turns=10_000, schemes=("leapfrog",), dtype="f64", voltage=4.5e6,
         transverse=True, stride=1, sep_frac=0.5,
-        wake=dict(nslices=512, z_lo=-0.75, z_hi=0.75, alpha=-5e-11)),
+        wake=dict(nslices=512, z_lo=-0.75, z_hi=0.75, alpha=-5e-11, alpha_sc=1e-9)),
     # small case for quick checks (not a bench line)
     "tiny": dict(n=20_000, turns=200, schemes=("euler_cromer", "leapfrog", "ruth4"),
                  dtype="f64", voltage=4.5e6, transverse=True, stride=1),
@@ -296,7 +297,7 @@ def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
                 wk = wl["wake"]
                 O.track_collective(d, s, z, dp, *tr, turns=turns, z_lo=wk["z_lo"],
                                    inv_dz=wk["nslices"] / (wk["z_hi"] - wk["z_lo"]),
-                                   w=wake_table(wl), alpha=wk["alpha"],
+                                   w=wake_table(wl), alpha=wk["alpha"], alpha_sc=wk["alpha_sc"],
                                    moments=wl["stride"] > 0, stride=max(1, wl["stride"]))
             else:
                 O.track(d, s, z, dp, *tr, turns=turns, moments=wl["stride"] > 0,
@@ -378,7 +379,7 @@ def run_ours(args, wl_name, wl):
     track = R.track_perturn if wl.get("perturn") else R.track
     if wl.get("wake"):
         wk = wl["wake"]
-        R.set_wake(wake_table(wl), wk["z_lo"], wk["z_hi"], wk["alpha"])
+        R.set_wake(wake_table(wl), wk["z_lo"], wk["z_hi"], wk["alpha"], wk["alpha_sc"])
         track = R.track_collective
     if wl.get("ramp"):
         R.set_programme(*ramp_programme(wl))

@@ -257,33 +257,39 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
 
 #define PHTL_MAX_SLICES 4096
 
-/* A wake acting through the bunch's own longitudinal line density.  The paper's
- * conclusion names collective effects as the next workload after single-particle tracking
- * and prints no formulas; the reading:
+/* A wake and longitudinal space charge acting through the bunch's own line density.  The
+ * paper's conclusion names collective effects as the next workload after single-particle
+ * tracking and prints no formulas; the reading:
  *   - slicing: nslices uniform slices on [z_lo, z_hi); particle i lies in slice
  *     k = floor((z_i - z_lo) * inv_dz), inv_dz = nslices / (z_hi - z_lo) (both FP64,
  *     subtract then multiply), when 0 <= k < nslices; c_k counts slice k's particles;
  *   - wake potential: V_k = sum over j >= k of c_j w[j - k] (z > 0 is ahead: a slice feels
  *     the slices ahead of it and itself; w[m] is the wake of one macro-particle m slices
  *     ahead, in units chosen with alpha);
- *   - kick: delta_i += alpha V_k(i) for the particles inside the grid (others unchanged). */
+ *   - space charge: D_k = (c_{k+1} - c_{k-1}) / 2, one-sided (c_1 - c_0, c_{N-1} - c_{N-2})
+ *     at the ends, 0 for a single slice: the slope of the line density in counts per slice,
+ *     to which the longitudinal space-charge field is proportional;
+ *   - kick: delta_i += alpha V_k(i) + alpha_sc D_k(i) for the particles inside the grid
+ *     (others unchanged). */
 typedef struct phtl_wake {
     double z_lo, z_hi;  /* slicing range [z_lo, z_hi), z_hi > z_lo                     */
     double alpha;       /* kick per unit wake potential                              */
+    double alpha_sc;    /* kick per unit density slope (space charge; 0 = none)       */
     const double* w;    /* host array of nslices wake samples w[0 .. nslices-1]       */
     int32_t nslices;    /* 1 .. PHTL_MAX_SLICES                                       */
     int32_t pad_;
 } phtl_wake;
 
 /* Attach a wake to the handle (NULL detaches).  The table is copied into library-owned
- * device memory together with the slice counts (two buffers) and the potential: 24 bytes
- * per slice, freed by phtl_destroy or a detaching call.  Synchronous.
+ * device memory together with the slice counts (two buffers), the wake potential and the
+ * per-slice kick: 32 bytes per slice, freed by phtl_destroy or a detaching call.
+ * Synchronous.
  * Errors: PHTL_E_BADHANDLE; PHTL_E_INVALID (nslices out of range, z_hi <= z_lo,
  * non-finite values, w NULL); PHTL_E_NODEVICE; PHTL_E_NOMEM.                           */
 int phtl_set_wake(phtl_handle* h, const phtl_wake* wake);
 
-/* One collective step on (z, dp) without the map: slice the bunch, form the potential,
- * kick.  FP64 buffers of n doubles (dtype must be PHTL_F64).  counts_out (nslices
+/* One collective step on (z, dp) without the map: slice the bunch, form the wake
+ * potential and the density slope, kick.  FP64 buffers of n doubles (dtype must be PHTL_F64).  counts_out (nslices
  * uint32) and V_out (nslices doubles): device pointers or NULL, receive the step's
  * counts and potential.  Stream-ordered.  Errors: as phtl_track, plus PHTL_E_INVALID
  * (no wake attached, or attached on another device, or dtype other than PHTL_F64).     */

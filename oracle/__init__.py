@@ -117,11 +117,11 @@ class Oracle:
         L.ref_track_ramp.restype = C.c_int
         lp = C.POINTER(C.c_long)
         L.ref_collective_kick.argtypes = [dp, dp, C.c_long, C.c_double, C.c_double, C.c_long, dp,
-                                          C.c_double, lp, dp]
+                                          C.c_double, C.c_double, lp, dp]
         L.ref_collective_kick.restype = C.c_int
         L.ref_track_collective.argtypes = [C.POINTER(RefDerived), C.c_int, dp, dp, dp, dp, dp, dp,
                                            C.c_long, C.c_long, C.c_double, C.c_double, C.c_long,
-                                           dp, C.c_double, dp, C.c_long]
+                                           dp, C.c_double, C.c_double, dp, C.c_long]
         L.ref_track_collective.restype = C.c_int
         L.ref_num_threads.argtypes = []
         L.ref_num_threads.restype = C.c_int
@@ -215,7 +215,7 @@ class Oracle:
             raise ValueError(f"ref_track_ramp returned {rc}")
         return (*arrs, mom)
 
-    def collective_kick(self, z, dp, z_lo, inv_dz, w, alpha):
+    def collective_kick(self, z, dp, z_lo, inv_dz, w, alpha, alpha_sc=0.0):
         """One collective step on copies of (z, dp): returns (z, dp, counts, V)."""
         z = np.array(z, dtype=np.float64, copy=True, order="C").reshape(-1)
         dp = np.array(dp, dtype=np.float64, copy=True, order="C").reshape(-1)
@@ -224,15 +224,15 @@ class Oracle:
         counts = np.zeros(ns, dtype=np.int64)
         V = np.zeros(ns)
         rc = self.lib.ref_collective_kick(_ptr(z), _ptr(dp), z.shape[0], float(z_lo), float(inv_dz),
-                                          ns, _ptr(w), float(alpha),
+                                          ns, _ptr(w), float(alpha), float(alpha_sc),
                                           counts.ctypes.data_as(C.POINTER(C.c_long)), _ptr(V))
         if rc != 0:
             raise ValueError(f"ref_collective_kick returned {rc}")
         return z, dp, counts, V
 
     def track_collective(self, d: RefDerived, scheme, z, dp, x=None, xp=None, y=None, yp=None,
-                         turns=1, z_lo=-1.0, inv_dz=1.0, w=(0.0,), alpha=0.0, moments=False,
-                         stride=1):
+                         turns=1, z_lo=-1.0, inv_dz=1.0, w=(0.0,), alpha=0.0, alpha_sc=0.0,
+                         moments=False, stride=1):
         """Turns of map + collective step on copies of the inputs; returns like track()."""
         if isinstance(scheme, str):
             scheme = SCHEMES[scheme]
@@ -243,7 +243,8 @@ class Oracle:
         mom = np.zeros((turns // stride + 1, NMOM)) if moments else None
         rc = self.lib.ref_track_collective(C.byref(d), int(scheme), *[_ptr(a) for a in arrs], n,
                                            int(turns), float(z_lo), float(inv_dz), w.shape[0],
-                                           _ptr(w), float(alpha), _ptr(mom), int(stride))
+                                           _ptr(w), float(alpha), float(alpha_sc), _ptr(mom),
+                                           int(stride))
         if rc != 0:
             raise ValueError(f"ref_track_collective returned {rc}")
         return (*arrs, mom)

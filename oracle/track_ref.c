@@ -36,7 +36,8 @@
  *   ramp (optional): per-turn eta_n, A_n, phi_s,n from a programme V_n, p0_n, with delta and
  *           the slopes re-expressed by p0_n / p0_{n+1} after each turn
  *   collective step (optional, after each turn): slice counts on a uniform grid, wake
- *           potential V_k = sum_{j >= k} c_j w[j - k], kick delta += alpha V_k
+ *           potential V_k = sum_{j >= k} c_j w[j - k], line-density slope D_k (central
+ *           difference of the counts), kick delta += alpha V_k + alpha_sc D_k
  * Derived constants (all FP64, from the ring parameters):
  *   beta*gamma = p0/m; gamma = sqrt(1 + (beta gamma)^2); beta = beta gamma / gamma
  *   eta = 1/gamma_t^2 - 1/gamma^2;  k = 2 pi h / C;  A = q V / (beta p0)   [p0 in eV/c]
@@ -487,7 +488,11 @@ int ref_track_ramp(const ref_derived* d, const double* tc, long nprog, long turn
  *   - wake potential: V_k = sum over j >= k of c_j w[j - k] (z > 0 is ahead: a slice is
  *     affected by the slices ahead of it and by itself, w[m] being the wake of one
  *     macro-particle m slices ahead), summed in order of increasing j;
- *   - kick: delta_i <- delta_i + alpha V_k(i) for the particles inside the range.
+ *   - space charge: D_k = (c_{k+1} - c_{k-1}) / 2, one-sided (c_1 - c_0, c_{N-1} - c_{N-2})
+ *     at the ends and 0 for a single slice: the slope of the line density in counts per
+ *     slice (the longitudinal space-charge field is proportional to it);
+ *   - kick: delta_i <- delta_i + (alpha V_k(i) + alpha_sc D_k(i)) for the particles inside
+ *     the range.
  * inv_dz is passed in (computed once by the caller) so that both implementations decide
  * the slice index from the same two operations.
  */
@@ -515,25 +520,38 @@ void ref_wake_potential(const long* counts, const double* w, long nslices, doubl
     }
 }
 
-/* One collective step on (z, dp): slice, wake potential, kick.  counts / V (optional)
- * receive the step's slice counts and potential. */
+/* Slope of the line density: central differences of the counts, one-sided at the ends. */
+void ref_density_slope(const long* counts, long nslices, double* D)
+{
+    long k;
+    if (nslices == 1) { D[0] = 0.0; return; }
+    D[0] = (double)(counts[1] - counts[0]);
+    D[nslices - 1] = (double)(counts[nslices - 1] - counts[nslices - 2]);
+    for (k = 1; k < nslices - 1; k++) D[k] = 0.5 * (double)(counts[k + 1] - counts[k - 1]);
+}
+
+/* One collective step on (z, dp): slice, wake potential, density slope, kick.  counts / V
+ * (optional) receive the step's slice counts and wake potential. */
 int ref_collective_kick(double* z, double* dp, long n, double z_lo, double inv_dz, long nslices,
-                        const double* w, double alpha, long* counts, double* V)
+                        const double* w, double alpha, double alpha_sc, long* counts, double* V)
 {
     long i;
     if (n < 0 || nslices < 1 || !w || (n > 0 && (!z || !dp))) return REF_E_INVALID;
     long* c = counts ? counts : (long*)malloc(sizeof(long) * nslices);
     double* v = V ? V : (double*)malloc(sizeof(double) * nslices);
-    if (!c || !v) return REF_E_INVALID;
+    double* sd = (double*)malloc(sizeof(double) * nslices);
+    if (!c || !v || !sd) return REF_E_INVALID;
     ref_slice_counts(z, n, z_lo, inv_dz, nslices, c);
     ref_wake_potential(c, w, nslices, v);
+    ref_density_slope(c, nslices, sd);
     for (i = 0; i < n; i++) {
         double u = (z[i] - z_lo) * inv_dz;
         if (u >= 0.0 && u < (double)nslices) {
             long k = (long)floor(u);
-            if (k < nslices) dp[i] = dp[i] + alpha * v[k];
+            if (k < nslices) dp[i] = dp[i] + (alpha * v[k] + alpha_sc * sd[k]);
         }
     }
+    free(sd);
     if (!counts) free(c);
     if (!V) free(v);
     return REF_OK;
@@ -545,7 +563,7 @@ int ref_collective_kick(double* z, double* dp, long n, double z_lo, double inv_d
 int ref_track_collective(const ref_derived* d, int scheme, double* z, double* dp, double* x,
                          double* xp, double* y, double* yp, long n, long turns, double z_lo,
                          double inv_dz, long nslices, const double* w, double alpha,
-                         double* moments, long stride)
+                         double alpha_sc, double* moments, long stride)
 {
     long t, i;
     if (!d || n < 0 || turns < 0 || scheme < 0 || scheme > 3) return REF_E_INVALID;
@@ -566,7 +584,7 @@ int ref_track_collective(const ref_derived* d, int scheme, double* z, double* dp
             ref_transverse(d, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
                            doy ? &y[i] : 0, doy ? &yp[i] : 0);
         }
-        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, c, v);
+        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, alpha_sc, c, v);
         if (moments && t % stride == 0)
             ref_moments(z, dp, dox ? x : 0, dox ? xp : 0, doy ? y : 0, doy ? yp : 0, n,
                         moments + (t / stride) * REF_NMOM);

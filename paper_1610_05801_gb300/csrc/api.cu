@@ -263,7 +263,7 @@ void free_wake(phtl_handle* h)
         if (cur >= 0 && cur != h->wake_device) cudaSetDevice(cur);
     }
     h->wake_mem = nullptr;
-    h->wake_w = h->wake_V = nullptr;
+    h->wake_w = h->wake_V = h->wake_U = nullptr;
     h->wake_counts = nullptr;
     h->wake_device = -1;
     std::memset(&h->coll, 0, sizeof(h->coll));
@@ -797,7 +797,8 @@ int phtl_set_wake(phtl_handle* h, const phtl_wake* wk)
     }
     const int ns = wk->nslices;
     if (ns < 1 || ns > PHTL_MAX_SLICES || !wk->w || !std::isfinite(wk->z_lo) ||
-        !std::isfinite(wk->z_hi) || !(wk->z_hi > wk->z_lo) || !std::isfinite(wk->alpha))
+        !std::isfinite(wk->z_hi) || !(wk->z_hi > wk->z_lo) || !std::isfinite(wk->alpha) ||
+        !std::isfinite(wk->alpha_sc))
         return PHTL_E_INVALID;
     for (int m = 0; m < ns; ++m)
         if (!std::isfinite(wk->w[m])) return PHTL_E_INVALID;
@@ -806,7 +807,7 @@ int phtl_set_wake(phtl_handle* h, const phtl_wake* wk)
     int rc = ensure_device(h);
     if (rc != PHTL_OK) return rc;
     free_wake(h);
-    const size_t bytes = static_cast<size_t>(ns) * (2 * sizeof(double) + 2 * sizeof(unsigned));
+    const size_t bytes = static_cast<size_t>(ns) * (3 * sizeof(double) + 2 * sizeof(unsigned));
     if (cudaMalloc(&h->wake_mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         h->wake_mem = nullptr;
@@ -814,9 +815,10 @@ int phtl_set_wake(phtl_handle* h, const phtl_wake* wk)
     }
     h->wake_w = static_cast<double*>(h->wake_mem);
     h->wake_V = h->wake_w + ns;
-    h->wake_counts = reinterpret_cast<unsigned*>(h->wake_V + ns);
+    h->wake_U = h->wake_V + ns;
+    h->wake_counts = reinterpret_cast<unsigned*>(h->wake_U + ns);
     if (cudaMemcpy(h->wake_w, wk->w, sizeof(double) * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(h->wake_V, 0, sizeof(double) * ns + 2 * sizeof(unsigned) * ns) != cudaSuccess) {
+        cudaMemset(h->wake_V, 0, 2 * sizeof(double) * ns + 2 * sizeof(unsigned) * ns) != cudaSuccess) {
         cudaGetLastError();
         free_wake(h);
         return PHTL_E_CUDA;
@@ -825,6 +827,7 @@ int phtl_set_wake(phtl_handle* h, const phtl_wake* wk)
     h->coll.z_lo = wk->z_lo;
     h->coll.inv_dz = inv_dz;
     h->coll.alpha = wk->alpha;
+    h->coll.alpha_sc = wk->alpha_sc;
     h->coll.nslices = ns;
     return PHTL_OK;
 }
@@ -890,15 +893,16 @@ int phtl_collective_kick(phtl_handle* h, void* z, void* dp, int64_t n, int dtype
         LaunchDesc L;
         rc = coll_launch(h, c, n, PHTL_LEAPFROG, L);
         if (rc == PHTL_OK)
-            rc = cuda_ok(launch_coll_turn(L, h->mc[PHTL_LEAPFROG], h->coll, h->wake_V, cnt, nullptr,
+            rc = cuda_ok(launch_coll_turn(L, h->mc[PHTL_LEAPFROG], h->coll, h->wake_U, cnt, nullptr,
                                           -1, false, false, s));
-        if (rc == PHTL_OK) rc = cuda_ok(launch_wake_potential(cnt, h->wake_w, ns, h->wake_V, nullptr, s));
         if (rc == PHTL_OK)
-            rc = cuda_ok(launch_coll_turn(L, h->mc[PHTL_LEAPFROG], h->coll, h->wake_V, nullptr, nullptr,
+            rc = cuda_ok(launch_wake_potential(cnt, h->wake_w, h->coll, h->wake_V, h->wake_U, nullptr, s));
+        if (rc == PHTL_OK)
+            rc = cuda_ok(launch_coll_turn(L, h->mc[PHTL_LEAPFROG], h->coll, h->wake_U, nullptr, nullptr,
                                           -1, true, false, s));
         if (rc == PHTL_OK) h->stats.launches += 3;
     } else if (rc == PHTL_OK) {
-        rc = cuda_ok(cudaMemsetAsync(h->wake_V, 0, sizeof(double) * ns, s));
+        rc = cuda_ok(cudaMemsetAsync(h->wake_V, 0, 2 * sizeof(double) * ns, s));
     }
     if (rc == PHTL_OK && counts_out)
         rc = cuda_ok(cudaMemcpyAsync(counts_out, cnt, sizeof(unsigned) * ns, cudaMemcpyDeviceToDevice, s));
@@ -936,14 +940,15 @@ int phtl_track_collective(phtl_handle* h, void* z, void* dp, void* x, void* xp, 
     // the potential of the new counts (clearing the other buffer for the next turn)
     for (int64_t t = 1; t <= turns && rc == PHTL_OK; ++t) {
         const int64_t rec = (mon && (t - 1) % stride == 0) ? (t - 1) / stride : -1;
-        rc = cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_V, cnt[t & 1], mon, rec, t > 1, true, s));
+        rc = cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_U, cnt[t & 1], mon, rec, t > 1, true, s));
         if (rc == PHTL_OK)
-            rc = cuda_ok(launch_wake_potential(cnt[t & 1], h->wake_w, ns, h->wake_V, cnt[(t + 1) & 1], s));
+            rc = cuda_ok(launch_wake_potential(cnt[t & 1], h->wake_w, h->coll, h->wake_V, h->wake_U,
+                                               cnt[(t + 1) & 1], s));
     }
     // the last turn's kick and monitor row
     if (rc == PHTL_OK) {
         const int64_t rec = (mon && turns % stride == 0) ? turns / stride : -1;
-        rc = cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_V, nullptr, mon, rec, turns > 0, false, s));
+        rc = cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_U, nullptr, mon, rec, turns > 0, false, s));
     }
     if (rc != PHTL_OK) return rc;
     h->stats.launches += 2 * turns + 1;

@@ -99,6 +99,7 @@ struct CollArgs {
     double z_lo;     // first slice edge
     double inv_dz;   // nslices / (z_hi - z_lo)
     double alpha;    // kick per unit wake potential
+    double alpha_sc; // kick per unit line-density slope (space charge)
     int32_t nslices;
     int32_t pad_;
 };
@@ -195,12 +196,13 @@ cudaError_t launch_ramp(const LaunchDesc& L, const MapConsts& c, const MonitorAr
 int occupancy_ramp(int scheme, int dtype, int block);
 
 // Collective step kernels (track_collective.cu): one turn (optionally the previous turn's
-// kick first, a monitor row, the map, the slicing of the new z), and the wake potential.
+// kick U first, a monitor row, the map, the slicing of the new z), and the per-slice wake
+// potential V and kick U.
 cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
-                             const double* V, unsigned* counts, double* mon_rows, int64_t rec_row,
+                             const double* U, unsigned* counts, double* mon_rows, int64_t rec_row,
                              bool kick, bool map, cudaStream_t s);
-cudaError_t launch_wake_potential(const unsigned* counts, const double* w, int ns, double* V,
-                                  unsigned* clear, cudaStream_t s);
+cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
+                                  double* V, double* U, unsigned* clear, cudaStream_t s);
 int occupancy_coll(int scheme, int block, int nslices);
 
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).

@@ -4,7 +4,8 @@
 // The paper's conclusion names collective effects as the next workload after tracking; the
 // reading is stated in phtl.h at phtl_set_wake: after each turn's map, the particles are
 // counted on a uniform grid of slices, V_k = sum_{j >= k} c_j w[j - k] is formed, and each
-// particle inside the grid gets delta += alpha V_k of its own slice.
+// particle inside the grid gets delta += alpha V_k + alpha_sc D_k of its own slice, D_k the
+// central difference of the counts (longitudinal space charge).
 //
 // The step needs the whole bunch's histogram between two turns, so the state cannot stay
 // in registers across turns as in the persistent kernels: each turn is one launch of
@@ -46,14 +47,14 @@ __device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, lo
 }
 
 // One turn of the collective tracking for one particle chunk per loop iteration.
-//   kick:  apply delta += alpha V[k] with the previous turn's potential V
+//   kick:  apply delta += U[k] with the previous turn's per-slice kick U
 //   rec:   monitor row to record after the kick (-1: none)
 //   map:   run the turn's map and the transverse rotation
 //   cnt:   counts buffer for the new z (nullptr: no slicing)
 // Shared memory: ns uint32 histogram bins, then the monitor's 2 * warps * 16 DF2.
 template <int S>
 __global__ void __launch_bounds__(256, 3)
-    k_coll_turn(LaunchDesc L, MapConsts c, CollArgs A, const double* __restrict__ V,
+    k_coll_turn(LaunchDesc L, MapConsts c, CollArgs A, const double* __restrict__ U,
                 unsigned* __restrict__ counts, double* __restrict__ mon_rows, int64_t rec_row,
                 int kick, int map)
 {
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const int k = base + p < L.n ? slice_of(z[p], A.z_lo, A.inv_dz, ns_bits) : -1;
-                if (k >= 0) d[p] = fma(A.alpha, __ldg(V + k), d[p]);
+                if (k >= 0) d[p] = d[p] + __ldg(U + k);
             }
         }
         if (mon_rows && rec_row >= 0) {
@@ -134,14 +135,16 @@ __global__ void __launch_bounds__(256, 3)
     }
 }
 
-// V_k = sum_{j >= k} c_j w[j - k].  Every block stages the counts (as doubles) and the wake
-// table in shared memory with one coalesced pass, then each of its warps forms the
-// potential of one slice at a time: lane-strided partial sums, then a butterfly
+// V_k = sum_{j >= k} c_j w[j - k] and the per-slice kick U_k = alpha V_k + alpha_sc D_k,
+// D_k the central difference of the counts (one-sided at the ends).  Every block stages the
+// counts (as doubles) and the wake table in shared memory with one coalesced pass, then
+// each of its warps forms one slice at a time: lane-strided partial sums, then a butterfly
 // reduction (a fixed order, so the result does not depend on the launch).  Block 0 also
 // clears `clear` (the other counts buffer) for the next turn.  Shared memory: 2 ns doubles.
 __global__ void __launch_bounds__(256)
     k_wake_potential(const unsigned* __restrict__ counts, const double* __restrict__ w, int ns,
-                     double* __restrict__ V, unsigned* __restrict__ clear)
+                     double alpha, double alpha_sc, double* __restrict__ V, double* __restrict__ U,
+                     unsigned* __restrict__ clear)
 {
     extern __shared__ double sm[];
     double* c = sm;
@@ -160,7 +163,13 @@ __global__ void __launch_bounds__(256)
         for (int j = k + lane; j < ns; j += 32) s = fma(c[j], ws[j - k], s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullMask, s, o);
-        if (lane == 0) V[k] = s;
+        if (lane == 0) {
+            double dk = 0.0;
+            if (ns > 1)
+                dk = k == 0 ? c[1] - c[0] : k == ns - 1 ? c[ns - 1] - c[ns - 2] : 0.5 * (c[k + 1] - c[k - 1]);
+            V[k] = s;
+            U[k] = fma(alpha, s, alpha_sc * dk);
+        }
     }
 }
 
@@ -203,7 +212,7 @@ int occupancy_coll(int scheme, int block, int nslices)
 }
 
 cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
-                             const double* V, unsigned* counts, double* mon_rows, int64_t rec_row,
+                             const double* U, unsigned* counts, double* mon_rows, int64_t rec_row,
                              bool kick, bool map, cudaStream_t s)
 {
     const void* k = coll_kernel(L.scheme);
@@ -211,7 +220,7 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
     LaunchDesc Lc = L;
     MapConsts cc = c;
     CollArgs aa = A;
-    const double* vv = V;
+    const double* vv = U;
     unsigned* cn = counts;
     double* mr = mon_rows;
     int64_t rr = rec_row;
@@ -220,9 +229,10 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
     return cudaLaunchKernel(k, dim3(L.grid), dim3(L.block), args, coll_smem(L.block, A.nslices), s);
 }
 
-cudaError_t launch_wake_potential(const unsigned* counts, const double* w, int ns, double* V,
-                                  unsigned* clear, cudaStream_t s)
+cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
+                                  double* V, double* U, unsigned* clear, cudaStream_t s)
 {
+    const int ns = A.nslices;
     const int block = 256;
     // one slice per warp, at most 152 blocks: few enough that staging the table in every
     // block stays cheap, enough to spread 4096 slices
@@ -234,7 +244,7 @@ cudaError_t launch_wake_potential(const unsigned* counts, const double* w, int n
         cudaFuncSetAttribute(k_wake_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sm)) != cudaSuccess)
         return cudaGetLastError();
-    k_wake_potential<<<grid, block, sm, s>>>(counts, w, ns, V, clear);
+    k_wake_potential<<<grid, block, sm, s>>>(counts, w, ns, A.alpha, A.alpha_sc, V, U, clear);
     return cudaGetLastError();
 }
 

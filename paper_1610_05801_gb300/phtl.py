@@ -60,7 +60,8 @@ class Derived(C.Structure):
 
 class Wake(C.Structure):
     _fields_ = [("z_lo", C.c_double), ("z_hi", C.c_double), ("alpha", C.c_double),
-                ("w", C.c_void_p), ("nslices", C.c_int32), ("pad_", C.c_int32)]
+                ("alpha_sc", C.c_double), ("w", C.c_void_p), ("nslices", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 MAX_SLICES = 4096
@@ -347,14 +348,16 @@ class Ring:
                                             _stream_ptr(stream))
         _check(rc, "phtl_track_programme")
 
-    def set_wake(self, w=None, z_lo=0.0, z_hi=1.0, alpha=0.0):
+    def set_wake(self, w=None, z_lo=0.0, z_hi=1.0, alpha=0.0, alpha_sc=0.0):
         """Attach a wake (phtl_set_wake): w[m] for m = 0..nslices-1 on the uniform slicing
-        [z_lo, z_hi), kick alpha * V; None detaches."""
+        [z_lo, z_hi), kick alpha * V + alpha_sc * D (D: slope of the line density, the
+        space-charge term); None detaches."""
         if w is None:
             _check(self._lib.phtl_set_wake(self._h, None), "phtl_set_wake")
             return
         wa = np.ascontiguousarray(w, dtype=np.float64)
-        wk = Wake(float(z_lo), float(z_hi), float(alpha), wa.ctypes.data, wa.shape[0], 0)
+        wk = Wake(float(z_lo), float(z_hi), float(alpha), float(alpha_sc), wa.ctypes.data,
+                  wa.shape[0], 0)
         _check(self._lib.phtl_set_wake(self._h, C.byref(wk)), "phtl_set_wake")
 
     def collective_kick(self, z, dp, counts_out=None, V_out=None, stream=None):

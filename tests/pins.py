@@ -887,6 +887,35 @@ def pin_collective_turn_order(O):
             assert np.array_equal(u, v), scheme
 
 
+def pin_collective_space_charge(O):
+    """The space-charge term is the slope of the line density: for counts on an exact
+    parabola c_k = A - B (k - k0)^2 (the parabolic bunch) the kick is exactly linear in the
+    slice, alpha_sc (-2 B (k - k0)) in the interior; a linear profile gives the same slope
+    everywhere, ends included (one-sided there); a symmetric profile an antisymmetric
+    kick; a flat one none."""
+    ns, lo, hi, inv, dz = _slices_setup(ns=41, lo=-1.025, hi=1.025)
+    s = 2.0 ** -20
+    k = np.arange(ns)
+
+    def kicks(pattern):
+        z = np.concatenate([np.full(c, lo + (i + 0.5) * dz) for i, c in enumerate(pattern)])
+        _, dp1, counts, _ = O.collective_kick(z, np.zeros(z.size), lo, inv, np.zeros(ns), 0.0, s)
+        assert np.array_equal(counts, pattern)
+        per_slice = np.full(ns, np.nan)
+        idx = np.floor((z - lo) * inv).astype(int)
+        per_slice[idx] = dp1
+        return per_slice
+
+    B, k0 = 3, 20
+    para = 1300 - B * (k - k0) ** 2
+    kp = kicks(para)
+    assert np.array_equal(kp[1:-1], s * (-2.0 * B * (k[1:-1] - k0)))
+    assert np.array_equal(kp[:ns // 2], -kp[ns // 2 + 1:][::-1])
+    lin = 5 + 7 * k
+    assert np.all(kicks(lin) == s * 7.0)
+    assert np.all(kicks(np.full(ns, 9)) == 0.0)
+
+
 ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_pendulum_detuning, pin_separatrix, pin_time_reversal, pin_inverse_map,
             pin_symplectic, pin_energy_order, pin_symmetry_and_fixed_point,
@@ -897,6 +926,6 @@ ALL_FAST = (pin_textbook_constants, pin_stability_rules, pin_linear_closed_form,
             pin_double_rf_energy, pin_ramp_constant_programme, pin_ramp_synchronous_phase,
             pin_ramp_adiabatic_invariant, pin_ramp_normalised_emittance,
             pin_collective_slicing, pin_collective_wake_library, pin_collective_kick,
-            pin_collective_turn_order)
+            pin_collective_turn_order, pin_collective_space_charge)
 # pins that need mpmath (skipped where it is missing)
 ALL_MPMATH = (pin_rk4_order,)

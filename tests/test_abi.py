@@ -158,6 +158,7 @@ def test_wake_validation_needs_no_gpu():
     assert setw(nslices=phtl.MAX_SLICES + 1) == phtl.E_INVALID
     assert setw(z_hi=-0.5) == phtl.E_INVALID
     assert setw(alpha=float("nan")) == phtl.E_INVALID
+    assert setw(alpha_sc=float("inf")) == phtl.E_INVALID
     assert setw(w=None) == phtl.E_INVALID
     bad = w.copy()
     bad[3] = float("inf")

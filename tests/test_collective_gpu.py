@@ -3,7 +3,8 @@ the oracle: one step on identical inputs, and turns of map + collective step.
 
 The reading (phtl.h at phtl_set_wake, and the oracle): after each turn's map the particles
 are counted on nslices uniform slices of [z_lo, z_hi), V_k = sum_{j >= k} c_j w[j - k],
-and delta += alpha V_k of the particle's own slice.
+D_k the central difference of the counts (space charge), and delta += alpha V_k +
+alpha_sc D_k of the particle's own slice.
 
 Tolerances:
   counts      bit-exact on identical z (the slice index is the same two FP64 operations on
@@ -49,26 +50,30 @@ def _t(a):
     return torch.tensor(np.asarray(a, dtype=np.float64), device=DEV)
 
 
-@pytest.mark.parametrize("ns", [1, 7, 256, 4096])
-def test_one_step_matches_oracle(ns):
+@pytest.mark.parametrize("ns,alpha_sc", [(1, 0.0), (7, 0.0), (256, 0.0), (4096, 0.0), (2, 3e-9),
+                                         (256, 3e-9), (4096, -1e-8)])
+def test_one_step_matches_oracle(ns, alpha_sc):
     inp = widened_inputs(100_003, seed=31)
     z, dp = inp["z"], inp["dp"]
     g = grid(ns)
     w = wake_table(ns)
     alpha = -2e-9
     R = phtl.Ring(**inp["ring"])
-    R.set_wake(w, g["z_lo"], g["z_hi"], alpha)
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha, alpha_sc)
     zt, dt = _t(z), _t(dp)
     cnt = torch.zeros(ns, dtype=torch.int32, device=DEV)
     V = torch.zeros(ns, dtype=torch.float64, device=DEV)
     R.collective_kick(zt, dt, counts_out=cnt, V_out=V)
     torch.cuda.synchronize()
-    z1, d1, c_ref, V_ref = oracle.collective_kick(z, dp, g["z_lo"], g["inv_dz"], w, alpha)
+    z1, d1, c_ref, V_ref = oracle.collective_kick(z, dp, g["z_lo"], g["inv_dz"], w, alpha, alpha_sc)
     assert np.array_equal(cnt.cpu().numpy().astype(np.int64), c_ref)
     assert np.array_equal(zt.cpu().numpy(), z)
     vs = np.max(np.abs(V_ref))
     assert np.max(np.abs(V.cpu().numpy() - V_ref)) <= 1e-13 * vs
-    assert np.max(np.abs(dt.cpu().numpy() - d1)) <= 1e-15 + abs(alpha) * 1e-13 * vs
+    # the kick: wake part to the V tolerance; the space-charge part (half-integer slopes
+    # times alpha_sc) and the sum to rounding
+    sc = abs(alpha_sc) * max(1, int(np.max(c_ref)))
+    assert np.max(np.abs(dt.cpu().numpy() - d1)) <= 1e-15 + abs(alpha) * 1e-13 * vs + 4e-16 * sc
     R.close()
 
 
@@ -93,11 +98,11 @@ def test_range_edges_and_outside_particles():
     R.close()
 
 
-def run_gpu(inp, scheme, turns, w, g, alpha, stride=None, tuning=None):
+def run_gpu(inp, scheme, turns, w, g, alpha, stride=None, tuning=None, alpha_sc=0.0):
     R = phtl.Ring(**inp["ring"])
     if tuning:
         R.set_tuning(**tuning)
-    R.set_wake(w, g["z_lo"], g["z_hi"], alpha)
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha, alpha_sc)
     bufs = [_t(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
     mon = None
     if stride:
@@ -112,11 +117,11 @@ def run_gpu(inp, scheme, turns, w, g, alpha, stride=None, tuning=None):
     return out, moms
 
 
-def run_ref(inp, scheme, turns, w, g, alpha, stride=None):
+def run_ref(inp, scheme, turns, w, g, alpha, stride=None, alpha_sc=0.0):
     r = oracle.track_collective(inp["d"], scheme, inp["z"], inp["dp"], inp["x"], inp["xp"],
                                 inp["y"], inp["yp"], turns=turns, z_lo=g["z_lo"],
-                                inv_dz=g["inv_dz"], w=w, alpha=alpha, moments=bool(stride),
-                                stride=stride or 1)
+                                inv_dz=g["inv_dz"], w=w, alpha=alpha, alpha_sc=alpha_sc,
+                                moments=bool(stride), stride=stride or 1)
     return list(r[:6]), r[6]
 
 
@@ -144,6 +149,20 @@ def test_turns_match_oracle(scheme):
     # the wake does act: without it the bunch ends elsewhere
     plain, _ = run_ref(inp, scheme, 1000, w, g, 0.0)
     assert np.max(np.abs(plain[1] - ref[1])) > 1e3 * np.max(np.abs(got[1] - ref[1]))
+
+
+@pytest.mark.parametrize("scheme", ["leapfrog", "ruth4"])
+def test_turns_with_space_charge(scheme):
+    """Wake and space charge together over 1000 turns."""
+    inp = widened_inputs(4099, seed=34)
+    ns = 128
+    g, w = grid(ns), wake_table(ns, seed=5)
+    got, mg = run_gpu(inp, scheme, 1000, w, g, -3e-9, stride=11, alpha_sc=2e-8)
+    ref, mr = run_ref(inp, scheme, 1000, w, g, -3e-9, stride=11, alpha_sc=2e-8)
+    assert errors(inp, got, ref) < 1e-10, errors(inp, got, ref)
+    assert moment_errors(inp["d"], mg, mr) < 1e-9
+    nosc, _ = run_ref(inp, scheme, 1000, w, g, -3e-9)
+    assert np.max(np.abs(nosc[1] - ref[1])) > 1e3 * np.max(np.abs(got[1] - ref[1]))
 
 
 def test_turns_widened_double_rf():

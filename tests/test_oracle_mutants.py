@@ -95,15 +95,20 @@ MUTANTS = {
                               "            k = (long)floor(u + 0.5);\n            if (k < nslices) counts[k]++;"),
     "slice_includes_z_hi": ("        if (u >= 0.0 && u < (double)nslices) {\n            k = (long)floor(u);",
                             "        if (u >= 0.0 && u <= (double)nslices) {\n            k = (long)floor(u) - (u == (double)nslices);"),
-    "collective_kick_sign": ("if (k < nslices) dp[i] = dp[i] + alpha * v[k];",
-                             "if (k < nslices) dp[i] = dp[i] - alpha * v[k];"),
+    "collective_kick_sign": ("if (k < nslices) dp[i] = dp[i] + (alpha * v[k] + alpha_sc * sd[k]);",
+                             "if (k < nslices) dp[i] = dp[i] + (-alpha * v[k] + alpha_sc * sd[k]);"),
+    "space_charge_sign": ("if (k < nslices) dp[i] = dp[i] + (alpha * v[k] + alpha_sc * sd[k]);",
+                          "if (k < nslices) dp[i] = dp[i] + (alpha * v[k] - alpha_sc * sd[k]);"),
+    "space_charge_forward_difference": ("D[k] = 0.5 * (double)(counts[k + 1] - counts[k - 1]);",
+                                        "D[k] = (double)(counts[k + 1] - counts[k]);"),
+    "space_charge_end_zero": ("D[0] = (double)(counts[1] - counts[0]);", "D[0] = 0.0;"),
     "collective_before_map": ("""        for (i = 0; i < n; i++) {
             ref_turn(d, scheme, 1.0, &z[i], &dp[i]);
             ref_transverse(d, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
                            doy ? &y[i] : 0, doy ? &yp[i] : 0);
         }
-        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, c, v);""",
-                              """        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, c, v);
+        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, alpha_sc, c, v);""",
+                              """        ref_collective_kick(z, dp, n, z_lo, inv_dz, nslices, w, alpha, alpha_sc, c, v);
         for (i = 0; i < n; i++) {
             ref_turn(d, scheme, 1.0, &z[i], &dp[i]);
             ref_transverse(d, 1.0, dox, doy, dp[i], dox ? &x[i] : 0, dox ? &xp[i] : 0,
