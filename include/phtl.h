@@ -289,18 +289,22 @@ typedef struct phtl_wake {
 int phtl_set_wake(phtl_handle* h, const phtl_wake* wake);
 
 /* One collective step on (z, dp) without the map: slice the bunch, form the wake
- * potential and the density slope, kick.  FP64 buffers of n doubles (dtype must be PHTL_F64).  counts_out (nslices
- * uint32) and V_out (nslices doubles): device pointers or NULL, receive the step's
- * counts and potential.  Stream-ordered.  Errors: as phtl_track, plus PHTL_E_INVALID
- * (no wake attached, or attached on another device, or dtype other than PHTL_F64).     */
+ * potential and the density slope, kick.  Buffers and layout as phtl_track (every dtype;
+ * the potential and the kick are formed in FP64, the FP32 types add the kick as a float
+ * pair; PHTL_F32C decides the slice in FP64 from hi + comp, PHTL_F32CD / PHTL_F32CS in
+ * double-float).  counts_out (nslices uint32) and V_out (nslices doubles): device
+ * pointers or NULL, receive the step's counts and wake potential.  Stream-ordered.
+ * Errors: as phtl_track, plus PHTL_E_INVALID (no wake attached, or attached on another
+ * device).                                                                              */
 int phtl_collective_kick(phtl_handle* h, void* z, void* dp, int64_t n, int dtype,
                          uint32_t* counts_out, double* V_out, void* cuda_stream);
 
 /* Track `turns` turns, each the scheme's one-turn map and the transverse rotation (as
  * phtl_track, widened map included) followed by the collective step on the whole bunch.
- * FP64 only; every integrator (RK4 included); the monitor (phtl_set_monitor) records
- * after each full turn, collective kick included.  Each turn is two kernel launches
- * (turn + slicing, potential), the state making one HBM round trip per turn.
+ * Every dtype (as phtl_collective_kick) and every integrator (RK4 included); the monitor
+ * (phtl_set_monitor) records after each full turn, collective kick included.  Each turn
+ * is two kernel launches (turn + slicing, potential), the state making one HBM round
+ * trip per turn.
  * Stream-ordered.  Errors: as phtl_collective_kick.                                     */
 int phtl_track_collective(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
                           int64_t n, int64_t turns, int integrator, int dtype, void* cuda_stream);

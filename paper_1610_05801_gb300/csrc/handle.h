@@ -41,11 +41,13 @@ struct phtl_handle {
     int64_t ramp_turns = 0;
     int ramp_device = -1;
     // collective step (phtl_set_wake): one device block holding the wake table w[ns],
-    // the wake potential V[ns], the per-slice kick U[ns] and two counts buffers [2][ns]
+    // the wake potential V[ns], the per-slice kick U[ns] (and as float pairs U2[ns]) and
+    // two counts buffers [2][ns]
     void* wake_mem = nullptr;
     double* wake_w = nullptr;
     double* wake_V = nullptr;
     double* wake_U = nullptr;
+    float2* wake_U2 = nullptr;   // U as float pairs for the FP32 paths
     unsigned* wake_counts = nullptr;
     phtl::CollArgs coll{};
     int wake_device = -1;

@@ -102,6 +102,8 @@ struct CollArgs {
     double alpha_sc; // kick per unit line-density slope (space charge)
     int32_t nslices;
     int32_t pad_;
+    // double-float copies for the FP32 paths (value = hi + lo)
+    float z_lo_h, z_lo_l, inv_dz_h, inv_dz_l;
 };
 
 // Where and when a launch records monitor rows.
@@ -202,8 +204,14 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
                              const double* U, unsigned* counts, double* mon_rows, int64_t rec_row,
                              bool kick, bool map, cudaStream_t s);
 cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
-                                  double* V, double* U, unsigned* clear, cudaStream_t s);
+                                  double* V, double* U, float2* U2, unsigned* clear, cudaStream_t s);
 int occupancy_coll(int scheme, int block, int nslices);
+// The FP32-compensated turn kernel (track_collective_f32.cu): the same steps on float-pair
+// state, the kick read from U2 (U as hi + lo floats).
+cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
+                                 const float2* U2, unsigned* counts, double* mon_rows,
+                                 int64_t rec_row, bool kick, bool map, int dtype, cudaStream_t s);
+int occupancy_coll_f32(int scheme, int dtype, int block, int nslices);
 
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).
 const void* general_kernel_single(int scheme, int dtype);

@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(256, 3)
 }
 
 // V_k = sum_{j >= k} c_j w[j - k] and the per-slice kick U_k = alpha V_k + alpha_sc D_k,
-// D_k the central difference of the counts (one-sided at the ends).  Every block stages the
+// D_k the central difference of the counts (one-sided at the ends); U2 holds U as float
+// pairs for the FP32 paths.  Every block stages the
 // counts (as doubles) and the wake table in shared memory with one coalesced pass, then
 // each of its warps forms one slice at a time: lane-strided partial sums, then a butterfly
 // reduction (a fixed order, so the result does not depend on the launch).  Block 0 also
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(256, 3)
 __global__ void __launch_bounds__(256)
     k_wake_potential(const unsigned* __restrict__ counts, const double* __restrict__ w, int ns,
                      double alpha, double alpha_sc, double* __restrict__ V, double* __restrict__ U,
-                     unsigned* __restrict__ clear)
+                     float2* __restrict__ U2, unsigned* __restrict__ clear)
 {
     extern __shared__ double sm[];
     double* c = sm;
@@ -168,7 +169,10 @@ __global__ void __launch_bounds__(256)
             if (ns > 1)
                 dk = k == 0 ? c[1] - c[0] : k == ns - 1 ? c[ns - 1] - c[ns - 2] : 0.5 * (c[k + 1] - c[k - 1]);
             V[k] = s;
-            U[k] = fma(alpha, s, alpha_sc * dk);
+            const double u = fma(alpha, s, alpha_sc * dk);
+            U[k] = u;
+            const DF2 p = split_bits(u);  // the FP32 paths' copy
+            U2[k] = make_float2(p.h, p.l);
         }
     }
 }
@@ -230,7 +234,7 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
 }
 
 cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
-                                  double* V, double* U, unsigned* clear, cudaStream_t s)
+                                  double* V, double* U, float2* U2, unsigned* clear, cudaStream_t s)
 {
     const int ns = A.nslices;
     const int block = 256;
@@ -244,7 +248,7 @@ cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const
         cudaFuncSetAttribute(k_wake_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sm)) != cudaSuccess)
         return cudaGetLastError();
-    k_wake_potential<<<grid, block, sm, s>>>(counts, w, ns, A.alpha, A.alpha_sc, V, U, clear);
+    k_wake_potential<<<grid, block, sm, s>>>(counts, w, ns, A.alpha, A.alpha_sc, V, U, U2, clear);
     return cudaGetLastError();
 }
 

@@ -360,13 +360,16 @@ class Ring:
                   wa.shape[0], 0)
         _check(self._lib.phtl_set_wake(self._h, C.byref(wk)), "phtl_set_wake")
 
-    def collective_kick(self, z, dp, counts_out=None, V_out=None, stream=None):
-        """One collective step (slice, potential, kick) on FP64 device tensors z, dp;
-        counts_out (int32/uint32 tensor) and V_out (float64 tensor) receive the step's
-        counts and potential when given."""
-        _check_tensor(z, "float64", "z")
-        _check_tensor(dp, "float64", "dp")
-        rc = self._lib.phtl_collective_kick(self._h, _ptr(z), _ptr(dp), z.numel(), F64,
+    def collective_kick(self, z, dp, counts_out=None, V_out=None, dtype="f64", stream=None):
+        """One collective step (slice, potential, kick) on device tensors z, dp (float64 for
+        "f64", float32 [hi | comp] for the FP32 types); counts_out (int32/uint32 tensor) and
+        V_out (float64 tensor) receive the step's counts and wake potential when given."""
+        dt = _dtype(dtype)
+        want = "float64" if dt == F64 else "float32"
+        _check_tensor(z, want, "z")
+        _check_tensor(dp, want, "dp")
+        n = z.numel() if dt == F64 else z.numel() // 2
+        rc = self._lib.phtl_collective_kick(self._h, _ptr(z), _ptr(dp), n, dt,
                                             _ptr(counts_out), _ptr(V_out), _stream_ptr(stream))
         _check(rc, "phtl_collective_kick")
 

@@ -220,14 +220,69 @@ def test_argument_errors():
         R.track_collective(*bufs, turns=1)              # no wake attached
     assert e.value.code == phtl.E_INVALID
     R.set_wake(np.ones(8), -0.5, 0.5, 1e-6)
-    f32 = [torch.zeros(128, dtype=torch.float32, device=DEV) for _ in range(2)]
-    with pytest.raises(phtl.PhtlError) as e:
-        R.track_collective(*f32, turns=1, dtype="f32cd")
-    assert e.value.code == phtl.E_INVALID
+    rc = phtl.load().phtl_track_collective(R.handle, bufs[0].data_ptr(), bufs[1].data_ptr(), None,
+                                           None, None, None, 64, 1, 9, 0, None)
+    assert rc == phtl.E_INVALID                          # no such integrator
     R.set_wake(None)
     with pytest.raises(phtl.PhtlError):
         R.collective_kick(*bufs)
     R.close()
+
+
+def _pair(a):
+    return torch.tensor(phtl.split_f32c(np.asarray(a, dtype=np.float64)), dtype=torch.float32,
+                        device=DEV)
+
+
+@pytest.mark.parametrize("dtype", ["f32c", "f32cd", "f32cs"])
+def test_one_step_f32(dtype):
+    """FP32 types: the same counts (slice decisions in FP64 from hi + comp, or exactly from
+    the double-float u: the inputs lie nowhere near an edge to 1e-12), the kick to the
+    pair's precision (FP32CS: one float, the pair's truncated high part)."""
+    inp = widened_inputs(50_001, seed=51)
+    z, dp = inp["z"], inp["dp"]
+    ns = 300
+    g, w = grid(ns), wake_table(ns)
+    alpha, alpha_sc = -2e-9, 5e-9
+    R = phtl.Ring(**inp["ring"])
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha, alpha_sc)
+    zt, dt = _pair(z), _pair(dp)
+    cnt = torch.zeros(ns, dtype=torch.int32, device=DEV)
+    R.collective_kick(zt, dt, counts_out=cnt, dtype=dtype)
+    torch.cuda.synchronize()
+    _, d1, c_ref, V_ref = oracle.collective_kick(z, dp, g["z_lo"], g["inv_dz"], w, alpha, alpha_sc)
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), c_ref)
+    got = phtl.join_f32c(dt.cpu().numpy())
+    kick = np.max(np.abs(d1 - dp))
+    # FP32CS adds the high float of the kick's pair: the FP64 value's top 24 bits,
+    # truncated (relative error below 2^-23)
+    tol = 1e-12 * np.max(np.abs(dp)) + (2.5e-7 * kick if dtype == "f32cs" else 1e-12 * kick)
+    assert np.max(np.abs(got - d1)) <= tol, (np.max(np.abs(got - d1)), tol)
+    R.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32c", "f32cd", "f32cs"])
+@pytest.mark.parametrize("scheme", ["leapfrog", "ruth4"])
+def test_turns_f32(dtype, scheme):
+    """FP32 types over 1000 turns against the FP64 oracle, with the tolerances of the FP32
+    paths (per particle 1e-8 / 2e-2, moments 1e-6 / 2e-3)."""
+    inp = widened_inputs(2051, seed=53)
+    ns = 128
+    g, w = grid(ns), wake_table(ns)
+    R = phtl.Ring(**inp["ring"])
+    R.set_wake(w, g["z_lo"], g["z_hi"], -5e-9, 1e-8)
+    bufs = [_pair(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    mon = torch.zeros((1000 // 10 + 1, phtl.MON_FIELDS), dtype=torch.float64, device=DEV)
+    R.set_monitor(mon, stride=10)
+    R.track_collective(*bufs, turns=1000, integrator=scheme, dtype=dtype)
+    torch.cuda.synchronize()
+    got = [phtl.join_f32c(b.cpu().numpy()) for b in bufs]
+    mg = phtl.moments_from_sums(mon.cpu().numpy())
+    R.close()
+    ref, mr = run_ref(inp, scheme, 1000, w, g, -5e-9, stride=10, alpha_sc=1e-8)
+    tol = {"f32c": (1e-8, 1e-6), "f32cd": (1e-8, 1e-6), "f32cs": (2e-2, 2e-3)}[dtype]
+    assert errors(inp, got, ref) < tol[0], errors(inp, got, ref)
+    assert moment_errors(inp["d"], mg, mr) < tol[1]
 
 
 def test_full_size_sampled():
