@@ -3,10 +3,11 @@
  * tracking, after A. Oeftiger, "Parallelisation of PyHEADTAIL" (2014).
  *
  * What the library computes (the paper names the schemes but prints no formulas; the
- * readings below are the textbook single-harmonic synchrotron map):
+ * readings below are the textbook synchrotron map):
  *   Sec. 1.1.2  longitudinal phase space (z, delta), integrated turn by turn for each
  *               macro-particle independently, by Euler-Cromer (1st order), leap-frog
- *               (2nd-order Verlet, drift-kick-drift) or a 4th-order Ruth scheme:
+ *               (2nd-order Verlet, drift-kick-drift), a 4th-order Ruth scheme or classic
+ *               RK4 (see PHTL_RK4):
  *                 kick  K(w): phi = phi_s + k z;  delta += w A (sin phi - sin phi_s)
  *                 drift D(w): z -= w eta(delta) C delta,
  *                             eta(delta) = eta0 + eta1 delta + eta2 delta^2
@@ -23,7 +24,10 @@
  *               longitudinal step (xi = 0: one matrix for all).
  *   Sec. 2.3    particles are independent, turns are sequential; the turn loop runs
  *               inside the kernel (state in registers), bounded per launch.
- * Per-turn bunch moments are accumulated into a caller-owned monitor buffer.
+ * Per-turn bunch moments are accumulated into a caller-owned monitor buffer.  Beyond the
+ * single-harmonic map: a second RF system (phtl_params.voltage2_V), a ramp programme
+ * (phtl_set_programme) and a collective step of slicing, wake and space-charge kick
+ * (phtl_set_wake), each stated where it is declared.
  *
  * Conventions for every entry point:
  *   - Return value: PHTL_OK (0) or a negative PHTL_E_* code.  No C++ exception

@@ -121,7 +121,7 @@ struct LaunchDesc {
     void* c[6];        // z, dp, x, xp, y, yp (nullptr = plane off)
     int64_t n;         // particles
     int32_t nturns;    // turns in this launch
-    int32_t scheme;    // PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4
+    int32_t scheme;    // PHTL_EULER_CROMER | PHTL_LEAPFROG | PHTL_RUTH4 | PHTL_RK4
     int32_t block;     // threads per block
     int32_t grid;      // blocks
     int32_t vec;       // nonzero: all pointers 16-byte aligned (128-bit loads)
@@ -168,6 +168,37 @@ inline void fill_float_weights(JobDesc& J)
         J.kw2_hi[i] = static_cast<float>(J.kw2[i]);
         J.kw2_lo[i] = static_cast<float>(J.kw2[i] - static_cast<double>(J.kw2_hi[i]));
     }
+}
+
+// Programmatic dependent launch (sm_90 and later): the kernel is launched while the previous
+// kernel on the stream is still finishing, and must execute griddep_wait() before it touches
+// memory that kernel writes (griddepcontrol.wait returns once the preceding grid has
+// completed and its memory operations are visible).  griddep_launch_dependents() lets the
+// next kernel's launch start early.
+// Build option PHTL_NO_PDL: plain stream-ordered launches instead (for comparison).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+inline cudaError_t launch_pdl(const void* k, dim3 grid, dim3 block, void** args, size_t smem,
+                              cudaStream_t s)
+{
+#ifdef PHTL_NO_PDL
+    return cudaLaunchKernel(k, grid, block, args, smem, s);
+#endif
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 // Launchers (one per kernel family); return cudaGetLastError() of the launch.

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(256, 3)
     if (counts)
         for (int k = threadIdx.x; k < A.nslices; k += blockDim.x) hist[k] = 0u;
     __syncthreads();
+    griddep_wait();  // the previous turn's state, kick and cleared counts
     const int64_t chunk = static_cast<int64_t>(blockDim.x) * P;
     const int64_t nchunks = (L.n + chunk - 1) / chunk;
     int parity = 0;
@@ -126,6 +127,9 @@ __global__ void __launch_bounds__(256, 3)
             store2(g[5], base, L.n, vec, yp);
         }
     }
+    // the potential kernel may launch now (it waits for this grid's completion); not earlier,
+    // so that its blocks do not sit on SM slots while this grid still works
+    griddep_launch_dependents();
     if (counts) {
         __syncthreads();
         for (int k = threadIdx.x; k < A.nslices; k += blockDim.x) {
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(256)
     extern __shared__ double sm[];
     double* c = sm;
     double* ws = sm + ns;
+    griddep_wait();  // the counts of the turn kernel that precedes this launch
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
         c[k] = static_cast<double>(counts[k]);
         ws[k] = w[k];
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(256)
             U2[k] = make_float2(p.h, p.l);
         }
     }
+    griddep_launch_dependents();
 }
 
 template <int S>
@@ -230,7 +236,7 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
     int64_t rr = rec_row;
     int kk = kick ? 1 : 0, mm = map ? 1 : 0;
     void* args[] = {&Lc, &cc, &aa, &vv, &cn, &mr, &rr, &kk, &mm};
-    return cudaLaunchKernel(k, dim3(L.grid), dim3(L.block), args, coll_smem(L.block, A.nslices), s);
+    return launch_pdl(k, dim3(L.grid), dim3(L.block), args, coll_smem(L.block, A.nslices), s);
 }
 
 cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
@@ -248,8 +254,12 @@ cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const
         cudaFuncSetAttribute(k_wake_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sm)) != cudaSuccess)
         return cudaGetLastError();
-    k_wake_potential<<<grid, block, sm, s>>>(counts, w, ns, A.alpha, A.alpha_sc, V, U, U2, clear);
-    return cudaGetLastError();
+    const unsigned* cc = counts;
+    int nn = ns;
+    double al = A.alpha, as = A.alpha_sc;
+    void* args[] = {&cc, const_cast<double**>(&w), &nn, &al, &as, &V, &U, &U2, &clear};
+    return launch_pdl(reinterpret_cast<const void*>(&k_wake_potential), dim3(grid), dim3(block),
+                      args, sm, s);
 }
 
 }  // namespace phtl

@@ -59,6 +59,7 @@ __global__ void PHTL_F32C_BOUNDS
     if (counts)
         for (int k = threadIdx.x; k < A.nslices; k += blockDim.x) hist[k] = 0u;
     __syncthreads();
+    griddep_wait();  // the previous turn's state, kick and cleared counts
     const int64_t chunk = static_cast<int64_t>(blockDim.x) * P;
     const int64_t nchunks = (L.n + chunk - 1) / chunk;
     int parity = 0;
@@ -124,6 +125,9 @@ __global__ void PHTL_F32C_BOUNDS
             store4(g[5], base, L.n, vec, yp);
         }
     }
+    // the potential kernel may launch now (it waits for this grid's completion); not earlier,
+    // so that its blocks do not sit on SM slots while this grid still works
+    griddep_launch_dependents();
     if (counts) {
         __syncthreads();
         for (int k = threadIdx.x; k < A.nslices; k += blockDim.x) {
@@ -184,7 +188,7 @@ cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const 
     int64_t rr = rec_row;
     int kk = kick ? 1 : 0, mm = map ? 1 : 0;
     void* args[] = {&Lc, &cc, &aa, &uu, &cn, &mr, &rr, &kk, &mm};
-    return cudaLaunchKernel(k, dim3(L.grid), dim3(L.block), args, smem_bytes(L.block, A.nslices), s);
+    return launch_pdl(k, dim3(L.grid), dim3(L.block), args, smem_bytes(L.block, A.nslices), s);
 }
 
 }  // namespace phtl
