@@ -61,6 +61,8 @@ void stop_server(phtl_handle* h);
 int ensure_device(phtl_handle* h);
 int handle_stream(phtl_handle* h, cudaStream_t* out);
 void release_handle_resources(phtl_handle* h);
+void free_programme(phtl_handle* h);  // api_programme.cu
+void free_wake(phtl_handle* h);       // api_collective.cu
 int check_track_args(const phtl_handle* h, void* const* c, int64_t n, int64_t turns,
                      int integrator, int dtype);
 int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int integrator,

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "phtl.h"
@@ -10,6 +11,16 @@
 namespace phtl {
 
 constexpr int kNumDtypes = 4;  // PHTL_F64 .. PHTL_F32CS
+constexpr double kPi = 3.14159265358979323846;
+
+inline bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// v as an unevaluated float pair hi + lo (host): hi rounded, lo the rounded remainder.
+inline void split_df(double v, float& hi, float& lo)
+{
+    hi = static_cast<float>(v);
+    lo = static_cast<float>(v - static_cast<double>(hi));
+}
 
 // Per-stage coefficients of one turn of the longitudinal map (Sec. 1.1.2 schemes),
 // pre-multiplied on the host in FP64:

@@ -152,7 +152,9 @@ def test_f64_perturn_variant_equals_persistent():
         b, mb = run_gpu(inp, scheme, 200, stride=10)
         for u, v in zip(a, b):
             assert np.array_equal(u, v)
-        assert np.allclose(ma, mb, rtol=1e-12, atol=0)
+        # the launches differ in shape, so the monitor sums are added in different orders:
+        # the moments agree to the ordering's rounding (means relative to the rms)
+        assert moment_errors(inp["d"], ma, mb) < 1e-11
 
 
 def test_f64_misaligned_pointers_take_the_scalar_path():

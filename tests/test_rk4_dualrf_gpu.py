@@ -130,7 +130,8 @@ def test_rk4_perturn_equals_persistent(dtype):
     b, mb = run_gpu(inp, "rk4", 150, dtype=dtype, stride=10, perturn=True)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
-    assert np.allclose(ma, mb, rtol=1e-12, atol=1e-300)
+    # monitor sums added in another order: the moments agree to its rounding
+    assert moment_errors(inp["d"], ma, mb) < 1e-11
 
 
 def _bufs(inp, dtype):

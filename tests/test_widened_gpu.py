@@ -115,7 +115,8 @@ def test_widened_perturn_equals_persistent():
     b, mb = run_gpu(inp, "ruth4", 200, stride=10, perturn=True)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
-    assert np.allclose(ma, mb, rtol=1e-12, atol=1e-300)
+    # monitor sums added in another order: the moments agree to its rounding
+    assert moment_errors(inp["d"], ma, mb) < 1e-11
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32cd"])
