@@ -41,7 +41,7 @@ WORKLOADS = {
     "single_bunch_1e6x1e4_ec_lf_ruth4_f64": dict(
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
         voltage=4.5e6, transverse=True, stride=1),
-    # the widened map (SURVEY next row f1): slippage expansion eta(d) = eta0 + 0.05 d + 2 d^2
+    # the widened map: slippage expansion eta(d) = eta0 + 0.05 d + 2 d^2
     # in the drift and chromaticities xi_x = 5, xi_y = -3 (per-particle transverse phase
     # advance), the same bunch size and turns; a bunch inside half the separatrix
     "widened_map_1e6x1e4_f64": dict(

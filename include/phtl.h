@@ -354,7 +354,7 @@ typedef struct phtl_batch_info {
 } phtl_batch_info;
 
 /* Project-written autotuner: times the batched kernel of `dtype`/`integrator` at block
- * sizes 64, 128 and 256 on scratch particles that fill the GPU once (the library
+ * sizes 64, 96, 128, 192 and 256 on scratch particles that fill the GPU once (the library
  * allocates and frees them; the call synchronises), keeps the fastest block, and picks
  * the turns per launch that make a launch over `active_particles` particles last about
  * target_launch_ms.  Errors: PHTL_E_BADHANDLE, PHTL_E_INVALID, PHTL_E_NODEVICE,

@@ -110,7 +110,7 @@ int autotune(phtl_handle* h, int dtype, int scheme, int64_t active, double targe
     rc = handle_stream(h, &s);
     if (rc != PHTL_OK) return rc;
     const int ppt = particles_per_thread(dtype);
-    const int candidates[] = {64, 128, 256};
+    const int candidates[] = {64, 96, 128, 192, 256};
     int best_block = 0;
     double best_rate = 0.0;
     for (int b : candidates) {

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
 seeded inputs.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (from the arithmetic: per-operation rounding differences -- FMA contraction,
+the library's sine within a few ulp -- act like a tune perturbation of ~1e-15):
   FP64 path  : per-particle relative error <= 1e-10 after up to 1e4 turns for particles
                inside 90 % of the separatrix (error relative to the particle's own
                amplitude, see helpers.py); monitor moments <= 1e-9 relative.
