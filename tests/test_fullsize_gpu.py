@@ -57,3 +57,55 @@ def test_bench_workload_sampled_parity():
         assert mon[turns, 0].item() == n
         state = got  # the next scheme continues from here; contours are (nearly) invariant
     R.close()
+
+
+def test_batched_workload_sampled_parity():
+    """The 64-bunch batch of the batched workload (5.5e7 particles, turns 1e3-1e5, V 1-6 MV,
+    leap-frog FP32C, per-bunch stride-1 monitors, one graph-captured autotuned batch) as
+    bench.py builds it, one run: for 8 bunches spread over the table, 24 sampled particles
+    re-tracked alone by the FP64 oracle at the bunch's voltage and turns (FP32C tolerance,
+    grown with the turns: 3e-8 per 1e4 turns inside 90 % of the separatrix), and every
+    bunch's last monitor row against the moments of its final arrays (FP32 partial sums)."""
+    wl = bench.WORKLOADS["batched_64_bunches_f32c_lf"]
+    specs = synth.batched_jobs(seed=3, nbunch=wl["nbunch"], total=wl["total"])
+    ring = synth.ring(2e6)
+    R = phtl.Ring(**ring)
+    dev = torch.device("cuda:0")
+    jobs, host, mons = [], [], []
+    for sp in specs:
+        der = phtl.Ring(**dict(ring, voltage_V=sp["voltage_V"])).derived()
+        b = synth.Bucket(k=der.k, A=der.A, etaC=der.etaC, Qs=der.Qs, betagamma=der.betagamma)
+        z, d, _ = synth.matched_bunch(sp["seed"], sp["n"], b)
+        bz = torch.tensor(phtl.split_f32c(z), dtype=torch.float32, device=dev)
+        bd = torch.tensor(phtl.split_f32c(d), dtype=torch.float32, device=dev)
+        mon = torch.zeros((sp["turns"] + 1, 16), dtype=torch.float64, device=dev)
+        jobs.append(phtl.make_job(bz, bd, turns=sp["turns"], voltage_V=sp["voltage_V"],
+                                  integrator="leapfrog", dtype="f32c", monitor=mon, stride=1))
+        host.append((z, d, bz, bd))
+        mons.append(mon)
+    B = phtl.Batch(R, jobs, use_graph=True)
+    B.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(321)
+    picks = np.linspace(0, len(specs) - 1, 8).astype(int)
+    for j, sp in enumerate(specs):
+        z0, d0, bz, bd = host[j]
+        zf, df = phtl.join_f32c(bz.cpu().numpy()), phtl.join_f32c(bd.cpu().numpy())
+        m_last = phtl.moments_from_sums(mons[j][sp["turns"]].cpu().numpy())
+        m_arr = oracle.moments(zf, df)
+        assert mons[j][sp["turns"], 0].item() == sp["n"]
+        for k in (2, 3):
+            assert abs(m_last[k] / m_arr[k] - 1) < 1e-6, (j, k)
+        if j not in picks:
+            continue
+        od = oracle.derive(dict(ring, voltage_V=sp["voltage_V"]))
+        idx = np.sort(rng.choice(sp["n"], min(24, sp["n"]), replace=False))
+        ref = oracle.track(od, "leapfrog", z0[idx], d0[idx], turns=sp["turns"])
+        err = helpers.rel_errors(od, list(ref[:6]), [zf[idx], df[idx], None, None, None, None],
+                                 z0[idx], d0[idx])
+        H = 0.5 * od.etaC * d0[idx] ** 2 + (od.A / od.k) * (1 - np.cos(od.k * z0[idx]))
+        ins = H <= (od.A / od.k) * (1 - np.cos(0.9 * np.pi))
+        tol = 3e-8 * max(1.0, sp["turns"] / 1e4)
+        assert np.max(err[ins]) < tol, (j, sp["turns"], np.max(err[ins]), tol)
+    B.close()
+    R.close()
