@@ -19,6 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphtl.so")
 SOURCES = ["api.cu", "api_programme.cu", "api_collective.cu", "track_f64.cu", "track_f32c.cu", "track_batched.cu", "track_general.cu",
            "track_general_batched.cu", "track_general_rk4.cu", "track_general_batched_f32.cu",
+           "track_general_dual.cu", "track_general_dual_f32.cu",
            "track_ramp.cu", "track_collective.cu",
            "track_collective_f32.cu", "batch.cu", "server.cu", "batch_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

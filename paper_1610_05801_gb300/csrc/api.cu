@@ -288,17 +288,17 @@ cudaError_t launch_perturn(const LaunchDesc& L, const MapConsts& c, const Monito
     return dtype == PHTL_F64 ? launch_track_f64(L, c, m, s) : launch_track_f32c(L, c, m, dtype, s);
 }
 
-int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, bool general)
+int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, int gen)
 {
-    return dtype == PHTL_F64 ? occupancy_f64(scheme, trans, mon, block, general)
-                             : occupancy_f32c(scheme, trans, mon, dtype, block, general);
+    return dtype == PHTL_F64 ? occupancy_f64(scheme, trans, mon, block, gen)
+                             : occupancy_f32c(scheme, trans, mon, dtype, block, gen);
 }
 
-int occupancy(int dtype, int scheme, bool trans, bool mon, int block, bool perturn, bool general)
+int occupancy(int dtype, int scheme, bool trans, bool mon, int block, bool perturn, int gen)
 {
-    if (perturn) return occupancy_perturn(scheme, trans, mon, dtype, block, general);
-    if (dtype == PHTL_F64) return occupancy_f64(scheme, trans, mon, block, general);
-    return occupancy_f32c(scheme, trans, mon, dtype, block, general);
+    if (perturn) return occupancy_perturn(scheme, trans, mon, dtype, block, gen);
+    if (dtype == PHTL_F64) return occupancy_f64(scheme, trans, mon, block, gen);
+    return occupancy_f32c(scheme, trans, mon, dtype, block, gen);
 }
 
 int check_track_args(const phtl_handle* h, void* const* c, int64_t n, int64_t turns,
@@ -354,7 +354,7 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     if (dtype != PHTL_F64 && (n * es) % 16 != 0) vec = false;
 
     const int occ = occupancy(dtype, integrator, trans, mon, block, perturn,
-                              h->mc[integrator].general != 0);
+                              gen_level(h->mc[integrator]));
     if (occ <= 0) return PHTL_E_INVALID;
     const int64_t chunk = static_cast<int64_t>(block) * ppt;
     const int64_t nchunks = (n + chunk - 1) / chunk;

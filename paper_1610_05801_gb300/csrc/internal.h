@@ -227,11 +227,15 @@ cudaError_t launch_batched(const JobDesc* jobs, int32_t njobs, const MapConsts& 
 int occupancy_batched(int dtype, bool mon, int block, bool general);
 int particles_per_thread(int dtype);
 
+// Which single-bunch kernel family a map needs: 0 the linear map's, 1 the widened map's,
+// 2 the widened map's with the second RF system.
+inline int gen_level(const MapConsts& c) { return c.general ? (c.dual_rf ? 2 : 1) : 0; }
+
 // Resident blocks per SM of a kernel variant at a block size (0 = cannot launch);
-// general: the widened map's kernels (MapConsts::general).
-int occupancy_f64(int scheme, bool trans, bool mon, int block, bool general);
-int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, bool general);
-int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, bool general);
+// gen: the kernel family (gen_level).
+int occupancy_f64(int scheme, bool trans, bool mon, int block, int gen);
+int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, int gen);
+int occupancy_perturn(int scheme, bool trans, bool mon, int dtype, int block, int gen);
 
 // Ramp programme kernels (track_ramp.cu): turns [turn0, turn0 + L.nturns) of the
 // programme table prog (device memory), linear map only.
@@ -256,8 +260,10 @@ cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const 
 int occupancy_coll_f32(int scheme, int dtype, int block, int nslices);
 
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).
-const void* general_kernel_single(int scheme, int dtype);
-const void* general_kernel_single_rk4(int dtype);  // track_general_rk4.cu
+const void* general_kernel_single(int scheme, int dtype, bool dual);
+const void* general_kernel_single_rk4(int dtype);                   // track_general_rk4.cu
+const void* general_kernel_single_dual(int scheme, int dtype);      // track_general_dual.cu
+const void* general_kernel_single_dual_f32(int scheme, int dtype);  // track_general_dual_f32.cu
 const void* general_kernel_batched(int dtype);
 const void* general_kernel_batched_f32(int dtype);  // PHTL_F32CD, PHTL_F32CS
 

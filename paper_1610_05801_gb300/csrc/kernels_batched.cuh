@@ -52,7 +52,7 @@ __device__ __forceinline__ void run_f64_zs(double (&z)[f64::P], double (&d)[f64:
     if (GEN) f64::slip_stages<SCHEME>(c, g1, g2);
     for (int t = 0; t < nt; ++t) {
         if (GEN) {
-            f64::long_turn_nl<SCHEME, ZS>(z, d, c, J.dc, J.kw, J.kw2, g1, g2);
+            f64::long_turn_nl<SCHEME, ZS>(z, d, c, J.dc, J.kw, J.kw2, g1, g2, c.dual_rf != 0);
             f64::transverse_gen(x, xp, y, yp, d, hx, hy, c);
         } else {
             f64::long_turn<SCHEME, ZS>(z, d, c, J.dc, J.kw);
@@ -176,7 +176,7 @@ __device__ __forceinline__ void run_f32c_zs(f32c::DF (&z)[f32c::P], f32c::DF (&d
     for (int t = 0; t < nt; ++t) {
         if (GEN) {
             long_turn_nl<SCHEME, DT, ZS>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo, J.kw2_hi,
-                                         J.kw2_lo, g1h, g1l, g2h, g2l);
+                                         J.kw2_lo, g1h, g1l, g2h, g2l, c.dual_rf != 0);
             transverse_gen<DT>(x, xp, y, yp, d, hx, hy, c);
         } else {
             long_turn<SCHEME, DT, ZS>(z, d, c, J.dc_hi, J.dc_lo, J.kw_hi, J.kw_lo);

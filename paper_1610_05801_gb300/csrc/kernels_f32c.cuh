@@ -33,7 +33,7 @@ using namespace f32c;
 
 // The turn loop of one particle chunk (state in registers throughout); ZS: phi_s == 0;
 // GEN: the widened map (slippage expansion, chromaticity), chosen once per launch.
-template <int SCHEME, int DT, bool TRANS, bool MON, bool ZS, bool GEN>
+template <int SCHEME, int DT, bool TRANS, bool MON, bool ZS, bool GEN, bool DUAL>
 __device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&xp)[P],
                                       DF (&y)[P], DF (&yp)[P], bool hx, bool hy, float cnt,
                                       const MapConsts& c, const MonitorArgs& m, int nturns,
@@ -45,7 +45,7 @@ __device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&x
     for (int t = 0; t < nturns; ++t) {
         if (GEN) {
             long_turn_nl<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo, c.kw2_hi,
-                                         c.kw2_lo, g1h, g1l, g2h, g2l);
+                                         c.kw2_lo, g1h, g1l, g2h, g2l, DUAL);
             if (TRANS) transverse_gen<DT>(x, xp, y, yp, d, hx, hy, c);
         } else {
             long_turn<SCHEME, DT, ZS>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo);
@@ -72,8 +72,9 @@ __device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&x
 }
 
 // GEN: the widened map, chosen on the host (separate kernels, built with TRANS = MON =
-// true; planes and monitor are checked at run time).
-template <int SCHEME, int DT, bool TRANS, bool MON, bool GEN>
+// true; planes and monitor are checked at run time); DUAL (GEN only): with the second RF
+// system.
+template <int SCHEME, int DT, bool TRANS, bool MON, bool GEN, bool DUAL = false>
 __global__ void PHTL_F32C_BOUNDS k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
     extern __shared__ double smem[];
@@ -110,11 +111,11 @@ __global__ void PHTL_F32C_BOUNDS k_track_f32c(LaunchDesc L, MapConsts c, Monitor
             parity ^= 1;
         }
         if (c.phis_zero)
-            turns<SCHEME, DT, TRANS, MON, true, GEN>(z, d, x, xp, y, yp, hx, hy, cnt, c, m,
-                                                     L.nturns, smem, parity);
+            turns<SCHEME, DT, TRANS, MON, true, GEN, DUAL>(z, d, x, xp, y, yp, hx, hy, cnt, c, m,
+                                                           L.nturns, smem, parity);
         else
-            turns<SCHEME, DT, TRANS, MON, false, GEN>(z, d, x, xp, y, yp, hx, hy, cnt, c, m,
-                                                      L.nturns, smem, parity);
+            turns<SCHEME, DT, TRANS, MON, false, GEN, DUAL>(z, d, x, xp, y, yp, hx, hy, cnt, c, m,
+                                                            L.nturns, smem, parity);
         store4(g[0], base, L.n, vec, z);
         store4(g[1], base, L.n, vec, d);
         if (hx) {

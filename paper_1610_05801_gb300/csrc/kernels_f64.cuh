@@ -27,8 +27,9 @@ namespace kf64 {
 using namespace f64;
 
 // The turn loop of one particle chunk (state in registers throughout).  GEN: the widened
-// map (slippage expansion, chromaticity), chosen once per launch.
-template <int SCHEME, bool TRANS, bool MON, bool ZS, bool GEN>
+// map (slippage expansion, chromaticity, RK4), DUAL: with the second RF system; both
+// chosen once per launch.
+template <int SCHEME, bool TRANS, bool MON, bool ZS, bool GEN, bool DUAL>
 __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x)[P],
                                       double (&xp)[P], double (&y)[P], double (&yp)[P], bool hx,
                                       bool hy, float cnt, const MapConsts& c,
@@ -39,7 +40,7 @@ __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x
     if (GEN) slip_stages<SCHEME>(c, g1, g2);
     for (int t = 0; t < nturns; ++t) {
         if (GEN) {
-            long_turn_nl<SCHEME, ZS>(z, d, c, c.dc, c.kw, c.kw2, g1, g2);
+            long_turn_nl<SCHEME, ZS>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, DUAL);
             if (TRANS) transverse_gen(x, xp, y, yp, d, hx, hy, c);
         } else {
             long_turn<SCHEME, ZS>(z, d, c, c.dc, c.kw);
@@ -60,10 +61,19 @@ __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x
 }
 
 // GEN: the widened map, chosen on the host (separate kernels, so the linear map's
-// kernels keep their registers).  The GEN kernels are built with TRANS = MON = true
-// and check the planes and the monitor at run time.
-template <int SCHEME, bool TRANS, bool MON, bool GEN>
-__global__ void __launch_bounds__(256, GEN ? 2 : min_blocks_256<SCHEME>())
+// kernels keep their registers); DUAL (GEN only): with the second RF system, again a kernel
+// of its own so that the rings without one keep theirs.  The GEN kernels are built with
+// TRANS = MON = true and check the planes and the monitor at run time.
+#ifdef PHTL_F64_RUTH4_MAXNREG
+// build option: a register cap for the linear map's Ruth4 kernel instead of the blocks-per-SM
+// bound (the other kernels keep the caps their bounds give: 80 for EC/LF, 128 for GEN)
+#define PHTL_F64_BOUNDS(S, G) \
+    __launch_bounds__(256) __maxnreg__((S) == PHTL_RUTH4 && !(G) ? PHTL_F64_RUTH4_MAXNREG : ((G) ? 128 : 80))
+#else
+#define PHTL_F64_BOUNDS(S, G) __launch_bounds__(256, (G) ? 2 : min_blocks_256<S>())
+#endif
+template <int SCHEME, bool TRANS, bool MON, bool GEN, bool DUAL = false>
+__global__ void PHTL_F64_BOUNDS(SCHEME, GEN)
     k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
     extern __shared__ double smem[];
@@ -103,11 +113,11 @@ __global__ void __launch_bounds__(256, GEN ? 2 : min_blocks_256<SCHEME>())
             parity ^= 1;
         }
         if (c.phis_zero)
-            turns<SCHEME, TRANS, MON, true, GEN>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
-                                                 smem, parity);
+            turns<SCHEME, TRANS, MON, true, GEN, DUAL>(z, d, x, xp, y, yp, hx, hy, cnt, c, m,
+                                                       L.nturns, smem, parity);
         else
-            turns<SCHEME, TRANS, MON, false, GEN>(z, d, x, xp, y, yp, hx, hy, cnt, c, m, L.nturns,
-                                                  smem, parity);
+            turns<SCHEME, TRANS, MON, false, GEN, DUAL>(z, d, x, xp, y, yp, hx, hy, cnt, c, m,
+                                                        L.nturns, smem, parity);
         store2(gz, base, L.n, vec, z);
         store2(gd, base, L.n, vec, d);
         if (hx) {

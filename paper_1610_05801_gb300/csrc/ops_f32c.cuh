@@ -324,10 +324,10 @@ __device__ __forceinline__ float force1_f(const MapConsts& c, DF2 z)
 // (k2h + k2l: this stage's w_j A2), each increment added on its own.
 template <int DT, bool ZS>
 __device__ __forceinline__ void kick_gen(const DF (&z)[P], DF (&d)[P], float kh, float kl, float k2h,
-                                         float k2l, const MapConsts& c)
+                                         float k2l, const MapConsts& c, bool dual)
 {
     kick<DT, ZS>(z, d, kh, kl, c);
-    if (!c.dual_rf) return;
+    if (!dual) return;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         if (DT == PHTL_F32CS) {
@@ -343,13 +343,13 @@ __device__ __forceinline__ void kick_gen(const DF (&z)[P], DF (&d)[P], float kh,
 // dd/dn = kw F1(z) + kw2 F2(z) (dc = eta0 C, g1 = eta1 C, g2 = eta2 C, kw = A, kw2 = A2).
 template <int DT, bool ZS>
 __device__ __forceinline__ void rk4_rhs_df(DF2 z, DF2 d, const MapConsts& c, DF2 dc, DF2 g1, DF2 g2,
-                                           DF2 kw, DF2 kw2, DF2& fz, DF2& fd)
+                                           DF2 kw, DF2 kw2, bool dual, DF2& fz, DF2& fd)
 {
     DF2 e = df_add(df_mul(g2, d), g1);
     e = df_add(df_mul(e, d), dc);
     fz = neg2(df_mul(e, d));
     fd = df_mul(kw, force1_df<DT, ZS>(c, z));
-    if (c.dual_rf) fd = df_add(fd, df_mul(kw2, force2_df<DT>(c, z)));
+    if (dual) fd = df_add(fd, df_mul(kw2, force2_df<DT>(c, z)));
 }
 
 __device__ __forceinline__ DF2 df_scale2(DF2 a, float s) { return DF2{s * a.h, s * a.l}; }  // s = 2^k: exact
@@ -361,7 +361,7 @@ __device__ __forceinline__ DF2 df_scale2(DF2 a, float s) { return DF2{s * a.h, s
 template <int DT, bool ZS>
 __device__ __forceinline__ void rk4_turn(DF (&z)[P], DF (&d)[P], const MapConsts& c, float dh,
                                          float dl, float kh, float kl, float k2h, float k2l,
-                                         float g1h, float g1l, float g2h, float g2l)
+                                         float g1h, float g1l, float g2h, float g2l, bool dual)
 {
     constexpr DFC sixth(1.0 / 6.0);
 #pragma unroll
@@ -379,7 +379,7 @@ __device__ __forceinline__ void rk4_turn(DF (&z)[P], DF (&d)[P], const MapConsts
                 const DF2 zz{zs, 0.0f};
                 const float f1 = force1_f<ZS>(c, zz);
                 float fd = __fmaf_rn(kh, f1, __fmul_rn(kl, f1));
-                if (c.dual_rf) fd = __fmaf_rn(k2h, force2_f(c, zz), fd);
+                if (dual) fd = __fmaf_rn(k2h, force2_f(c, zz), fd);
                 kd[st] = fd;
             }
             const float sz = __fmaf_rn(2.0f, __fadd_rn(kz[1], kz[2]), __fadd_rn(kz[0], kz[3]));
@@ -390,12 +390,12 @@ __device__ __forceinline__ void rk4_turn(DF (&z)[P], DF (&d)[P], const MapConsts
             const DF2 dc{dh, dl}, g1{g1h, g1l}, g2{g2h, g2l}, kw{kh, kl}, kw2{k2h, k2l};
             const DF2 z0 = as2(z[p]), d0 = as2(d[p]);
             DF2 k1z, k1d, k2z, k2d, k3z, k3d, k4z, k4d;
-            rk4_rhs_df<DT, ZS>(z0, d0, c, dc, g1, g2, kw, kw2, k1z, k1d);
+            rk4_rhs_df<DT, ZS>(z0, d0, c, dc, g1, g2, kw, kw2, dual, k1z, k1d);
             rk4_rhs_df<DT, ZS>(df_add(z0, df_scale2(k1z, 0.5f)), df_add(d0, df_scale2(k1d, 0.5f)), c,
-                               dc, g1, g2, kw, kw2, k2z, k2d);
+                               dc, g1, g2, kw, kw2, dual, k2z, k2d);
             rk4_rhs_df<DT, ZS>(df_add(z0, df_scale2(k2z, 0.5f)), df_add(d0, df_scale2(k2d, 0.5f)), c,
-                               dc, g1, g2, kw, kw2, k3z, k3d);
-            rk4_rhs_df<DT, ZS>(df_add(z0, k3z), df_add(d0, k3d), c, dc, g1, g2, kw, kw2, k4z, k4d);
+                               dc, g1, g2, kw, kw2, dual, k3z, k3d);
+            rk4_rhs_df<DT, ZS>(df_add(z0, k3z), df_add(d0, k3d), c, dc, g1, g2, kw, kw2, dual, k4z, k4d);
             const DF2 sz = df_add(df_add(k1z, k4z), df_scale2(df_add(k2z, k3z), 2.0f));
             const DF2 sd = df_add(df_add(k1d, k4d), df_scale2(df_add(k2d, k3d), 2.0f));
             acc2(z[p], df_mul(sz, DF2{sixth.h, sixth.l}));
@@ -412,25 +412,25 @@ __device__ __forceinline__ void long_turn_nl(DF (&z)[P], DF (&d)[P], const MapCo
                                              const float* dh, const float* dl, const float* kh,
                                              const float* kl, const float* k2h, const float* k2l,
                                              const float (&g1h)[4], const float (&g1l)[4],
-                                             const float (&g2h)[4], const float (&g2l)[4])
+                                             const float (&g2h)[4], const float (&g2l)[4], bool dual)
 {
     if (SCHEME == PHTL_RK4) {
         rk4_turn<DT, ZS>(z, d, c, dh[0], dl[0], kh[0], kl[0], k2h[0], k2l[0], g1h[0], g1l[0],
-                         g2h[0], g2l[0]);
+                         g2h[0], g2l[0], dual);
     } else if (SCHEME == PHTL_EULER_CROMER) {
-        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c);
+        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c, dual);
         drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
     } else if (SCHEME == PHTL_LEAPFROG) {
         drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
-        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c);
+        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c, dual);
         drift_nl<DT>(z, d, dh[1], dl[1], g1h[1], g1l[1], g2h[1], g2l[1]);
     } else {
         drift_nl<DT>(z, d, dh[0], dl[0], g1h[0], g1l[0], g2h[0], g2l[0]);
-        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c);
+        kick_gen<DT, ZS>(z, d, kh[0], kl[0], k2h[0], k2l[0], c, dual);
         drift_nl<DT>(z, d, dh[1], dl[1], g1h[1], g1l[1], g2h[1], g2l[1]);
-        kick_gen<DT, ZS>(z, d, kh[1], kl[1], k2h[1], k2l[1], c);
+        kick_gen<DT, ZS>(z, d, kh[1], kl[1], k2h[1], k2l[1], c, dual);
         drift_nl<DT>(z, d, dh[2], dl[2], g1h[2], g1l[2], g2h[2], g2l[2]);
-        kick_gen<DT, ZS>(z, d, kh[2], kl[2], k2h[2], k2l[2], c);
+        kick_gen<DT, ZS>(z, d, kh[2], kl[2], k2h[2], k2l[2], c, dual);
         drift_nl<DT>(z, d, dh[3], dl[3], g1h[3], g1l[3], g2h[3], g2l[3]);
     }
 }

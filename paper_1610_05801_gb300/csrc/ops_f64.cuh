@@ -135,16 +135,17 @@ __device__ __forceinline__ double rf_force2(const MapConsts& c, double z)
     return sin_f64(fma(c.k2, z, c.phi2)) - c.sinphi2;
 }
 
-// Kick of the widened map: the main RF system, then the second one when it is on
-// (kw2: this stage's w_j A2).
+// Kick of the widened map: the main RF system, then the second one when `dual` (a
+// compile-time constant in the single-bunch kernels, which have a variant without the
+// second system; the batched kernels pass the ring's flag) -- kw2: this stage's w_j A2.
 template <bool ZS>
 __device__ __forceinline__ void kick_gen(const double (&z)[P], double (&d)[P], double kw, double kw2,
-                                         const MapConsts& c)
+                                         const MapConsts& c, bool dual)
 {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         d[p] = fma(kw, rf_force<ZS>(c, z[p]), d[p]);
-        if (c.dual_rf) d[p] = fma(kw2, rf_force2(c, z[p]), d[p]);
+        if (dual) d[p] = fma(kw2, rf_force2(c, z[p]), d[p]);
     }
 }
 
@@ -153,30 +154,36 @@ __device__ __forceinline__ void kick_gen(const double (&z)[P], double (&d)[P], d
 // dc = eta0 C, g1 = eta1 C, g2 = eta2 C, kw = A, kw2 = A2.
 template <bool ZS>
 __device__ __forceinline__ void rk4_rhs(double z, double d, const MapConsts& c, double dc, double g1,
-                                        double g2, double kw, double kw2, double& fz, double& fd)
+                                        double g2, double kw, double kw2, bool dual, double& fz,
+                                        double& fd)
 {
+    // the products are rounded on their own (__dmul_rn): the stage arguments and the
+    // weighted sum reuse them, and an FMA contraction chosen differently where `dual` is a
+    // compile-time constant than where it is not would break the bitwise agreement of the
+    // single-bunch and batched kernels
     const double e = fma(fma(g2, d, g1), d, dc);
-    fz = -e * d;
-    fd = kw * rf_force<ZS>(c, z);
-    if (c.dual_rf) fd = fma(kw2, rf_force2(c, z), fd);
+    fz = -__dmul_rn(e, d);
+    fd = __dmul_rn(kw, rf_force<ZS>(c, z));
+    if (dual) fd = fma(kw2, rf_force2(c, z), fd);
 }
 
 // One classic RK4 step of one turn: k1 at the start, k2 and k3 at the half step from k1
 // and k2, k4 at the full step from k3, and the weighted sum (k1 + 2 k2 + 2 k3 + k4) / 6.
 template <bool ZS>
 __device__ __forceinline__ void rk4_turn(double (&z)[P], double (&d)[P], const MapConsts& c,
-                                         double dc, double kw, double kw2, double g1, double g2)
+                                         double dc, double kw, double kw2, double g1, double g2,
+                                         bool dual)
 {
     constexpr double kSixth = 1.0 / 6.0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         double k1z, k1d, k2z, k2d, k3z, k3d, k4z, k4d;
-        rk4_rhs<ZS>(z[p], d[p], c, dc, g1, g2, kw, kw2, k1z, k1d);
-        rk4_rhs<ZS>(fma(0.5, k1z, z[p]), fma(0.5, k1d, d[p]), c, dc, g1, g2, kw, kw2, k2z, k2d);
-        rk4_rhs<ZS>(fma(0.5, k2z, z[p]), fma(0.5, k2d, d[p]), c, dc, g1, g2, kw, kw2, k3z, k3d);
-        rk4_rhs<ZS>(z[p] + k3z, d[p] + k3d, c, dc, g1, g2, kw, kw2, k4z, k4d);
-        z[p] = fma(fma(2.0, k2z + k3z, k1z + k4z), kSixth, z[p]);
-        d[p] = fma(fma(2.0, k2d + k3d, k1d + k4d), kSixth, d[p]);
+        rk4_rhs<ZS>(z[p], d[p], c, dc, g1, g2, kw, kw2, dual, k1z, k1d);
+        rk4_rhs<ZS>(fma(0.5, k1z, z[p]), fma(0.5, k1d, d[p]), c, dc, g1, g2, kw, kw2, dual, k2z, k2d);
+        rk4_rhs<ZS>(fma(0.5, k2z, z[p]), fma(0.5, k2d, d[p]), c, dc, g1, g2, kw, kw2, dual, k3z, k3d);
+        rk4_rhs<ZS>(__dadd_rn(z[p], k3z), __dadd_rn(d[p], k3d), c, dc, g1, g2, kw, kw2, dual, k4z, k4d);
+        z[p] = fma(fma(2.0, __dadd_rn(k2z, k3z), __dadd_rn(k1z, k4z)), kSixth, z[p]);
+        d[p] = fma(fma(2.0, __dadd_rn(k2d, k3d), __dadd_rn(k1d, k4d)), kSixth, d[p]);
     }
 }
 
@@ -185,24 +192,24 @@ __device__ __forceinline__ void rk4_turn(double (&z)[P], double (&d)[P], const M
 template <int SCHEME, bool ZS>
 __device__ __forceinline__ void long_turn_nl(double (&z)[P], double (&d)[P], const MapConsts& c,
                                              const double* dc, const double* kw, const double* kw2,
-                                             const double (&g1)[4], const double (&g2)[4])
+                                             const double (&g1)[4], const double (&g2)[4], bool dual)
 {
     if (SCHEME == PHTL_RK4) {
-        rk4_turn<ZS>(z, d, c, dc[0], kw[0], kw2[0], g1[0], g2[0]);
+        rk4_turn<ZS>(z, d, c, dc[0], kw[0], kw2[0], g1[0], g2[0], dual);
     } else if (SCHEME == PHTL_EULER_CROMER) {
-        kick_gen<ZS>(z, d, kw[0], kw2[0], c);
+        kick_gen<ZS>(z, d, kw[0], kw2[0], c, dual);
         drift_nl(z, d, dc[0], g1[0], g2[0]);
     } else if (SCHEME == PHTL_LEAPFROG) {
         drift_nl(z, d, dc[0], g1[0], g2[0]);
-        kick_gen<ZS>(z, d, kw[0], kw2[0], c);
+        kick_gen<ZS>(z, d, kw[0], kw2[0], c, dual);
         drift_nl(z, d, dc[1], g1[1], g2[1]);
     } else {
         drift_nl(z, d, dc[0], g1[0], g2[0]);
-        kick_gen<ZS>(z, d, kw[0], kw2[0], c);
+        kick_gen<ZS>(z, d, kw[0], kw2[0], c, dual);
         drift_nl(z, d, dc[1], g1[1], g2[1]);
-        kick_gen<ZS>(z, d, kw[1], kw2[1], c);
+        kick_gen<ZS>(z, d, kw[1], kw2[1], c, dual);
         drift_nl(z, d, dc[2], g1[2], g2[2]);
-        kick_gen<ZS>(z, d, kw[2], kw2[2], c);
+        kick_gen<ZS>(z, d, kw[2], kw2[2], c, dual);
         drift_nl(z, d, dc[3], g1[3], g2[3]);
     }
 }

@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(256, 3)
             parity ^= 1;
         }
         if (map) {
-            if (c.phis_zero) long_turn_nl<S, true>(z, d, c, c.dc, c.kw, c.kw2, g1, g2);
-            else long_turn_nl<S, false>(z, d, c, c.dc, c.kw, c.kw2, g1, g2);
+            if (c.phis_zero) long_turn_nl<S, true>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, c.dual_rf != 0);
+            else long_turn_nl<S, false>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, c.dual_rf != 0);
             transverse_gen(x, xp, y, yp, d, hx, hy, c);
         }
         if (counts) {

@@ -101,10 +101,10 @@ __global__ void PHTL_F32C_BOUNDS
         if (map) {
             if (c.phis_zero)
                 long_turn_nl<S, DT, true>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo, c.kw2_hi,
-                                          c.kw2_lo, g1h, g1l, g2h, g2l);
+                                          c.kw2_lo, g1h, g1l, g2h, g2l, c.dual_rf != 0);
             else
                 long_turn_nl<S, DT, false>(z, d, c, c.dc_hi, c.dc_lo, c.kw_hi, c.kw_lo, c.kw2_hi,
-                                           c.kw2_lo, g1h, g1l, g2h, g2l);
+                                           c.kw2_lo, g1h, g1l, g2h, g2l, c.dual_rf != 0);
             transverse_gen<DT>(x, xp, y, yp, d, hx, hy, c);
         }
         if (counts) {

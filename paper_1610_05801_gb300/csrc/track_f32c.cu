@@ -43,10 +43,10 @@ const void* select_kernel(int scheme, int dtype, bool trans, bool mon)
 
 }  // namespace
 
-int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, bool general)
+int occupancy_f32c(int scheme, bool trans, bool mon, int dtype, int block, int gen)
 {
-    const void* k = general ? general_kernel_single(scheme, dtype)
-                            : select_kernel(scheme, dtype, trans, mon);
+    const void* k = gen ? general_kernel_single(scheme, dtype, gen == 2)
+                        : select_kernel(scheme, dtype, trans, mon);
     if (!k) return 0;
     int nb = 0;
     const size_t smem = mon ? 2u * (block / 32) * 16 * sizeof(double) : 0;
@@ -59,7 +59,7 @@ cudaError_t launch_track_f32c(const LaunchDesc& L, const MapConsts& c, const Mon
 {
     const bool trans = L.c[2] != nullptr || L.c[4] != nullptr;
     const bool mon = m.rows != nullptr;
-    const void* k = c.general ? general_kernel_single(L.scheme, dtype)
+    const void* k = c.general ? general_kernel_single(L.scheme, dtype, c.dual_rf != 0)
                               : select_kernel(L.scheme, dtype, trans, mon);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = mon ? 2u * (L.block / 32) * 16 * sizeof(double) : 0;

@@ -36,10 +36,10 @@ const void* select_kernel(int scheme, bool trans, bool mon)
 
 }  // namespace
 
-int occupancy_f64(int scheme, bool trans, bool mon, int block, bool general)
+int occupancy_f64(int scheme, bool trans, bool mon, int block, int gen)
 {
-    const void* k = general ? general_kernel_single(scheme, PHTL_F64)
-                            : select_kernel(scheme, trans, mon);
+    const void* k = gen ? general_kernel_single(scheme, PHTL_F64, gen == 2)
+                        : select_kernel(scheme, trans, mon);
     if (!k) return 0;
     int nb = 0;
     const size_t smem = mon ? 2u * (block / 32) * 16 * sizeof(double) : 0;
@@ -52,7 +52,7 @@ cudaError_t launch_track_f64(const LaunchDesc& L, const MapConsts& c, const Moni
 {
     const bool trans = L.c[2] != nullptr || L.c[4] != nullptr;
     const bool mon = m.rows != nullptr;
-    const void* k = c.general ? general_kernel_single(L.scheme, PHTL_F64)
+    const void* k = c.general ? general_kernel_single(L.scheme, PHTL_F64, c.dual_rf != 0)
                               : select_kernel(L.scheme, trans, mon);
     if (!k) return cudaErrorInvalidValue;
     const size_t smem = mon ? 2u * (L.block / 32) * 16 * sizeof(double) : 0;

@@ -12,8 +12,9 @@
 
 namespace phtl {
 
-const void* general_kernel_single(int scheme, int dtype)
+const void* general_kernel_single(int scheme, int dtype, bool dual)
 {
+    if (dual) return general_kernel_single_dual(scheme, dtype);
 #define PHTL_GEN(S)                                                                          \
     if (scheme == S) {                                                                       \
         if (dtype == PHTL_F64) return reinterpret_cast<const void*>(&kf64::k_track_f64<S, true, true, true>); \
