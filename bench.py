@@ -119,8 +119,8 @@ RF2_FLOPS = 2 + SINE_FLOPS + 1 + 2
 KICKS = {"euler_cromer": 1, "leapfrog": 1, "ruth4": 3, "rk4": 4}
 # ramp programme: per particle-turn delta, x' and y' are multiplied by r_n
 RAMP_FLOPS = 3
-# collective step per particle-turn: the slice index twice (2 flops each) and the kick FMA
-COLLECTIVE_FLOPS = 6
+# collective step per particle-turn: the slice index (subtract, multiply) and the kick's add
+COLLECTIVE_FLOPS = 3
 TRANSVERSE_FLOPS = 12
 MONITOR_FLOPS = 24
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flops x max clock
@@ -449,8 +449,8 @@ def run_ours(args, wl_name, wl):
     if wl.get("ramp"):
         flops_pt += RAMP_FLOPS
     if wl.get("wake"):
-        # the general kernel's drifts, and per particle the slice index twice (subtract,
-        # multiply) and the kick FMA
+        # the general kernel's drifts, and per particle the slice index (subtract, multiply)
+        # and the kick's add
         flops_pt += {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4, "rk4": 0}[dom] * (
             DRIFT_FLOPS_NL - DRIFT_FLOPS) + COLLECTIVE_FLOPS
     flops = flops_pt * n * tpl

@@ -22,8 +22,11 @@ void free_wake(phtl_handle* h)
         if (h->wake_device >= 0 && cur != h->wake_device) cudaSetDevice(h->wake_device);
         cudaDeviceSynchronize();
         cudaFree(h->wake_mem);
+        if (h->coll_slot) cudaFree(h->coll_slot);
         if (cur >= 0 && cur != h->wake_device) cudaSetDevice(cur);
     }
+    h->coll_slot = nullptr;
+    h->coll_slot_cap = 0;
     h->wake_mem = nullptr;
     h->wake_w = h->wake_V = h->wake_U = nullptr;
     h->wake_U2 = nullptr;
@@ -132,14 +135,36 @@ int cuda_ok(cudaError_t e)
     return PHTL_E_CUDA;
 }
 
+// The per-particle slice buffer for n particles on the wake's device (grown, never shrunk;
+// the old one is freed after the work that may still use it).
+int ensure_slots(phtl_handle* h, int64_t n)
+{
+    if (n <= h->coll_slot_cap) return PHTL_OK;
+    if (h->coll_slot) {
+        cudaDeviceSynchronize();
+        cudaFree(h->coll_slot);
+        h->coll_slot = nullptr;
+        h->coll_slot_cap = 0;
+    }
+    const int64_t cap = (n + 4095) / 4096 * 4096;
+    if (cudaMalloc(&h->coll_slot, static_cast<size_t>(cap) * sizeof(uint16_t)) != cudaSuccess) {
+        cudaGetLastError();
+        h->coll_slot = nullptr;
+        return PHTL_E_NOMEM;
+    }
+    h->coll_slot_cap = cap;
+    return PHTL_OK;
+}
+
 // One launch of the collective turn kernel of the arithmetic type.
 int coll_turn(phtl_handle* h, const LaunchDesc& L, const MapConsts& mc, unsigned* counts,
               double* mon, int64_t rec, bool kick, bool map, int dtype, cudaStream_t s)
 {
     if (dtype == PHTL_F64)
-        return cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_U, counts, mon, rec, kick, map, s));
-    return cuda_ok(launch_coll_turn_f32(L, mc, h->coll, h->wake_U2, counts, mon, rec, kick, map,
-                                        dtype, s));
+        return cuda_ok(launch_coll_turn(L, mc, h->coll, h->wake_U, counts, h->coll_slot, mon, rec,
+                                        kick, map, s));
+    return cuda_ok(launch_coll_turn_f32(L, mc, h->coll, h->wake_U2, counts, h->coll_slot, mon, rec,
+                                        kick, map, dtype, s));
 }
 
 int coll_potential(phtl_handle* h, unsigned* counts, unsigned* clear, cudaStream_t s)
@@ -165,7 +190,8 @@ int phtl_collective_kick(phtl_handle* h, void* z, void* dp, int64_t n, int dtype
     if (rc == PHTL_OK && n > 0) {
         LaunchDesc L;
         const MapConsts& mc = h->mc[PHTL_LEAPFROG];
-        rc = coll_launch(h, c, n, PHTL_LEAPFROG, dtype, L);
+        rc = ensure_slots(h, n);
+        if (rc == PHTL_OK) rc = coll_launch(h, c, n, PHTL_LEAPFROG, dtype, L);
         if (rc == PHTL_OK) rc = coll_turn(h, L, mc, cnt, nullptr, -1, false, false, dtype, s);
         if (rc == PHTL_OK) rc = coll_potential(h, cnt, nullptr, s);
         if (rc == PHTL_OK) rc = coll_turn(h, L, mc, nullptr, nullptr, -1, true, false, dtype, s);
@@ -198,6 +224,8 @@ int phtl_track_collective(phtl_handle* h, void* z, void* dp, void* x, void* xp, 
         if (rc != PHTL_OK) return rc;
     }
     if (n == 0 || (turns == 0 && !mon)) return PHTL_OK;
+    rc = ensure_slots(h, n);
+    if (rc != PHTL_OK) return rc;
     LaunchDesc L;
     rc = coll_launch(h, c, n, integrator, dtype, L);
     if (rc != PHTL_OK) return rc;

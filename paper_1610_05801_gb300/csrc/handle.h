@@ -51,6 +51,9 @@ struct phtl_handle {
     unsigned* wake_counts = nullptr;
     phtl::CollArgs coll{};
     int wake_device = -1;
+    // per-particle slice of the last slicing (2 bytes per particle, grown on demand)
+    uint16_t* coll_slot = nullptr;
+    int64_t coll_slot_cap = 0;
     phtl_stats stats{};
 };
 

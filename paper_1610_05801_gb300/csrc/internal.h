@@ -193,6 +193,65 @@ __device__ __forceinline__ void griddep_launch_dependents()
     asm volatile("griddepcontrol.launch_dependents;" :::);
 }
 
+// Per-particle slice of the collective step's last slicing, kept between the turn kernel that
+// counts a particle and the next one, which kicks it by that slice: 2 bytes per particle,
+// kSlotOutside for a particle outside the grid.  NP consecutive particles from base (a
+// multiple of NP, so the vector access is NP * 2-byte aligned).
+constexpr unsigned kSlotOutside = 0xFFFFu;
+
+template <int NP>
+__device__ __forceinline__ void slots_load(const uint16_t* __restrict__ s, int64_t base, int64_t n,
+                                           int (&k)[NP])
+{
+    static_assert(NP == 2 || NP == 4, "2 or 4 particles per thread");
+    if (base + NP <= n) {
+        if constexpr (NP == 2) {
+            const unsigned v = *reinterpret_cast<const unsigned*>(s + base);
+            k[0] = static_cast<int>(v & 0xFFFFu);
+            k[1] = static_cast<int>(v >> 16);
+        } else {
+            const uint2 v = *reinterpret_cast<const uint2*>(s + base);
+            k[0] = static_cast<int>(v.x & 0xFFFFu);
+            k[1] = static_cast<int>(v.x >> 16);
+            k[2] = static_cast<int>(v.y & 0xFFFFu);
+            k[3] = static_cast<int>(v.y >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) k[p] = base + p < n ? static_cast<int>(s[base + p]) : kSlotOutside;
+    }
+}
+
+// k[p] < 0 is stored as kSlotOutside.
+template <int NP>
+__device__ __forceinline__ void slots_store(uint16_t* __restrict__ s, int64_t base, int64_t n,
+                                            const int (&k)[NP])
+{
+    unsigned v[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) v[p] = k[p] < 0 ? kSlotOutside : static_cast<unsigned>(k[p]);
+    if (base + NP <= n) {
+        if constexpr (NP == 2)
+            *reinterpret_cast<unsigned*>(s + base) = v[0] | (v[1] << 16);
+        else
+            *reinterpret_cast<uint2*>(s + base) = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+    } else {
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+            if (base + p < n) s[base + p] = static_cast<uint16_t>(v[p]);
+    }
+}
+
+// floor(u) of a double u with 0 <= u < 4096, from its high word alone (the integer part
+// has at most 12 bits, all among the 21 leading significand bits held there); no FP64
+// instruction.  hi: the high word of u's bit pattern, non-negative.
+__device__ __forceinline__ int floor_small(int hi)
+{
+    const int e = (hi >> 20) - 1023;  // unbiased exponent
+    if (e < 0) return 0;              // u < 1 (zero and subnormals included)
+    return ((hi & 0xFFFFF) | 0x100000) >> (20 - e);
+}
+
 inline cudaError_t launch_pdl(const void* k, dim3 grid, dim3 block, void** args, size_t smem,
                               cudaStream_t s)
 {
@@ -246,17 +305,19 @@ int occupancy_ramp(int scheme, int dtype, int block);
 // Collective step kernels (track_collective.cu): one turn (optionally the previous turn's
 // kick U first, a monitor row, the map, the slicing of the new z), and the per-slice wake
 // potential V and kick U.
+// slot: the per-particle slices (written when counting, read when kicking).
 cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
-                             const double* U, unsigned* counts, double* mon_rows, int64_t rec_row,
-                             bool kick, bool map, cudaStream_t s);
+                             const double* U, unsigned* counts, uint16_t* slot, double* mon_rows,
+                             int64_t rec_row, bool kick, bool map, cudaStream_t s);
 cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
                                   double* V, double* U, float2* U2, unsigned* clear, cudaStream_t s);
 int occupancy_coll(int scheme, int block, int nslices);
 // The FP32-compensated turn kernel (track_collective_f32.cu): the same steps on float-pair
 // state, the kick read from U2 (U as hi + lo floats).
 cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
-                                 const float2* U2, unsigned* counts, double* mon_rows,
-                                 int64_t rec_row, bool kick, bool map, int dtype, cudaStream_t s);
+                                 const float2* U2, unsigned* counts, uint16_t* slot,
+                                 double* mon_rows, int64_t rec_row, bool kick, bool map, int dtype,
+                                 cudaStream_t s);
 int occupancy_coll_f32(int scheme, int dtype, int block, int nslices);
 
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).

@@ -11,11 +11,12 @@
 // in registers across turns as in the persistent kernels: each turn is one launch of
 // k_coll_turn (apply the previous turn's kick, record the monitor row, run the turn's map,
 // count the new z into a block-private shared-memory histogram that is flushed to the
-// global counts with one atomic per non-empty slice), then one launch of k_wake_potential
+// global counts with one atomic per non-empty slice, and keep each particle's slice for the
+// next launch's kick), then one launch of k_wake_potential
 // (counts and table staged in shared memory, one warp per slice, lane-strided partial sums
 // and a shuffle reduction; it also clears the other counts buffer for the next turn).  The state makes one HBM round trip per
-// turn (96 bytes per particle with both transverse planes), well under the FP64 work of
-// the turn on GB300.  Integer counts make the histogram exact and independent of the
+// turn (96 bytes per particle with both transverse planes, and 4 bytes of slices), well
+// under the FP64 work of the turn on GB300.  Integer counts make the histogram exact and independent of the
 // order of the atomics.
 #include <cuda_runtime.h>
 
@@ -32,18 +33,18 @@ using namespace f64;
 
 // Slice of z on the uniform grid [z_lo, z_lo + ns / inv_dz), or -1 outside: the same two
 // FP64 operations (subtract, multiply) as the definition give u, and the decision
-// 0 <= u < ns, k = floor(u) is taken exactly, on u's bit pattern: non-negative doubles
-// order like their bits (-0.0 counts as 0; NaN and +Inf lie above every finite bound),
-// and adding 2^52 rounded down leaves floor(u) in the low mantissa bits.  Three FP64
-// operations instead of the compare, floor and conversion instructions, which also run
-// on the FP64 pipe.  ns_bits: the bit pattern of (double)ns.
-__device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, long long ns_bits)
+// 0 <= u < ns, k = floor(u) is taken exactly on u's bit pattern with integer instructions:
+// non-negative doubles order like their bits, so u < ns (ns integral, its low word zero)
+// is hi < ns_hi on the high words; -0.0 counts as 0; NaN and +Inf lie above every finite
+// bound.  The compare, floor and conversion instructions would run on the FP64 pipe.
+// ns_hi: the high word of (double)ns.
+__device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, int ns_hi)
 {
     const double u = __dmul_rn(__dsub_rn(z, z_lo), inv_dz);
-    long long b = __double_as_longlong(u);
-    if (b == static_cast<long long>(0x8000000000000000ull)) b = 0;  // -0.0
-    if (b < 0 || b >= ns_bits) return -1;
-    return __double2loint(__dadd_rd(u, 4503599627370496.0));      // floor(u) < ns <= 4096
+    const int hi = __double2hiint(u);
+    if (hi < 0) return ((hi << 1) | __double2loint(u)) == 0 ? 0 : -1;  // -0.0, or u < 0
+    if (hi >= ns_hi) return -1;
+    return floor_small(hi);
 }
 
 // One turn of the collective tracking for one particle chunk per loop iteration.
@@ -51,12 +52,14 @@ __device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, lo
 //   rec:   monitor row to record after the kick (-1: none)
 //   map:   run the turn's map and the transverse rotation
 //   cnt:   counts buffer for the new z (nullptr: no slicing)
+//   slot:  per-particle slices: written with the counts, read by the kick (the kick of the
+//          next launch needs the slice of the same z, so it is decided once per turn)
 // Shared memory: ns uint32 histogram bins, then the monitor's 2 * warps * 16 DF2.
 template <int S>
 __global__ void __launch_bounds__(256, 3)
     k_coll_turn(LaunchDesc L, MapConsts c, CollArgs A, const double* __restrict__ U,
-                unsigned* __restrict__ counts, double* __restrict__ mon_rows, int64_t rec_row,
-                int kick, int map)
+                unsigned* __restrict__ counts, uint16_t* __restrict__ slot,
+                double* __restrict__ mon_rows, int64_t rec_row, int kick, int map)
 {
     extern __shared__ double smem_d[];
     unsigned* hist = reinterpret_cast<unsigned*>(smem_d);
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(256, 3)
     int parity = 0;
     double g1[4], g2[4];
     slip_stages<S>(c, g1, g2);
-    const long long ns_bits = __double_as_longlong(static_cast<double>(A.nslices));
+    const int ns_hi = __double2hiint(static_cast<double>(A.nslices));
     for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
         const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
         double z[P], d[P], x[P], xp[P], y[P], yp[P];
@@ -94,11 +97,11 @@ __global__ void __launch_bounds__(256, 3)
         const int64_t left = L.n - base;
         const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
         if (kick) {
+            int k[P];
+            slots_load<P>(slot, base, L.n, k);
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const int k = base + p < L.n ? slice_of(z[p], A.z_lo, A.inv_dz, ns_bits) : -1;
-                if (k >= 0) d[p] = d[p] + __ldg(U + k);
-            }
+            for (int p = 0; p < P; ++p)
+                if (k[p] != static_cast<int>(kSlotOutside)) d[p] = d[p] + __ldg(U + k[p]);
         }
         if (mon_rows && rec_row >= 0) {
             record<true>(z, d, x, xp, y, yp, cnt, hx, hy, msm, parity, mon_rows, rec_row);
@@ -110,11 +113,13 @@ __global__ void __launch_bounds__(256, 3)
             transverse_gen(x, xp, y, yp, d, hx, hy, c);
         }
         if (counts) {
+            int k[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const int k = base + p < L.n ? slice_of(z[p], A.z_lo, A.inv_dz, ns_bits) : -1;
-                if (k >= 0) atomicAdd(hist + k, 1u);
+                k[p] = base + p < L.n ? slice_of(z[p], A.z_lo, A.inv_dz, ns_hi) : -1;
+                if (k[p] >= 0) atomicAdd(hist + k[p], 1u);
             }
+            slots_store<P>(slot, base, L.n, k);
         }
         store2(g[0], base, L.n, vec, z);
         store2(g[1], base, L.n, vec, d);
@@ -222,8 +227,8 @@ int occupancy_coll(int scheme, int block, int nslices)
 }
 
 cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
-                             const double* U, unsigned* counts, double* mon_rows, int64_t rec_row,
-                             bool kick, bool map, cudaStream_t s)
+                             const double* U, unsigned* counts, uint16_t* slot, double* mon_rows,
+                             int64_t rec_row, bool kick, bool map, cudaStream_t s)
 {
     const void* k = coll_kernel(L.scheme);
     if (!k) return cudaErrorInvalidValue;
@@ -232,10 +237,11 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
     CollArgs aa = A;
     const double* vv = U;
     unsigned* cn = counts;
+    uint16_t* sl = slot;
     double* mr = mon_rows;
     int64_t rr = rec_row;
     int kk = kick ? 1 : 0, mm = map ? 1 : 0;
-    void* args[] = {&Lc, &cc, &aa, &vv, &cn, &mr, &rr, &kk, &mm};
+    void* args[] = {&Lc, &cc, &aa, &vv, &cn, &sl, &mr, &rr, &kk, &mm};
     return launch_pdl(k, dim3(L.grid), dim3(L.block), args, coll_smem(L.block, A.nslices), s);
 }
 

@@ -5,7 +5,8 @@
 //   - The previous turn's kick U_k (alpha V_k + alpha_sc D_k, formed in FP64 by
 //     k_wake_potential and kept as a float pair) is added with TwoSum (PHTL_F32C/CD) or
 //     as one float increment (PHTL_F32CS).
-//   - The slice of a particle: PHTL_F32C takes the same FP64 decision as the FP64 kernel on
+//   - The slice of a particle (decided once per turn, when counting, and kept per particle
+//     for the next launch's kick): PHTL_F32C takes the same FP64 decision as the FP64 kernel on
 //     hi + comp (exact in FP64); PHTL_F32CD and PHTL_F32CS form u = (z - z_lo) inv_dz in
 //     double-float and take floor(u_hi + u_lo) exactly from the pair (u_hi integral with a
 //     negative low part lies below u_hi).  Their decisions can differ from the FP64 oracle's
@@ -23,15 +24,15 @@ namespace {
 using namespace f32c;
 
 template <int DT>
-__device__ __forceinline__ int slice_pair(const DF& z, const CollArgs& A, long long ns_bits)
+__device__ __forceinline__ int slice_pair(const DF& z, const CollArgs& A, int ns_hi)
 {
     if (DT == PHTL_F32C) {
         const double zd = widen_bits(z.hi) + widen_bits(z.c);
         const double u = __dmul_rn(__dsub_rn(zd, A.z_lo), A.inv_dz);
-        long long b = __double_as_longlong(u);
-        if (b == static_cast<long long>(0x8000000000000000ull)) b = 0;
-        if (b < 0 || b >= ns_bits) return -1;
-        return __double2loint(__dadd_rd(u, 4503599627370496.0));
+        const int hi = __double2hiint(u);
+        if (hi < 0) return ((hi << 1) | __double2loint(u)) == 0 ? 0 : -1;  // -0.0, or u < 0
+        if (hi >= ns_hi) return -1;
+        return floor_small(hi);
     }
     const DF2 t = df_add(as2(z), DF2{-A.z_lo_h, -A.z_lo_l});
     const DF2 u = df_mul(t, DF2{A.inv_dz_h, A.inv_dz_l});
@@ -45,8 +46,8 @@ __device__ __forceinline__ int slice_pair(const DF& z, const CollArgs& A, long l
 template <int S, int DT>
 __global__ void PHTL_F32C_BOUNDS
     k_coll_turn_f32(LaunchDesc L, MapConsts c, CollArgs A, const float2* __restrict__ U2,
-                    unsigned* __restrict__ counts, double* __restrict__ mon_rows, int64_t rec_row,
-                    int kick, int map)
+                    unsigned* __restrict__ counts, uint16_t* __restrict__ slot,
+                    double* __restrict__ mon_rows, int64_t rec_row, int kick, int map)
 {
     extern __shared__ double smem_d[];
     unsigned* hist = reinterpret_cast<unsigned*>(smem_d);
@@ -65,7 +66,7 @@ __global__ void PHTL_F32C_BOUNDS
     int parity = 0;
     float g1h[4], g1l[4], g2h[4], g2l[4];
     slip_stages<S>(c, g1h, g1l, g2h, g2l);
-    const long long ns_bits = __double_as_longlong(static_cast<double>(A.nslices));
+    const int ns_hi = __double2hiint(static_cast<double>(A.nslices));
     for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
         const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
         DF z[P], d[P], x[P], xp[P], y[P], yp[P];
@@ -84,11 +85,12 @@ __global__ void PHTL_F32C_BOUNDS
         const int64_t left = L.n - base;
         const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
         if (kick) {
+            int k[P];
+            slots_load<P>(slot, base, L.n, k);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const int k = base + p < L.n ? slice_pair<DT>(z[p], A, ns_bits) : -1;
-                if (k >= 0) {
-                    const float2 u = __ldg(U2 + k);
+                if (k[p] != static_cast<int>(kSlotOutside)) {
+                    const float2 u = __ldg(U2 + k[p]);
                     if (DT == PHTL_F32CS) acc(d[p], u.x);
                     else acc2(d[p], DF2{u.x, u.y});
                 }
@@ -108,11 +110,13 @@ __global__ void PHTL_F32C_BOUNDS
             transverse_gen<DT>(x, xp, y, yp, d, hx, hy, c);
         }
         if (counts) {
+            int k[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const int k = base + p < L.n ? slice_pair<DT>(z[p], A, ns_bits) : -1;
-                if (k >= 0) atomicAdd(hist + k, 1u);
+                k[p] = base + p < L.n ? slice_pair<DT>(z[p], A, ns_hi) : -1;
+                if (k[p] >= 0) atomicAdd(hist + k[p], 1u);
             }
+            slots_store<P>(slot, base, L.n, k);
         }
         store4(g[0], base, L.n, vec, z);
         store4(g[1], base, L.n, vec, d);
@@ -174,8 +178,9 @@ int occupancy_coll_f32(int scheme, int dtype, int block, int nslices)
 }
 
 cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
-                                 const float2* U2, unsigned* counts, double* mon_rows,
-                                 int64_t rec_row, bool kick, bool map, int dtype, cudaStream_t s)
+                                 const float2* U2, unsigned* counts, uint16_t* slot,
+                                 double* mon_rows, int64_t rec_row, bool kick, bool map, int dtype,
+                                 cudaStream_t s)
 {
     const void* k = coll_kernel_f32(L.scheme, dtype);
     if (!k) return cudaErrorInvalidValue;
@@ -184,10 +189,11 @@ cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const 
     CollArgs aa = A;
     const float2* uu = U2;
     unsigned* cn = counts;
+    uint16_t* sl = slot;
     double* mr = mon_rows;
     int64_t rr = rec_row;
     int kk = kick ? 1 : 0, mm = map ? 1 : 0;
-    void* args[] = {&Lc, &cc, &aa, &uu, &cn, &mr, &rr, &kk, &mm};
+    void* args[] = {&Lc, &cc, &aa, &uu, &cn, &sl, &mr, &rr, &kk, &mm};
     return launch_pdl(k, dim3(L.grid), dim3(L.block), args, smem_bytes(L.block, A.nslices), s);
 }
 

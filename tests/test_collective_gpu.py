@@ -202,6 +202,42 @@ def test_ragged_small(n):
     assert np.allclose(mg[:, :4], mr[:, :4], rtol=1e-9, atol=1e-18)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32cd"])
+def test_one_ring_growing_and_shrinking_bunches(dtype):
+    """The slice of each particle is kept between launches in a buffer of the ring's that
+    grows with the bunch: calls with 1001, 5003, 3 and 4099 particles on one ring, a one-step
+    kick in between, each against the oracle (no slice of an earlier call leaks in)."""
+    g, w = grid(64), wake_table(64)
+    alpha = -2e-9
+    R = phtl.Ring(**widened_inputs(1, seed=1)["ring"])
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha)
+    tol = 1e-10 if dtype == "f64" else 1e-8
+    for i, n in enumerate((1001, 5003, 3, 4099)):
+        inp = widened_inputs(n, seed=60 + i)
+        if dtype == "f64":
+            bufs = [_t(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+        else:
+            bufs = [_pair(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+        R.track_collective(*bufs, turns=200, integrator="leapfrog", dtype=dtype)
+        torch.cuda.synchronize()
+        got = [b.cpu().numpy() if dtype == "f64" else phtl.join_f32c(b.cpu().numpy()) for b in bufs]
+        ref, _ = run_ref(inp, "leapfrog", 200, w, g, alpha)
+        assert errors(inp, got, ref) < tol, (n, errors(inp, got, ref))
+        if n == 5003:
+            # a one-step kick on the first 1000 particles of the tracked bunch
+            z0 = got[0][:1000].copy()
+            d0 = got[1][:1000].copy()
+            zt, dt = (_t(z0), _t(d0)) if dtype == "f64" else (_pair(z0), _pair(d0))
+            R.collective_kick(zt, dt, dtype=dtype)
+            torch.cuda.synchronize()
+            d1 = dt.cpu().numpy() if dtype == "f64" else phtl.join_f32c(dt.cpu().numpy())
+            _, dref, _, _ = oracle.collective_kick(z0, d0, g["z_lo"], g["inv_dz"], w, alpha)
+            # V to rounding (1000 counts at most); the pair's precision on delta itself
+            scale = abs(alpha) * np.max(np.abs(w)) * 1000
+            assert np.max(np.abs(d1 - dref)) <= 1e-12 * scale + 1e-14 * np.max(np.abs(d0))
+    R.close()
+
+
 def test_zero_turns_records_row_zero_only():
     inp = widened_inputs(1001, seed=41)
     g, w = grid(32), wake_table(32)
