@@ -509,7 +509,7 @@ def run_ours(args, wl_name, wl):
 # persistent FP64 kernel, from one ncu capture of the current kernel on a 3e6-particle case
 # (state larger than L2); the launch's traffic grows in proportion to its particles.
 # Summary: profiles/k_track_f64_ruth4_transverse_monitor_3e6x100.md.
-NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.428032e6 + 83.029248e6) / 3e6}
+NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.354816e6 + 82.915840e6) / 3e6}
 
 
 def kernel_traffic(dt, scheme, wl, n):
