@@ -449,10 +449,9 @@ def run_ours(args, wl_name, wl):
     if wl.get("ramp"):
         flops_pt += RAMP_FLOPS
     if wl.get("wake"):
-        # the general kernel's drifts, and per particle the slice index (subtract, multiply)
-        # and the kick's add
-        flops_pt += {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4, "rk4": 0}[dom] * (
-            DRIFT_FLOPS_NL - DRIFT_FLOPS) + COLLECTIVE_FLOPS
+        # per particle the slice index (subtract, multiply) and the kick's add (the map's
+        # flops are the ring's, linear or widened, as for the other workloads)
+        flops_pt += COLLECTIVE_FLOPS
     flops = flops_pt * n * tpl
     achieved = flops / dur_s / 1e12
 

@@ -21,7 +21,7 @@ SOURCES = ["api.cu", "api_programme.cu", "api_collective.cu", "track_f64.cu", "t
            "track_general_batched.cu", "track_general_rk4.cu", "track_general_batched_f32.cu",
            "track_general_dual.cu", "track_general_dual_f32.cu",
            "track_ramp.cu", "track_collective.cu",
-           "track_collective_f32.cu", "batch.cu", "server.cu", "batch_static.cu"]
+           "track_collective_f32.cu", "track_collective_f32_lin.cu", "batch.cu", "server.cu", "batch_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -96,8 +96,10 @@ namespace {
 int coll_launch(phtl_handle* h, void* const* c, int64_t n, int integrator, int dtype, LaunchDesc& L)
 {
     const int block = h->block > 0 ? h->block : 128;
-    const int occ = dtype == PHTL_F64 ? occupancy_coll(integrator, block, h->coll.nslices)
-                                      : occupancy_coll_f32(integrator, dtype, block, h->coll.nslices);
+    const int occ = dtype == PHTL_F64 ? occupancy_coll(integrator, h->mc[integrator].general != 0, block,
+                                                       h->coll.nslices)
+                                      : occupancy_coll_f32(integrator, dtype, h->mc[integrator].general != 0,
+                                                           block, h->coll.nslices);
     if (occ <= 0) return PHTL_E_INVALID;
     const int64_t chunk = static_cast<int64_t>(block) * particles_per_thread(dtype);
     const int64_t nchunks = (n + chunk - 1) / chunk;

@@ -311,14 +311,16 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
                              int64_t rec_row, bool kick, bool map, cudaStream_t s);
 cudaError_t launch_wake_potential(const unsigned* counts, const double* w, const CollArgs& A,
                                   double* V, double* U, float2* U2, unsigned* clear, cudaStream_t s);
-int occupancy_coll(int scheme, int block, int nslices);
+int occupancy_coll(int scheme, bool gen, int block, int nslices);  // gen: MapConsts::general
 // The FP32-compensated turn kernel (track_collective_f32.cu): the same steps on float-pair
 // state, the kick read from U2 (U as hi + lo floats).
 cudaError_t launch_coll_turn_f32(const LaunchDesc& L, const MapConsts& c, const CollArgs& A,
                                  const float2* U2, unsigned* counts, uint16_t* slot,
                                  double* mon_rows, int64_t rec_row, bool kick, bool map, int dtype,
                                  cudaStream_t s);
-int occupancy_coll_f32(int scheme, int dtype, int block, int nslices);
+int occupancy_coll_f32(int scheme, int dtype, bool gen, int block, int nslices);
+// The linear map's FP32 collective turn kernels (track_collective_f32_lin.cu; not RK4).
+const void* coll_kernel_f32_lin(int scheme, int dtype);
 
 // Kernels of the widened map (track_general.cu, track_general_batched.cu).
 const void* general_kernel_single(int scheme, int dtype, bool dual);

@@ -54,8 +54,11 @@ __device__ __forceinline__ int slice_of(double z, double z_lo, double inv_dz, in
 //   cnt:   counts buffer for the new z (nullptr: no slicing)
 //   slot:  per-particle slices: written with the counts, read by the kick (the kick of the
 //          next launch needs the slice of the same z, so it is decided once per turn)
+// GEN: the widened map's code (slippage expansion, chromaticity, second RF system, RK4);
+// otherwise the linear map's, which a ring without those terms gives bitwise the same result
+// with fewer FP64 operations (a drift is one FMA instead of three).
 // Shared memory: ns uint32 histogram bins, then the monitor's 2 * warps * 16 DF2.
-template <int S>
+template <int S, bool GEN>
 __global__ void __launch_bounds__(256, 3)
     k_coll_turn(LaunchDesc L, MapConsts c, CollArgs A, const double* __restrict__ U,
                 unsigned* __restrict__ counts, uint16_t* __restrict__ slot,
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(256, 3)
     const int64_t nchunks = (L.n + chunk - 1) / chunk;
     int parity = 0;
     double g1[4], g2[4];
-    slip_stages<S>(c, g1, g2);
+    if (GEN) slip_stages<S>(c, g1, g2);
     const int ns_hi = __double2hiint(static_cast<double>(A.nslices));
     for (int64_t ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
         const int64_t base = ci * chunk + static_cast<int64_t>(threadIdx.x) * P;
@@ -108,9 +111,16 @@ __global__ void __launch_bounds__(256, 3)
             parity ^= 1;
         }
         if (map) {
-            if (c.phis_zero) long_turn_nl<S, true>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, c.dual_rf != 0);
-            else long_turn_nl<S, false>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, c.dual_rf != 0);
-            transverse_gen(x, xp, y, yp, d, hx, hy, c);
+            if constexpr (GEN) {
+                if (c.phis_zero) long_turn_nl<S, true>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, c.dual_rf != 0);
+                else long_turn_nl<S, false>(z, d, c, c.dc, c.kw, c.kw2, g1, g2, c.dual_rf != 0);
+                transverse_gen(x, xp, y, yp, d, hx, hy, c);
+            } else {
+                if (c.phis_zero) long_turn<S, true>(z, d, c, c.dc, c.kw);
+                else long_turn<S, false>(z, d, c, c.dc, c.kw);
+                if (hx) rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
+                if (hy) rotate(y, yp, c.my, c.shy, c.shear_y != 0);
+            }
         }
         if (counts) {
             int k[P];
@@ -189,17 +199,20 @@ __global__ void __launch_bounds__(256)
 }
 
 template <int S>
-const void* coll_kernel_s()
+const void* coll_kernel_s(bool gen)
 {
-    return reinterpret_cast<const void*>(&k_coll_turn<S>);
+    return gen ? reinterpret_cast<const void*>(&k_coll_turn<S, true>)
+               : reinterpret_cast<const void*>(&k_coll_turn<S, false>);
 }
 
-const void* coll_kernel(int scheme)
+// The linear map's variant where the ring has no widened term (RK4 always takes the
+// widened map's code).
+const void* coll_kernel(int scheme, bool gen)
 {
-    if (scheme == PHTL_EULER_CROMER) return coll_kernel_s<PHTL_EULER_CROMER>();
-    if (scheme == PHTL_LEAPFROG) return coll_kernel_s<PHTL_LEAPFROG>();
-    if (scheme == PHTL_RUTH4) return coll_kernel_s<PHTL_RUTH4>();
-    if (scheme == PHTL_RK4) return coll_kernel_s<PHTL_RK4>();
+    if (scheme == PHTL_EULER_CROMER) return coll_kernel_s<PHTL_EULER_CROMER>(gen);
+    if (scheme == PHTL_LEAPFROG) return coll_kernel_s<PHTL_LEAPFROG>(gen);
+    if (scheme == PHTL_RUTH4) return coll_kernel_s<PHTL_RUTH4>(gen);
+    if (scheme == PHTL_RK4) return reinterpret_cast<const void*>(&k_coll_turn<PHTL_RK4, true>);
     return nullptr;
 }
 
@@ -210,9 +223,9 @@ size_t coll_smem(int block, int ns)
 
 }  // namespace
 
-int occupancy_coll(int scheme, int block, int nslices)
+int occupancy_coll(int scheme, bool gen, int block, int nslices)
 {
-    const void* k = coll_kernel(scheme);
+    const void* k = coll_kernel(scheme, gen);
     if (!k) return 0;
     const size_t sm = coll_smem(block, nslices);
     if (sm > 48 * 1024 &&
@@ -230,7 +243,7 @@ cudaError_t launch_coll_turn(const LaunchDesc& L, const MapConsts& c, const Coll
                              const double* U, unsigned* counts, uint16_t* slot, double* mon_rows,
                              int64_t rec_row, bool kick, bool map, cudaStream_t s)
 {
-    const void* k = coll_kernel(L.scheme);
+    const void* k = coll_kernel(L.scheme, c.general != 0);
     if (!k) return cudaErrorInvalidValue;
     LaunchDesc Lc = L;
     MapConsts cc = c;

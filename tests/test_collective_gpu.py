@@ -176,6 +176,48 @@ def test_turns_widened_double_rf():
     assert moment_errors(inp["d"], mg, mr) < 1e-9
 
 
+@pytest.mark.parametrize("dtype", ["f32c", "f32cd", "f32cs"])
+def test_turns_widened_double_rf_f32(dtype):
+    """The FP32 types on the widened, double-RF ring (the widened map's double-float code)."""
+    inp = widened_inputs(2049, seed=35, eta1=0.05, eta2=2.0, xi_x=5.0, xi_y=-3.0,
+                         harmonic2=2 * 4620, voltage2_V=1.35e6, phi2_rad=0.0)
+    ns = 200
+    g, w = grid(ns), wake_table(ns, seed=4)
+    R = phtl.Ring(**inp["ring"])
+    R.set_wake(w, g["z_lo"], g["z_hi"], 3e-9)
+    bufs = [_pair(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    mon = torch.zeros((500 // 50 + 1, phtl.MON_FIELDS), dtype=torch.float64, device=DEV)
+    R.set_monitor(mon, stride=50)
+    R.track_collective(*bufs, turns=500, integrator="ruth4", dtype=dtype)
+    torch.cuda.synchronize()
+    got = [phtl.join_f32c(b.cpu().numpy()) for b in bufs]
+    mg = phtl.moments_from_sums(mon.cpu().numpy())
+    R.close()
+    ref, mr = run_ref(inp, "ruth4", 500, w, g, 3e-9, stride=50)
+    tol = {"f32c": (1e-8, 1e-6), "f32cd": (1e-8, 1e-6), "f32cs": (2e-2, 2e-3)}[dtype]
+    assert errors(inp, got, ref) < tol[0], errors(inp, got, ref)
+    assert moment_errors(inp["d"], mg, mr) < tol[1]
+
+
+@pytest.mark.parametrize("dtype", ["f32cd", "f32cs"])
+@pytest.mark.parametrize("scheme", ["leapfrog", "ruth4"])
+def test_zero_strength_equals_plain_tracking_f32(dtype, scheme):
+    """alpha = 0 in the FP32 types: bitwise the pairs of phtl_track (the linear map's
+    double-float code on both sides)."""
+    inp = widened_inputs(3001, seed=38)
+    g, w = grid(64), wake_table(64)
+    R = phtl.Ring(**inp["ring"])
+    R.set_wake(w, g["z_lo"], g["z_hi"], 0.0)
+    a = [_pair(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    b = [_pair(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    R.track_collective(*a, turns=300, integrator=scheme, dtype=dtype)
+    R.track(*b, turns=300, integrator=scheme, dtype=dtype)
+    torch.cuda.synchronize()
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+    R.close()
+
+
 @pytest.mark.parametrize("scheme", ["euler_cromer", "ruth4"])
 def test_zero_strength_equals_plain_tracking(scheme):
     """alpha = 0: bitwise the particles of phtl_track (the turn's map is the same code; the
