@@ -289,7 +289,9 @@ typedef struct phtl_wake {
  * per-slice kick: 32 bytes per slice, freed by phtl_destroy or a detaching call.  The
  * collective calls below also keep each particle's slice between two launches in
  * library-owned memory (2 bytes per particle, allocated by the first call with more
- * particles than before, which synchronises the device; freed with the wake).
+ * particles than before, which synchronises the device; freed with the wake).  These
+ * buffers belong to the handle: collective calls on one handle must be ordered (one
+ * stream, or streams synchronised between the calls); use one handle per concurrent bunch.
  * Synchronous.
  * Errors: PHTL_E_BADHANDLE; PHTL_E_INVALID (nslices out of range, z_hi <= z_lo,
  * non-finite values, w NULL); PHTL_E_NODEVICE; PHTL_E_NOMEM.                           */
