@@ -98,6 +98,55 @@ def test_range_edges_and_outside_particles():
     R.close()
 
 
+def _edge_positions(ns):
+    """Positions on [0, 1) whose slice decision sits on a bit-pattern edge: signed zeros,
+    subnormals, the slice edges k / ns and their neighbours, the top edge and just below it,
+    non-finite values."""
+    tiny = 5e-324
+    zs = [-0.0, 0.0, tiny, -tiny, 2.2250738585072014e-308, -1e-300, 1.0, 1.0 - 2.0 ** -53,
+          np.nextafter(1.0, 2.0), float("nan"), -float("nan"), float("inf"), -float("inf"), 0.5]
+    for k in range(0, ns + 1, max(1, ns // 37)):
+        e = k / ns
+        zs += [e, np.nextafter(e, -1.0), np.nextafter(e, 2.0)]
+    return np.array(zs, dtype=np.float64)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32c"])
+@pytest.mark.parametrize("ns", [1, 3, 7, 4096])
+def test_slice_decision_at_bit_pattern_edges(ns, dtype):
+    """The slice decision (two FP64 operations, then integer range test and floor on u's bit
+    pattern) counts exactly the particles the oracle's floor((z - z_lo) inv_dz) counts, on
+    signed zeros, subnormals, every slice edge and its neighbours, the top edge and
+    non-finite positions; the kick then moves exactly those particles.  FP32C decides on
+    hi + comp in FP64, so it takes positions that a float pair holds exactly."""
+    z = _edge_positions(ns)
+    if dtype == "f32c":
+        z = np.array([v for v in z if not np.isfinite(v) or float(np.float32(v)) == v
+                      or v == 0.0], dtype=np.float64)
+    dp = np.linspace(-1e-3, 1e-3, z.size)
+    if dtype == "f32c":
+        dp = phtl.join_f32c(phtl.split_f32c(dp))  # values a float pair holds exactly
+    w = wake_table(ns)
+    alpha = -1e-7
+    R = phtl.Ring(**widened_inputs(1, seed=1)["ring"])
+    R.set_wake(w, 0.0, 1.0, alpha)
+    with np.errstate(invalid="ignore"):  # the pair of an infinity has a NaN low part
+        zt = _t(z) if dtype == "f64" else _pair(z)
+    dt = _t(dp) if dtype == "f64" else _pair(dp)
+    cnt = torch.zeros(ns, dtype=torch.int32, device=DEV)
+    R.collective_kick(zt, dt, counts_out=cnt, dtype=dtype)
+    torch.cuda.synchronize()
+    _, d1, c_ref, V_ref = oracle.collective_kick(z, dp, 0.0, float(ns), w, alpha)
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), c_ref)
+    got = dt.cpu().numpy() if dtype == "f64" else phtl.join_f32c(dt.cpu().numpy())
+    moved_ref = d1 != dp
+    moved = got != dp
+    assert np.array_equal(moved, moved_ref)
+    vs = max(np.max(np.abs(V_ref)), 1.0)
+    assert np.max(np.abs(got - d1)) <= 1e-15 + abs(alpha) * 1e-13 * vs
+    R.close()
+
+
 def run_gpu(inp, scheme, turns, w, g, alpha, stride=None, tuning=None, alpha_sc=0.0):
     R = phtl.Ring(**inp["ring"])
     if tuning:
