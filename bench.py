@@ -492,7 +492,8 @@ def run_ours(args, wl_name, wl):
                            "counts and max clock); DFMA rate confirmed by a microbenchmark",
             "alg_flops_per_particle_turn": flops_pt,
             "moment_flops_per_particle_turn_fp32_pipe": MONITOR_FLOPS if wl["stride"] else 0,
-            "launch_ms": dur_s * 1e3, "turns_per_launch": tpl},
+            "launch_ms": dur_s * 1e3, "turns_per_launch": tpl,
+            **executed_flops(dt, dom, wl, n * tpl / dur_s)},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,
@@ -509,6 +510,28 @@ def run_ours(args, wl_name, wl):
 # (state larger than L2); the launch's traffic grows in proportion to its particles.
 # Summary: profiles/k_track_f64_ruth4_transverse_monitor_3e6x100.md.
 NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.354816e6 + 82.915840e6) / 3e6}
+
+
+# FP64 flops the kernel executes per particle-turn, from the same ncu capture:
+# (2 x DFMA + DMUL + DADD thread instructions per cycle) x cycles / particle-turns, i.e.
+# (2 x 225.610532 + 33.841580 + 0.475363) x 22.909184 ms x 2.043125 GHz / (3e6 x 88).
+# Fewer than the algorithmic count: for phi_s = 0 the kernel skips the phase addition and the
+# sin(phi_s) subtraction of the general kick and flips the sine's sign with an integer XOR.
+NCU_EXEC_FLOPS_PER_PARTICLE_TURN = {("f64", "ruth4", True, True):
+                                    (2 * 225.610532 + 33.841580 + 0.475363) * 22.909184e-3
+                                    * 2.043125e9 / (3e6 * 88)}
+
+
+def executed_flops(dt, scheme, wl, particle_turns_per_s):
+    """ncu's executed DP FLOP/s rescaled to the live launch duration, where a capture of
+    this kernel exists: the fraction of the FP64 peak the pipe's own flop count gives."""
+    key = (dt, scheme, bool(wl["transverse"]), bool(wl["stride"]))
+    f = NCU_EXEC_FLOPS_PER_PARTICLE_TURN.get(key)
+    if f is None or wl.get("perturn") or wl.get("ring") or wl.get("ramp") or wl.get("wake"):
+        return {}
+    tf = f * particle_turns_per_s / 1e12
+    return {"executed_flops_per_particle_turn_ncu": f, "executed_tflops": tf,
+            "executed_frac": tf / FP64_PEAK_TFLOPS}
 
 
 def kernel_traffic(dt, scheme, wl, n):
