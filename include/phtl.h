@@ -237,7 +237,7 @@ int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* 
  * The ring's harmonic, gamma_t, transverse optics and rf_linear flag apply to every turn;
  * the ring's own voltage_V, phi_s_rad and p0_eVc do not.  The constants of all turns are
  * derived in FP64 on the host (the long-horizon reference bookkeeping) and kept in a
- * library-owned device table of 96 bytes per turn (replacing any previous programme; freed
+ * library-owned device table of 192 bytes per turn (replacing any previous programme; freed
  * by phtl_destroy or a call with nturns == 0).  Synchronous.
  * Errors: PHTL_E_BADHANDLE; PHTL_E_INVALID (null arrays with nturns > 0, non-positive or
  * non-finite momenta, V = 0 on a turn whose momentum changes, a ring with eta1, eta2,

@@ -58,6 +58,16 @@ int derive_programme(const phtl_params& p, const double* V, const double* p0, in
         }
         T.lin = std::cos(T.phis) * k;
         T.r = pa / pb;
+        const struct {
+            int scheme;
+            double* w;
+            int nd, nk;
+        } sw[3] = {{PHTL_EULER_CROMER, T.w_ec, 1, 1}, {PHTL_LEAPFROG, T.w_lf, 2, 1},
+                   {PHTL_RUTH4, T.w_r4, 4, 3}};
+        for (const auto& e : sw) {
+            for (int i = 0; i < e.nd; ++i) e.w[i] = drift_weight(e.scheme, i) * T.etaC;
+            for (int j = 0; j < e.nk; ++j) e.w[e.nd + j] = kick_weight(e.scheme, j) * T.A;
+        }
         split_df(T.etaC, T.etaC_h, T.etaC_l);
         split_df(T.A, T.A_h, T.A_l);
         split_df(T.phis, T.phis_h, T.phis_l);

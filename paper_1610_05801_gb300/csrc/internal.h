@@ -102,8 +102,14 @@ struct RampTurn {
     double r;        // p0_n / p0_{n+1}: delta and the slopes are re-expressed after the turn
     // double-float copies for the FP32 paths (value = hi + lo)
     float etaC_h, etaC_l, A_h, A_l, phis_h, phis_l, sinphis_h, sinphis_l, lin_h, lin_l, r_h, r_l;
+    // each scheme's stage weights times this turn's eta_n C (drifts, first) and A_n (kicks),
+    // as FP64 products: Euler-Cromer {dc0, kw0}, leap-frog {dc0, dc1, kw0}, Ruth4
+    // {dc0..dc3, kw0..kw2}
+    double w_ec[2];
+    double w_lf[3];
+    double w_r4[7];
 };
-static_assert(sizeof(RampTurn) == 96, "RampTurn is 96 bytes");
+static_assert(sizeof(RampTurn) == 192, "RampTurn is 192 bytes");
 
 // Slicing grid and strength of the collective (wake) step.
 struct CollArgs {

@@ -5,12 +5,14 @@
 // The same persistent structure as the fixed-machine kernels (Sec. 2.3: turn loop inside
 // the kernel, state in registers, grid-stride over particle chunks), but each turn reads
 // its constants -- eta_n C, A_n, phi_s,n, sin(phi_s,n), r_n = p0_n / p0_{n+1} -- from a
-// device table that the host derived in FP64 (96 bytes per turn, the same address for
-// every thread, so the loads are L1 broadcasts).  The next turn's entry is loaded while
-// the current turn computes.  After the turn's stages and the transverse rotation, delta
-// and the slopes x', y' are re-expressed against the next turn's reference momentum
-// (multiplied by r_n).  Stage weights are the compile-time constants of the scheme times
-// the turn's eta_n C and A_n.  The kick is the general one (phi_s,n != 0 in general).
+// device table that the host derived in FP64 (192 bytes per turn, the same address for
+// every thread, so the loads are L1 broadcasts).  The next turn's phase constants are
+// loaded while the current turn computes.  After the turn's stages and the transverse
+// rotation, delta and the slopes x', y' are re-expressed against the next turn's reference
+// momentum (multiplied by r_n).  Stage weights are the compile-time constants of the scheme
+// times the turn's eta_n C and A_n: the FP64 kernels read these products from the table
+// (the host formed them, the same FP64 products), the FP32 kernels form them as
+// double-float products.  The kick is the general one (phi_s,n != 0 in general).
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -26,14 +28,12 @@ namespace rf64 {
 using namespace f64;
 
 struct Turn {
-    double etaC, A, phis, sinphis, lin, r;
+    double phis, sinphis, lin, r;
 };
 
 __device__ __forceinline__ Turn load_turn(const RampTurn* __restrict__ p)
 {
     Turn t;
-    t.etaC = __ldg(&p->etaC);
-    t.A = __ldg(&p->A);
     t.phis = __ldg(&p->phis);
     t.sinphis = __ldg(&p->sinphis);
     t.lin = __ldg(&p->lin);
@@ -41,10 +41,19 @@ __device__ __forceinline__ Turn load_turn(const RampTurn* __restrict__ p)
     return t;
 }
 
-__device__ __forceinline__ void kick(const double (&z)[P], double (&d)[P], double w,
+// The scheme's stage weights of one turn, precomputed on the host as the FP64 products of
+// the scheme's constants and eta_n C, A_n (drifts first, then kicks): the same values the
+// device would form, without spending FP64 operations on them every turn.
+template <int S>
+__device__ __forceinline__ const double* stage_weights(const RampTurn* __restrict__ e)
+{
+    return S == PHTL_EULER_CROMER ? e->w_ec : (S == PHTL_LEAPFROG ? e->w_lf : e->w_r4);
+}
+
+// delta += kw (sin(phi_s,n + k z) - sin(phi_s,n)), kw this stage's weight times A_n
+__device__ __forceinline__ void kick(const double (&z)[P], double (&d)[P], double kw,
                                      const Turn& T, const MapConsts& c)
 {
-    const double kw = w * T.A;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const double f = c.linear ? T.lin * z[p] : sin_f64(fma(c.k, z[p], T.phis)) - T.sinphis;
@@ -52,29 +61,25 @@ __device__ __forceinline__ void kick(const double (&z)[P], double (&d)[P], doubl
     }
 }
 
-__device__ __forceinline__ void drift_w(double (&z)[P], const double (&d)[P], double w, const Turn& T)
-{
-    drift(z, d, w * T.etaC);
-}
-
 template <int S>
-__device__ __forceinline__ void turn(double (&z)[P], double (&d)[P], const Turn& T, const MapConsts& c)
+__device__ __forceinline__ void turn(double (&z)[P], double (&d)[P], const Turn& T, const MapConsts& c,
+                                     const double* __restrict__ w)
 {
     if (S == PHTL_EULER_CROMER) {
-        kick(z, d, kick_weight(S, 0), T, c);
-        drift_w(z, d, drift_weight(S, 0), T);
+        kick(z, d, __ldg(w + 1), T, c);
+        drift(z, d, __ldg(w + 0));
     } else if (S == PHTL_LEAPFROG) {
-        drift_w(z, d, drift_weight(S, 0), T);
-        kick(z, d, kick_weight(S, 0), T, c);
-        drift_w(z, d, drift_weight(S, 1), T);
+        drift(z, d, __ldg(w + 0));
+        kick(z, d, __ldg(w + 2), T, c);
+        drift(z, d, __ldg(w + 1));
     } else {
-        drift_w(z, d, drift_weight(S, 0), T);
-        kick(z, d, kick_weight(S, 0), T, c);
-        drift_w(z, d, drift_weight(S, 1), T);
-        kick(z, d, kick_weight(S, 1), T, c);
-        drift_w(z, d, drift_weight(S, 2), T);
-        kick(z, d, kick_weight(S, 2), T, c);
-        drift_w(z, d, drift_weight(S, 3), T);
+        drift(z, d, __ldg(w + 0));
+        kick(z, d, __ldg(w + 4), T, c);
+        drift(z, d, __ldg(w + 1));
+        kick(z, d, __ldg(w + 5), T, c);
+        drift(z, d, __ldg(w + 2));
+        kick(z, d, __ldg(w + 6), T, c);
+        drift(z, d, __ldg(w + 3));
     }
 }
 
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(256, 2)
         for (int t = 0; t < L.nturns; ++t) {
             // the next turn's constants, loaded while this turn computes
             const Turn Tn = load_turn(prog + turn0 + (t + 1 < L.nturns ? t + 1 : t));
-            turn<S>(z, d, T, c);
+            turn<S>(z, d, T, c, stage_weights<S>(prog + turn0 + t));
             if (hx) rotate(x, xp, c.mx, c.shx, c.shear_x != 0);
             if (hy) rotate(y, yp, c.my, c.shy, c.shear_y != 0);
 #pragma unroll
