@@ -48,8 +48,19 @@ __device__ __forceinline__ int slice_pair(const DF& z, const CollArgs& A, int ns
     return (k >= 0 && k < A.nslices) ? k : -1;
 }
 
+// Register cap of the turn kernel.  Unlike the persistent FP32 kernels (issue-bound, state in
+// registers), it loads its state every turn and waits on memory, so more resident warps pay:
+// 96 registers (20 warps per SM at 128-thread blocks, a few bytes of spills in some variants)
+// ran 7-18 % faster than the uncapped 115-126 (16 warps) on GB300, 104 about 2 %, and 88 or
+// fewer spilled more.  Build option PHTL_COLL_F32_MAXNREG overrides it.  (Blocks are at most
+// 256 threads; __maxnreg__ and __launch_bounds__ do not combine.)
+#ifndef PHTL_COLL_F32_MAXNREG
+#define PHTL_COLL_F32_MAXNREG 96
+#endif
+#define PHTL_COLL_F32_BOUNDS __maxnreg__(PHTL_COLL_F32_MAXNREG)
+
 template <int S, int DT, bool GEN>
-__global__ void PHTL_F32C_BOUNDS
+__global__ void PHTL_COLL_F32_BOUNDS
     k_coll_turn_f32(LaunchDesc L, MapConsts c, CollArgs A, const float2* __restrict__ U2,
                     unsigned* __restrict__ counts, uint16_t* __restrict__ slot,
                     double* __restrict__ mon_rows, int64_t rec_row, int kick, int map)
