@@ -286,7 +286,8 @@ typedef struct phtl_wake {
 
 /* Attach a wake to the handle (NULL detaches).  The table is copied into library-owned
  * device memory together with the slice counts (two buffers), the wake potential and the
- * per-slice kick: 32 bytes per slice, freed by phtl_destroy or a detaching call.  The
+ * per-slice kick (in FP64 and as a float pair): 40 bytes per slice, freed by phtl_destroy
+ * or a detaching call.  The
  * collective calls below also keep each particle's slice between two launches in
  * library-owned memory (2 bytes per particle, allocated by the first call with more
  * particles than before, which synchronises the device; freed with the wake).  These
