@@ -329,6 +329,26 @@ def test_one_ring_growing_and_shrinking_bunches(dtype):
     R.close()
 
 
+@pytest.mark.parametrize("dtype", ["f32c", "f32cd"])
+@pytest.mark.parametrize("n", [1, 3, 5, 4097])
+def test_ragged_small_f32(dtype, n):
+    """FP32 types on sizes that leave a partial thread (4 particles per thread) and an
+    unaligned comp half: the kept slices take the scalar path there."""
+    inp = widened_inputs(n, seed=80 + n)
+    g, w = grid(16), wake_table(16)
+    alpha = -1e-6 if n < 10 else -2e-9
+    R = phtl.Ring(**inp["ring"])
+    R.set_tuning(block_threads=32)
+    R.set_wake(w, g["z_lo"], g["z_hi"], alpha)
+    bufs = [_pair(inp[k]) for k in ("z", "dp", "x", "xp", "y", "yp")]
+    R.track_collective(*bufs, turns=300, integrator="leapfrog", dtype=dtype)
+    torch.cuda.synchronize()
+    got = [phtl.join_f32c(b.cpu().numpy()) for b in bufs]
+    R.close()
+    ref, _ = run_ref(inp, "leapfrog", 300, w, g, alpha)
+    assert errors(inp, got, ref) < 1e-8, errors(inp, got, ref)
+
+
 def test_zero_turns_records_row_zero_only():
     inp = widened_inputs(1001, seed=41)
     g, w = grid(32), wake_table(32)
