@@ -108,11 +108,13 @@ DRIFT_FLOPS = 2
 SCHEME_FLOPS = {"euler_cromer": DRIFT_FLOPS + KICK_FLOPS,
                 "leapfrog": 2 * DRIFT_FLOPS + KICK_FLOPS,
                 "ruth4": 4 * DRIFT_FLOPS + 3 * KICK_FLOPS}
-# Classic RK4 per particle-turn: four right-hand sides, each the slippage term
-# -(eta0 C + eta1 C d + eta2 C d^2) d (2 FMA + 1 MUL = 5) and the force A F1(z) (phase FMA,
-# sine, subtract, multiply = 24); the stage arguments z + c k, d + c k (2 x 2 FMA + 2 ADD =
-# 10) and the weighted sums (per coordinate 2 ADD + 2 FMA = 6, x 2 = 12).
-RK4_RHS_FLOPS = 5 + 2 + SINE_FLOPS + 1 + 1
+# Classic RK4 per particle-turn: four right-hand sides, each the slippage term -eta0 C d
+# (1 MUL; with the expansion -(eta0 C + eta1 C d + eta2 C d^2) d, 2 FMA + 1 MUL = 5) and the
+# force A F1(z) (phase FMA, sine, subtract, multiply = 24); the stage arguments z + c k,
+# d + c k (2 x 2 FMA + 2 ADD = 10) and the weighted sums (per coordinate 2 ADD + 2 FMA = 6,
+# x 2 = 12).
+RK4_RHS_FLOPS = 1 + 2 + SINE_FLOPS + 1 + 1
+RK4_SLIP_NL_EXTRA = 4
 SCHEME_FLOPS["rk4"] = 4 * RK4_RHS_FLOPS + 10 + 12
 # the second RF system: each force evaluation adds phase FMA, sine, subtract and FMA
 RF2_FLOPS = 2 + SINE_FLOPS + 1 + 2
@@ -135,16 +137,22 @@ CHROMA_PLANE_FLOPS = 41
 
 
 def alg_flops(scheme, transverse, monitor, ring=None):
-    """FP64-pipe algorithmic flops per particle-turn (the monitor is FP32-pipe work)."""
+    """FP64-pipe algorithmic flops per particle-turn (the monitor is FP32-pipe work): the
+    method's arithmetic for the ring's parameters -- a drift takes the slippage expansion
+    only where eta1 or eta2 is nonzero (the widened map's kernels, which a chromaticity or
+    a second RF system also selects, execute the expansion's FMAs on zeros otherwise; those
+    are not counted)."""
     ring = ring or {}
     nl = ring.get("eta1", 0.0) != 0.0 or ring.get("eta2", 0.0) != 0.0
     chroma = [ring.get("xi_x", 0.0) != 0.0, ring.get("xi_y", 0.0) != 0.0]
     dual = ring.get("voltage2_V", 0.0) != 0.0
     f = SCHEME_FLOPS[scheme]
-    if (nl or any(chroma) or dual) and scheme != "rk4":
-        # the general kernel evaluates every drift with the expansion
-        ndrift = {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4}[scheme]
-        f += ndrift * (DRIFT_FLOPS_NL - DRIFT_FLOPS)
+    if nl:
+        if scheme == "rk4":
+            f += 4 * RK4_SLIP_NL_EXTRA
+        else:
+            ndrift = {"euler_cromer": 1, "leapfrog": 2, "ruth4": 4}[scheme]
+            f += ndrift * (DRIFT_FLOPS_NL - DRIFT_FLOPS)
     if dual:
         f += KICKS[scheme] * RF2_FLOPS
     if transverse:

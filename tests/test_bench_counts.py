@@ -1,0 +1,43 @@
+"""bench.py's roofline accounting on the CPU: the algorithmic FP64 flops per particle-turn that
+the roofline's `achieved` divides by the kernel's duration, spelled out term by term, and the
+executed-flop figure taken from the ncu capture of the Ruth4 kernel."""
+import bench
+
+
+def test_algorithmic_flops_of_the_paper_scale_workload():
+    # drift = 1 FMA (2 flops); kick = phase FMA (2) + sine (20) + subtract (1) + FMA (2) = 25;
+    # transverse = 2 planes x (2 MUL + 2 FMA) = 12
+    assert bench.KICK_FLOPS == 25
+    assert bench.alg_flops("euler_cromer", True, True) == 2 + 25 + 12
+    assert bench.alg_flops("leapfrog", True, True) == 2 * 2 + 25 + 12
+    assert bench.alg_flops("ruth4", True, True) == 4 * 2 + 3 * 25 + 12
+    assert bench.alg_flops("ruth4", False, False) == 4 * 2 + 3 * 25
+
+
+def test_algorithmic_flops_of_the_extensions():
+    ring = {"eta1": 0.05, "eta2": 2.0, "xi_x": 5.0, "xi_y": -3.0}
+    # widened drift 3 FMA (6 flops) per drift; a chromatic plane 41 flops
+    assert bench.alg_flops("ruth4", True, True, ring) == 4 * 6 + 3 * 25 + 2 * 41
+    dual = {"voltage2_V": 1.35e6}
+    # the second RF system adds a phase FMA, sine, subtract and FMA per kick; with eta1 =
+    # eta2 = 0 the drifts stay linear in the count (the kernel's expansion FMAs on zeros are
+    # not the method's work)
+    assert bench.alg_flops("ruth4", True, True, dual) == 4 * 2 + 3 * 25 + 3 * 25 + 12
+    # classic RK4: four right-hand sides of slippage (1 MUL, or 2 FMA + 1 MUL with the
+    # expansion), phase FMA, sine, subtract and multiply; stage arguments 10; weighted sums 12
+    assert bench.alg_flops("rk4", True, True) == 4 * (1 + 2 + 20 + 1 + 1) + 10 + 12 + 12
+    assert bench.alg_flops("rk4", True, True, dual) == 4 * (1 + 2 + 20 + 1 + 1) + 10 + 12 + 4 * 25 + 12
+    assert bench.alg_flops("rk4", False, False, {"eta1": 0.1}) == 4 * (5 + 2 + 20 + 1 + 1) + 10 + 12
+    # collective step: the slice index (subtract, multiply) and the kick's add
+    assert bench.COLLECTIVE_FLOPS == 3
+    assert bench.alg_flops("leapfrog", True, True) + bench.COLLECTIVE_FLOPS == 44
+
+
+def test_executed_flops_only_where_the_capture_applies():
+    wl = {"transverse": True, "stride": 1}
+    e = bench.executed_flops("f64", "ruth4", wl, 1e10)
+    assert abs(e["executed_flops_per_particle_turn_ncu"] - 86.08) < 0.01
+    assert abs(e["executed_tflops"] - 0.8608) < 1e-3
+    assert bench.executed_flops("f64", "leapfrog", wl, 1e10) == {}
+    assert bench.executed_flops("f64", "ruth4", dict(wl, ramp={"p0_end": 3e10}), 1e10) == {}
+    assert bench.executed_flops("f32cd", "ruth4", wl, 1e10) == {}
