@@ -85,10 +85,10 @@ WORKLOADS = {
     # the same batch in FP64 (per-job FP64 reference point; turns scaled down by 100)
     "batched_64_bunches_f64_lf": dict(kind="batched", nbunch=64, total=6e7, dtype="f64",
                                       scheme="leapfrog", stride=1, turn_scale=0.01),
-    # serving: Poisson arrivals at 200 jobs/s (first `count` of the trace), sizes
+    # serving: Poisson arrivals at 200 jobs/s (the first --serving-jobs of the trace), sizes
     # log-uniform 1e4-8e6, turns log-uniform 1e2-1e5, integrator uniform over three,
     # FP64 or FP32C 50/50, 150 GB admission budget; then the same jobs at ~70 % load
-    "serving_poisson_200hz": dict(kind="serving", count=48, rate_hz=200.0, budget=150e9),
+    "serving_poisson_200hz": dict(kind="serving", count=2000, rate_hz=200.0, budget=150e9),
     # precision sweep: 4e6 particles x 1e6 turns leap-frog FP32C (60 % core, 40 % halo to
     # 98 % of the separatrix) against FP64 on a 1e4-particle subsample
     "precision_sweep_4e6x1e6_lf": dict(kind="precision", n=4_000_000, turns=1_000_000,
@@ -273,16 +273,44 @@ def wake_table(wl):
     return np.exp(-m / (0.1 * ns)) * np.cos(m / (0.05 * ns))
 
 
-def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# The oracle's bounded sample of the paper-scale workload, the same in both arms: 1e4
+# particles x the workload's 1e4 turns x its three schemes (transverse planes and per-turn
+# moments included), i.e. 3e8 particle-turns per step.
+CPU_SAMPLE_PARTICLES = 10_000
+
+
+def cpu_baseline(wl, steps=1, warmup=0, n_sample=CPU_SAMPLE_PARTICLES, turns_sample=None,
+                 threads=0):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the workload
     (n_sample particles x turns_sample turns x every scheme, with the same transverse
-    planes and per-turn moments).  Returns (particle-turns/s, threads, sample text)."""
+    planes and per-turn moments); threads = 0: all cores.  Returns (particle-turns/s,
+    threads, sample text, per-step seconds)."""
     import oracle
     from paper_1610_05801_gb300 import synth
 
     turns = turns_sample or wl["turns"]
     ring = synth.ring(wl["voltage"], transverse=True, **(wl.get("ring") or {}))
     O = oracle.load()
+    O.set_num_threads(threads if threads > 0 else (os.cpu_count() or 1))
     d = O.derive(ring)
     b = synth.Bucket(k=d.k, A=d.A, etaC=d.etaC, Qs=d.Qs, betagamma=d.betagamma)
     z, dp, _ = synth.matched_bunch(1, n_sample, b)
@@ -313,11 +341,32 @@ def cpu_baseline(wl, steps=1, warmup=0, n_sample=20_000, turns_sample=None):
         dt = time.perf_counter() - t0
         if it >= warmup:
             times.append(dt)
+    used = O.num_threads()
+    O.set_num_threads(os.cpu_count() or 1)
     pt = n_sample * turns * len(wl["schemes"])
     sample = (f"{n_sample} particles x {turns} turns x {len(wl['schemes'])} schemes "
               f"({'+transverse' if wl['transverse'] else ''}{' +moments' if wl['stride'] else ''})"
               f" of the same workload, FP64 oracle, OpenMP over particles")
-    return pt / (sum(times) / len(times)), O.num_threads(), sample, times
+    return pt / (sum(times) / len(times)), used, sample, times
+
+
+def cpu_baseline_report(wl, n_sample=CPU_SAMPLE_PARTICLES):
+    """The CPU baseline the line carries: the oracle on all host cores (the value) and on one
+    core, on the workload's bounded sample, plus the small workload (1e3 particles x 1e3
+    leap-frog turns, FP64, no transverse planes, no monitor) both ways, and the CPU model."""
+    v, cores, sample, _ = cpu_baseline(wl, steps=2, warmup=1, n_sample=n_sample)
+    # one core on a tenth of the turns (the same particles and schemes): ~15 s of CPU work
+    v1, _, sample1, _ = cpu_baseline(wl, steps=1, n_sample=n_sample,
+                                     turns_sample=max(1, wl["turns"] // 10), threads=1)
+    small = dict(n=1000, turns=1000, schemes=("leapfrog",), voltage=2e6, transverse=False,
+                 stride=0)
+    s_all, c_all, _, _ = cpu_baseline(small, steps=5, warmup=1, n_sample=1000)
+    s_one, _, _, _ = cpu_baseline(small, steps=5, warmup=1, n_sample=1000, threads=1)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "single_thread": {"value": v1, "sample": sample1},
+            "small_workload_1e3x1e3_lf": {"all_cores": s_all, "single_thread": s_one,
+                                         "cores": c_all}}
 
 
 # ----------------------------------------------------------------------------------------
@@ -325,9 +374,8 @@ def run_reference(args, wl_name, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n_sample = 10_000
     v, cores, sample, times = cpu_baseline(wl, steps=args.steps, warmup=args.warmup,
-                                           n_sample=n_sample)
+                                           n_sample=args.cpu_sample)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
@@ -337,7 +385,7 @@ def run_reference(args, wl_name, wl):
                    "integrators": list(wl["schemes"]), "transverse": wl["transverse"],
                    "monitor_stride": wl["stride"], "step_sample": sample},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -491,7 +539,9 @@ def run_ours(args, wl_name, wl):
                    "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
-        "roofline": roof or (issue_roofline(kname) if dt != "f64" else None) or {
+        "roofline": roof or (issue_roofline(
+            kname, (dt, dom, bool(wl["transverse"]), bool(wl["stride"]), False),
+            n * tpl / dur_s, clk.get("sm_mhz")) if dt != "f64" else None) or {
             "bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
@@ -510,7 +560,7 @@ def run_ours(args, wl_name, wl):
         "per_scheme_ms": per_scheme_ms,
         "wall_s_timed_region": wall,
     }
-    return finish_line(line, args, wl, rank, R, dist)
+    return finish_line(line, args, wl, rank, R, dist, ws)
 
 
 # DRAM bytes per particle per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -546,16 +596,6 @@ def kernel_traffic(dt, scheme, wl, n):
     key = (dt, scheme, bool(wl["transverse"]), bool(wl["stride"]))
     b = NCU_TRAFFIC_BYTES_PER_PARTICLE.get(key)
     return None if b is None or wl.get("perturn") else b * n
-
-
-def issue_roofline(kname):
-    """The FP32-compensated kernels are bound by instruction issue (double-float arithmetic
-    on the FP32 and integer pipes), not by FP64 flops: the FP64 roofline does not apply, and
-    an issue-rate fraction needs ncu's instruction count (profiles/), so none is claimed."""
-    return {"bound": "issue", "kernel": kname, "achieved": None,
-            "peak": 152 * 4 * 2.07, "unit": "G warp-instructions/s", "frac": None,
-            "traffic": None,
-            "note": "double-float FP32 path, issue-bound; the FP64-flop roofline does not apply"}
 
 
 def per_turn_roofline(wl, per_scheme_ms, n, turns, dt):
@@ -616,14 +656,14 @@ def e2e_host(R, host, wl, args, dist, dev, ws):
     return n * turns * len(wl["schemes"]) * e2e_steps * ws / e2e_t, h2d, d2h, e2e_steps
 
 
-def finish_line(line, args, wl, rank, R, dist):
+def finish_line(line, args, wl, rank, R, dist, ws=1):
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, sample, _ = cpu_baseline(wl, n_sample=args.cpu_sample)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample}
+        line["cpu_baseline"] = cpu_baseline_report(wl, n_sample=args.cpu_sample)
+    R.close()
+    if rank == 0 and ws == 1 and not args.no_extras and args.workload == DEFAULT_WORKLOAD:
+        line.update(default_extras(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
-    R.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -641,21 +681,43 @@ def _clocked(fn):
     return v, clk
 
 
-def run_batched(args, wl_name, wl):
-    """64 uneven bunches: one graph-captured batch per step."""
-    import numpy as np
+# Executed warp-instructions per particle-turn of the FP32-compensated persistent kernels
+# (smsp__inst_executed.sum / particle-turns), from one ncu capture per kernel (launch list
+# and summaries in profiles/); keyed by (dtype, scheme, transverse, monitor, batched).
+NCU_WARP_INST_PER_PARTICLE_TURN = {}
+ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
+
+
+def issue_roofline(kname, key=None, pts=None, sm_mhz=None):
+    """Issue-rate roofline of an FP32-compensated kernel: executed warp-instructions per
+    particle-turn (ncu) x particle-turns per second / (SMs x 4 issue slots x SM clock).  The
+    double-float arithmetic runs on the FP32 and integer pipes at one instruction per issue
+    slot, so instruction issue, not FP64 flops, bounds it."""
+    clk = (sm_mhz or 2070.0) * 1e6
+    peak = 152 * ISSUE_PER_SM_PER_CLK * clk / 1e9
+    per = NCU_WARP_INST_PER_PARTICLE_TURN.get(key) if key else None
+    out = {"bound": "issue", "kernel": kname, "peak": peak, "unit": "G warp-instructions/s",
+           "peak_source": f"152 SMs x {ISSUE_PER_SM_PER_CLK} warp-instructions/clk x "
+                          f"{clk / 1e9:.3f} GHz (median SM clock sampled during the run)",
+           "traffic": None}
+    if per is None or pts is None:
+        out.update(achieved=None, frac=None,
+                   note="no ncu instruction count for this kernel variant")
+        return out
+    ach = per * pts / 1e9
+    out.update(achieved=ach, frac=ach / peak, warp_inst_per_particle_turn_ncu=per)
+    return out
+
+
+def batch_jobs(wl, dev):
+    """The batched workload's bunches as device buffers (seeded, matched to each voltage)."""
     import torch
 
-    from paper_1610_05801_gb300 import build as _build
     from paper_1610_05801_gb300 import phtl, synth
 
-    _build.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     specs = synth.batched_jobs(seed=3, nbunch=wl["nbunch"], total=wl["total"])
     scale = wl.get("turn_scale", 1.0)
     ring = synth.ring(2e6)
-    R = phtl.Ring(**ring)
     dt = wl["dtype"]
     jobs, keep = [], []
     for sp in specs:
@@ -674,11 +736,26 @@ def run_batched(args, wl_name, wl):
                                   integrator=wl["scheme"], dtype=dt, monitor=mon,
                                   stride=wl["stride"]))
         keep += [bz, bd, mon]
+    return specs, ring, jobs, keep
+
+
+def measure_batched(wl, steps, warmup):
+    """64 uneven bunches, one graph-captured batch per step: particle-turns/s over the timed
+    runs (CUDA events on the launching stream), with the clocks sampled meanwhile."""
+    import torch
+
+    from paper_1610_05801_gb300 import phtl
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs, ring, jobs, keep = batch_jobs(wl, dev)
+    R = phtl.Ring(**ring)
+    dt = wl["dtype"]
     t_create = time.perf_counter()
     B = phtl.Batch(R, jobs, use_graph=True)
     t_create = time.perf_counter() - t_create
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         B.run(stream)
     torch.cuda.synchronize()
     info = B.info()
@@ -686,7 +763,7 @@ def run_batched(args, wl_name, wl):
 
     def timed():
         evs = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             B.run(stream)
@@ -700,15 +777,14 @@ def run_batched(args, wl_name, wl):
     launches = R.stats().launches - st0.launches
     t = sum(ms) / 1e3
     slot = phtl.DTYPES[dt]
-    line = {
-        "metric": METRIC, "value": pt * args.steps / t, "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
-        "data": "synthetic (seeded uneven bunches)",
-        "config": {"workload": wl_name, "bunches": len(specs),
+    value = pt * steps / t
+    out = {
+        "value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+        "ms_per_step": sum(ms) / len(ms), "dtype": dt,
+        "config": {"bunches": len(specs),
                    "particles_total": int(sum(s["n"] for s in specs)),
                    "particle_turns_per_step": pt, "integrator": wl["scheme"],
-                   "monitor_stride": wl["stride"], "turn_scale": scale,
+                   "monitor_stride": wl["stride"], "turn_scale": wl.get("turn_scale", 1.0),
                    "block_threads": info.block_threads[slot],
                    "turns_per_launch": info.turns_per_launch[slot],
                    "launches_per_step": info.launches_per_run, "graph": bool(info.graph),
@@ -717,147 +793,245 @@ def run_batched(args, wl_name, wl):
                    "l2": "state ~1 GB (> L2) resident in HBM"},
         "gpu_launches": launches, "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    if dt != "f64":
+        out["roofline"] = issue_roofline(f"k_batched_f32c<{dt}, {wl['scheme']}, monitor>",
+                                         (dt, wl["scheme"], False, True, True), value,
+                                         clk.get("sm_mhz"))
     B.close()
     R.close()
+    del keep
+    return out
+
+
+def run_batched(args, wl_name, wl):
+    from paper_1610_05801_gb300 import build as _build
+
+    _build.build()
+    m = measure_batched(wl, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": m.pop("value"), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": m.pop("dtype"), "data": "synthetic (seeded uneven bunches)"}
+    m["config"]["workload"] = wl_name
+    line.update(m)
+    print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args, wl_name, wl):
-    """Serving: continuous batching of a Poisson trace of jobs; p50/p99 latency."""
+def _play(S, trace, hosts, times, dtype_override=None):
+    """Submit the trace's jobs at their arrival times (host buffers in, results in place)
+    and wait for all of them; returns the makespan in seconds."""
+    from paper_1610_05801_gb300 import phtl
+
+    t0 = time.perf_counter()
+    tickets = []
+    for j, (z, d), ta in zip(trace, hosts, times):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(S.submit(z, d, turns=j["turns"], integrator=j["integrator"],
+                                dtype=dtype_override if dtype_override else j["dtype"],
+                                out=[z, d, None, None, None, None]))
+    for t in tickets:
+        rc, st = S.wait(t, 3_600_000)
+        assert rc == phtl.OK and st.state == phtl.DONE, (rc, st.state, st.error)
+    return time.perf_counter() - t0
+
+
+def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=False):
+    """Serving: the first `count` arrivals of the 2000-arrival Poisson trace (seed 4), through
+    the continuous-batching loop with their own arithmetic (FP64 or FP32C); then the same
+    jobs every one FP32C through the loop (the batched FP32-compensated serving path), and
+    every one FP64 through the plain per-job path (one phtl_track_host call per job, in
+    arrival order) -- the comparison the throughput claim rests on."""
     import numpy as np
 
-    from paper_1610_05801_gb300 import build as _build
     from paper_1610_05801_gb300 import phtl, synth
 
-    _build.build()
-    trace = synth.serving_trace(seed=4, count=wl["count"], rate_hz=wl["rate_hz"])
+    trace = synth.serving_trace(seed=4, count=2000, rate_hz=rate_hz)[:count]
     ring = synth.ring(2e6)
     R = phtl.Ring(**ring)
     der = R.derived()
     b = synth.Bucket(k=der.k, A=der.A, etaC=der.etaC, Qs=der.Qs, betagamma=der.betagamma)
-    hosts = []
+    fp64 = []
     for j in trace:
         z, d, _ = synth.matched_bunch(j["seed"], j["n"], b)
-        if j["dtype"] == 0:
-            hosts.append((np.ascontiguousarray(z), np.ascontiguousarray(d)))
-        else:
-            hosts.append((phtl.split_f32c(z), phtl.split_f32c(d)))
+        fp64.append((np.ascontiguousarray(z), np.ascontiguousarray(d)))
 
-    def play(S, times):
-        t0 = time.perf_counter()
-        tickets = []
-        for j, (z, d), ta in zip(trace, hosts, times):
-            now = time.perf_counter() - t0
-            if ta > now:
-                time.sleep(ta - now)
-            tickets.append(S.submit(z, d, turns=j["turns"], integrator=j["integrator"],
-                                    dtype=j["dtype"], out=[z, d, None, None, None, None]))
-        for t in tickets:
-            rc, st = S.wait(t, 3_600_000)
-            assert rc == phtl.OK and st.state == phtl.DONE, (rc, st.state, st.error)
-        return time.perf_counter() - t0
+    def host(dt_of):
+        return [(z.copy(), d.copy()) if dt_of(j) == 0 else (phtl.split_f32c(z), phtl.split_f32c(d))
+                for j, (z, d) in zip(trace, fp64)]
 
-    S = phtl.Server(R, memory_budget_bytes=int(wl["budget"]), max_active=64)
-    (mk1, clk) = _clocked(lambda: play(S, [j["t_arrive_s"] for j in trace]))
-    s1 = S.stats()
-    S.stop()
-    cap = s1.throughput_pts
+    arrivals = [j["t_arrive_s"] for j in trace]
     work = sum(j["n"] * j["turns"] for j in trace)
-    # the same jobs at ~70 % of the measured capacity: mean gap = mean work / (0.7 cap)
-    gaps = np.array([j["t_arrive_s"] for j in trace])
-    gaps = np.diff(np.concatenate([[0.0], gaps]))
-    scale = (work / len(trace)) / (0.7 * cap) / max(gaps.mean(), 1e-12)
-    S2 = phtl.Server(R, memory_budget_bytes=int(wl["budget"]), max_active=64)
-    mk2 = play(S2, list(np.cumsum(gaps * scale)))
-    s2 = S2.stats()
-    S2.stop()
-    # the same trace two more ways: every job FP32CD through the serving loop (the batched
-    # FP32-compensated path), and every job FP64 through the plain per-job path (one
-    # phtl_track_host call per job, in arrival order)
-    fp64 = [(np.ascontiguousarray(z), np.ascontiguousarray(d)) if j["dtype"] == 0
-            else (phtl.join_f32c(z), phtl.join_f32c(d)) for j, (z, d) in zip(trace, hosts)]
-    hosts_cd = [(phtl.split_f32c(z), phtl.split_f32c(d)) for z, d in fp64]
-    S3 = phtl.Server(R, memory_budget_bytes=int(wl["budget"]), max_active=64)
-    t0 = time.perf_counter()
-    tk = []
-    for j, (z, d) in zip(trace, hosts_cd):
-        now = time.perf_counter() - t0
-        if j["t_arrive_s"] > now:
-            time.sleep(j["t_arrive_s"] - now)
-        tk.append(S3.submit(z, d, turns=j["turns"], integrator=j["integrator"], dtype="f32cd",
-                            out=[z, d, None, None, None, None]))
-    for t in tk:
-        rc, st = S3.wait(t, 3_600_000)
-        assert rc == phtl.OK and st.state == phtl.DONE
-    mk3 = time.perf_counter() - t0
-    s3 = S3.stats()
-    S3.stop()
-    lat = []
-    t0 = time.perf_counter()
-    for j, (z, d) in zip(trace, fp64):
-        now = time.perf_counter() - t0
-        if j["t_arrive_s"] > now:
-            time.sleep(j["t_arrive_s"] - now)
-        zz, dd = z.copy(), d.copy()
-        R.track_host(zz, dd, turns=j["turns"], integrator=j["integrator"], dtype="f64")
-        lat.append(time.perf_counter() - t0 - j["t_arrive_s"])
-    mk4 = time.perf_counter() - t0
-    lat = np.sort(np.array(lat))
-    line = {
-        "metric": METRIC, "value": s1.throughput_pts, "unit": UNIT, "n_gpus": 1, "steps": 1,
-        "warmup": 0, "ms_per_step": mk1 * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "mixed f64/f32c", "data": "synthetic Poisson trace",
-        "config": {"workload": wl_name, "jobs": len(trace), "offered_rate_hz": wl["rate_hz"],
-                   "particle_turns": work, "budget_bytes": wl["budget"], "max_active": 64,
-                   "f64_jobs": sum(1 for j in trace if j["dtype"] == 0)},
-        "latency": {"p50_s": s1.p50_latency_s, "p99_s": s1.p99_latency_s,
-                    "mean_s": s1.mean_latency_s, "makespan_s": mk1, "rounds": s1.rounds,
-                    "bytes_peak": s1.bytes_peak},
-        "at_70pct_load": {"rate_hz": len(trace) / float(np.sum(gaps * scale)),
-                          "throughput_pts": s2.throughput_pts, "p50_s": s2.p50_latency_s,
-                          "p99_s": s2.p99_latency_s, "makespan_s": mk2},
-        "all_jobs_f32cd_serving": {"throughput_pts": s3.throughput_pts, "p50_s": s3.p50_latency_s,
-                                   "p99_s": s3.p99_latency_s, "makespan_s": mk3,
-                                   "moment_accuracy": "bunch moments within 1e-8 of FP64 "
-                                   "after 1e6 turns (precision sweep)"},
-        "all_jobs_f64_plain_per_job": {"throughput_pts": work / mk4,
-                                       "p50_s": float(np.percentile(lat, 50)),
-                                       "p99_s": float(np.percentile(lat, 99)), "makespan_s": mk4,
-                                       "api": "one phtl_track_host call per job, arrival order"},
-        "gpu_launches": s1.launches, "clocks": clk,
+
+    def served(hosts, times, dtype_override=None):
+        S = phtl.Server(R, memory_budget_bytes=int(budget), max_active=64)
+        mk, clk = _clocked(lambda: _play(S, trace, hosts, times, dtype_override))
+        st = S.stats()
+        S.stop()
+        return mk, st, clk
+
+    mixed = host(lambda j: j["dtype"])
+    mk1, s1, clk = served(mixed, arrivals)
+    out = {
+        "jobs": len(trace), "trace": "first arrivals of the 2000-arrival Poisson trace (seed 4)",
+        "offered_rate_hz": rate_hz, "particle_turns": work, "budget_bytes": budget,
+        "max_active": 64, "f64_jobs": sum(1 for j in trace if j["dtype"] == 0),
+        "mixed": {"throughput_pts": s1.throughput_pts, "p50_s": s1.p50_latency_s,
+                  "p99_s": s1.p99_latency_s, "mean_s": s1.mean_latency_s, "makespan_s": mk1,
+                  "rounds": s1.rounds, "bytes_peak": s1.bytes_peak, "gpu_launches": s1.launches,
+                  "clocks": clk},
         "e2e": {"value": s1.throughput_pts, "unit": UNIT,
-                "h2d_bytes_per_step": int(sum(z.nbytes + d.nbytes for z, d in hosts)),
-                "d2h_bytes_per_step": int(sum(z.nbytes + d.nbytes for z, d in hosts)),
+                "h2d_bytes_per_step": int(sum(z.nbytes + d.nbytes for z, d in mixed)),
+                "d2h_bytes_per_step": int(sum(z.nbytes + d.nbytes for z, d in mixed)),
                 "api": "phtl_submit / phtl_wait on host buffers"},
     }
-    print(json.dumps(line), flush=True)
+    if load70:
+        cap = s1.throughput_pts
+        gaps = np.diff(np.concatenate([[0.0], np.array(arrivals)]))
+        scale = (work / len(trace)) / (0.7 * cap) / max(gaps.mean(), 1e-12)
+        mk2, s2, _ = served(host(lambda j: j["dtype"]), list(np.cumsum(gaps * scale)))
+        out["at_70pct_load"] = {"rate_hz": len(trace) / float(np.sum(gaps * scale)),
+                                "throughput_pts": s2.throughput_pts, "p50_s": s2.p50_latency_s,
+                                "p99_s": s2.p99_latency_s, "makespan_s": mk2}
+    mk3, s3, clk3 = served(host(lambda j: 1), arrivals, "f32c")
+    out["all_jobs_f32c_serving"] = {
+        "throughput_pts": s3.throughput_pts, "p50_s": s3.p50_latency_s,
+        "p99_s": s3.p99_latency_s, "makespan_s": mk3, "clocks": clk3,
+        "arithmetic": "PHTL_F32C: double-float state and sine, FP64 RF phase argument"}
+    if cd_leg:
+        mk5, s5, _ = served(host(lambda j: 1), arrivals, "f32cd")
+        out["all_jobs_f32cd_serving"] = {
+            "throughput_pts": s5.throughput_pts, "p50_s": s5.p50_latency_s,
+            "p99_s": s5.p99_latency_s, "makespan_s": mk5,
+            "arithmetic": "PHTL_F32CD: as F32C with the phase in double-float (a measured "
+                          "variant)"}
+
+    def per_job():
+        lat = []
+        t0 = time.perf_counter()
+        for j, (z, d) in zip(trace, fp64):
+            now = time.perf_counter() - t0
+            if j["t_arrive_s"] > now:
+                time.sleep(j["t_arrive_s"] - now)
+            zz, dd = z.copy(), d.copy()
+            R.track_host(zz, dd, turns=j["turns"], integrator=j["integrator"], dtype="f64")
+            lat.append(time.perf_counter() - t0 - j["t_arrive_s"])
+        return time.perf_counter() - t0, np.sort(np.array(lat))
+
+    (mk4, lat), clk4 = _clocked(per_job)
+    out["all_jobs_f64_plain_per_job"] = {
+        "throughput_pts": work / mk4, "p50_s": float(np.percentile(lat, 50)),
+        "p99_s": float(np.percentile(lat, 99)), "makespan_s": mk4, "clocks": clk4,
+        "api": "one phtl_track_host call per job, arrival order"}
+    out["f32c_served_over_f64_per_job"] = s3.throughput_pts / (work / mk4)
     R.close()
+    return out
+
+
+def run_serving(args, wl_name, wl):
+    from paper_1610_05801_gb300 import build as _build
+
+    _build.build()
+    m = measure_serving(args.serving_jobs or wl["count"], wl["rate_hz"], wl["budget"],
+                        load70=True, cd_leg=True)
+    line = {"metric": METRIC, "value": m["mixed"]["throughput_pts"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": m["mixed"]["makespan_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed f64/f32c", "data": "synthetic Poisson trace",
+            "config": {"workload": wl_name},
+            "latency": {"p50_s": m["mixed"]["p50_s"], "p99_s": m["mixed"]["p99_s"]},
+            "gpu_launches": m["mixed"]["gpu_launches"], "clocks": m["mixed"]["clocks"],
+            "e2e": m.pop("e2e"), "serving": m}
+    print(json.dumps(line), flush=True)
     return 0
 
 
-def run_precision(args, wl_name, wl):
-    """Precision sweep: FP32C vs FP64 moments after 1e6 turns (halo bunch), on the GPU; the FP64
-    oracle re-tracks the 1e4-particle subsample (with --oracle)."""
+def hamiltonian(der, z, dp):
+    """Smooth single-RF Hamiltonian eta C d^2 / 2 + (A / k)(1 - cos k z) (phi_s = 0)."""
+    import numpy as np
+
+    return 0.5 * der.etaC * dp * dp + (der.A / der.k) * (1.0 - np.cos(der.k * z))
+
+
+def moment_rel_errors(m, mref):
+    """Max over rows of the relative moment errors: means relative to the matching rms, rms
+    to itself, emittance relative to rms_z * rms_d (longitudinal plane)."""
+    import numpy as np
+
+    out = {}
+    for name, j, sc in (("mean_z", 0, 2), ("mean_dp", 1, 3), ("rms_z", 2, 2), ("rms_dp", 3, 3)):
+        out[name] = float(np.max(np.abs(m[:, j] - mref[:, j]) / np.abs(mref[:, sc])))
+    out["eps_z"] = float(np.max(np.abs(m[:, 4] - mref[:, 4]) / (mref[:, 2] * mref[:, 3])))
+    out["max"] = max(out.values())
+    return out
+
+
+class OracleThread(threading.Thread):
+    """The FP64 oracle tracking a sample on a background host thread (its C loops run
+    without the interpreter lock), with a set number of OpenMP threads."""
+
+    def __init__(self, der, scheme, z, dp, turns, stride, threads):
+        super().__init__(daemon=True)
+        self.args = (der, scheme, z, dp, turns, stride)
+        self.threads = threads
+        self.ref = None
+        self.secs = None
+        self.error = None
+
+    def run(self):
+        try:
+            import oracle
+
+            O = oracle.load()
+            O.set_num_threads(self.threads)
+            der, scheme, z, dp, turns, stride = self.args
+            t0 = time.perf_counter()
+            self.ref = O.track(der, scheme, z.copy(), dp.copy(), turns=turns, moments=True,
+                               stride=stride)
+            self.secs = time.perf_counter() - t0
+        except Exception as e:  # reported in the line, never swallowed silently
+            self.error = repr(e)
+
+
+def precision_setup(wl):
+    """The precision sweep's ring, bunch (4e6 particles: 60 % matched core, 40 % halo to 98 %
+    of the separatrix) and the oracle's constants; the subsample is a prefix."""
+    import oracle
+    from paper_1610_05801_gb300 import synth
+
+    ring = synth.ring(wl["voltage"])
+    O = oracle.load()
+    dO = O.derive(ring)
+    b = synth.Bucket(k=dO.k, A=dO.A, etaC=dO.etaC, Qs=dO.Qs, betagamma=dO.betagamma)
+    z, d = synth.halo_bunch(2, wl["n"], b)
+    return ring, dO, z, d
+
+
+def measure_precision_subsample(wl, ring, z, d, oracle_thread=None):
+    """The subsample tracked 1e6 leap-frog turns on the GPU in FP32C, FP32CD, FP32CS and FP64
+    (monitor every `stride` turns); moment errors against the FP64 oracle (its result from
+    oracle_thread) and against the FP64 GPU path, and the Hamiltonian drift of each."""
     import numpy as np
     import torch
 
-    from paper_1610_05801_gb300 import build as _build
-    from paper_1610_05801_gb300 import phtl, synth
+    from paper_1610_05801_gb300 import phtl
 
-    _build.build()
     dev = torch.device("cuda", 0)
-    ring = synth.ring(wl["voltage"])
     R = phtl.Ring(**ring)
     der = R.derived()
-    b = synth.Bucket(k=der.k, A=der.A, etaC=der.etaC, Qs=der.Qs, betagamma=der.betagamma)
-    z, d = synth.halo_bunch(2, wl["n"], b)
     turns, sub, stride = wl["turns"], wl["subsample"], wl["stride"]
     rows = turns // stride + 1
+    zs, ds = np.ascontiguousarray(z[:sub]), np.ascontiguousarray(d[:sub])
     res = {}
-    for dt in ("f32c", "f32cd", "f32cs"):
-        bz = torch.tensor(phtl.split_f32c(z), dtype=torch.float32, device=dev)
-        bd = torch.tensor(phtl.split_f32c(d), dtype=torch.float32, device=dev)
+    for dt in ("f64", "f32c", "f32cd", "f32cs"):
+        if dt == "f64":
+            bz = torch.tensor(zs, dtype=torch.float64, device=dev)
+            bd = torch.tensor(ds, dtype=torch.float64, device=dev)
+        else:
+            bz = torch.tensor(phtl.split_f32c(zs), dtype=torch.float32, device=dev)
+            bd = torch.tensor(phtl.split_f32c(ds), dtype=torch.float32, device=dev)
         mon = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
         R.set_monitor(mon, stride=stride)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -866,72 +1040,115 @@ def run_precision(args, wl_name, wl):
         e.record()
         torch.cuda.synchronize()
         R.set_monitor(None)
-        zf = phtl.join_f32c(bz.cpu().numpy())
-        df = phtl.join_f32c(bd.cpu().numpy())
-        res[dt] = dict(ms=a.elapsed_time(e), z=zf[:sub], d=df[:sub],
-                       mom_full=phtl.moments_from_sums(mon.cpu().numpy()))
-    # FP64 on the subsample (GPU), with per-row monitors of the subsample
-    bz = torch.tensor(z[:sub], dtype=torch.float64, device=dev)
-    bd = torch.tensor(d[:sub], dtype=torch.float64, device=dev)
-    mon = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
-    R.set_monitor(mon, stride=stride)
-    R.track(bz, bd, turns=turns, integrator="leapfrog", dtype="f64")
-    torch.cuda.synchronize()
-    R.set_monitor(None)
-    m64 = phtl.moments_from_sums(mon.cpu().numpy())
-    z64, d64 = bz.cpu().numpy(), bd.cpu().numpy()
-    out = {"metric": "moment relative error FP32C vs FP64 after 1e6 turns", "workload": wl_name,
-           "n": wl["n"], "turns": turns, "subsample": sub}
-    Hs = lambda zz, dd: 0.5 * der.etaC * dd * dd + (der.A / der.k) * (1 - np.cos(der.k * zz))
-    h0s, h64s = Hs(z[:sub], d[:sub]), Hs(z64, d64)
-    out["f64_hamiltonian_drift_median"] = float(np.median((h64s - h0s) / h0s))
-    out["f64_hamiltonian_drift_abs_max"] = float(np.max(np.abs(h64s - h0s) / h0s))
-    for dt in ("f32c", "f32cd", "f32cs"):
-        # the FP32 path's subsample, tracked separately so its moments can be compared row by row
-        sz = torch.tensor(phtl.split_f32c(z[:sub]), dtype=torch.float32, device=dev)
-        sd = torch.tensor(phtl.split_f32c(d[:sub]), dtype=torch.float32, device=dev)
-        ms = torch.zeros((rows, 16), dtype=torch.float64, device=dev)
-        R.set_monitor(ms, stride=stride)
-        R.track(sz, sd, turns=turns, integrator="leapfrog", dtype=dt)
-        torch.cuda.synchronize()
-        R.set_monitor(None)
-        m32 = phtl.moments_from_sums(ms.cpu().numpy())
-        assert np.array_equal(phtl.join_f32c(sz.cpu().numpy()), res[dt]["z"])  # same bits
-        rel = {}
-        for name, j, sc in (("mean_z", 0, 2), ("mean_dp", 1, 3), ("rms_z", 2, 2),
-                            ("rms_dp", 3, 3), ("eps_z", 4, 4)):
-            rel[name] = float(np.max(np.abs(m32[:, j] - m64[:, j]) / np.abs(m64[:, sc])))
-        # invariant of each particle after 1e6 turns, FP32 path vs FP64 path (the same map,
-        # so the scheme's own oscillation of H cancels), and the per-particle distance
-        H = lambda zz, dd: 0.5 * der.etaC * dd * dd + (der.A / der.k) * (1 - np.cos(der.k * zz))
-        h64, h32 = H(z64, d64), H(res[dt]["z"], res[dt]["d"])
-        h0 = H(z[:sub], d[:sub])
-        dh = np.abs(h32 - h64) / h64
-        zb, db = np.pi / der.k, der.bucket_half_height
-        dist = np.hypot((res[dt]["z"] - z64) / zb, (res[dt]["d"] - d64) / db)
-        out[dt] = {"pts_full": wl["n"] * turns / (res[dt]["ms"] / 1e3), "kernel_ms": res[dt]["ms"],
-                   "max_rel_moment_err": rel,
-                   "invariant_rel_diff_median": float(np.median(dh)),
-                   "invariant_rel_diff_max": float(np.max(dh)),
-                   # the Hamiltonian drift over the 1e6 turns, (H_end - H_start) / H_start per
-                   # particle of the subsample: the scheme's own O(K) variation of the smooth
-                   # H (the same for FP64, reported beside) plus the arithmetic's drift
-                   "hamiltonian_drift_median": float(np.median((h32 - h0) / h0)),
-                   "hamiltonian_drift_abs_max": float(np.max(np.abs(h32 - h0) / h0)),
-                   "particle_dist_median": float(np.median(dist)),
-                   "particle_dist_p90": float(np.quantile(dist, 0.9))}
-    if args.oracle:
-        import oracle
-
-        O = oracle.load()
-        t0 = time.perf_counter()
-        ref = O.track(O.derive(ring), "leapfrog", z[:sub], d[:sub], turns=turns, moments=True,
-                      stride=stride)
-        out["oracle_s"] = time.perf_counter() - t0
-        mo = ref[6]
-        out["f64_gpu_vs_oracle_max_rel_rms"] = float(np.max(np.abs(m64[:, 2:4] - mo[:, 2:4]) / mo[:, 2:4]))
-    print(json.dumps(out), flush=True)
+        zf = bz.cpu().numpy() if dt == "f64" else phtl.join_f32c(bz.cpu().numpy())
+        df = bd.cpu().numpy() if dt == "f64" else phtl.join_f32c(bd.cpu().numpy())
+        res[dt] = dict(ms=a.elapsed_time(e), z=zf, d=df,
+                       mom=phtl.moments_from_sums(mon.cpu().numpy()))
     R.close()
+    h0 = hamiltonian(der, zs, ds)
+    out = {"subsample": sub, "turns": turns, "monitor_stride": stride, "integrator": "leapfrog",
+           "bunch": f"{wl['n']} particles, 60 % matched core + 40 % halo to 98 % of the "
+                    f"separatrix, {wl['voltage'] / 1e6:g} MV; the subsample is its first {sub}"}
+    ref = None
+    if oracle_thread is not None:
+        oracle_thread.join()
+        if oracle_thread.error:
+            out["oracle_error"] = oracle_thread.error
+        else:
+            ref = oracle_thread.ref
+            out["oracle_s"] = oracle_thread.secs
+            out["oracle_threads"] = oracle_thread.threads
+            hr = hamiltonian(der, ref[0], ref[1])
+            out["oracle_hamiltonian_drift_median"] = float(np.median((hr - h0) / h0))
+            out["oracle_hamiltonian_drift_abs_max"] = float(np.max(np.abs(hr - h0) / h0))
+    for dt, r in res.items():
+        h = hamiltonian(der, r["z"], r["d"])
+        e = {"kernel_ms_subsample": r["ms"],
+             "hamiltonian_drift_median": float(np.median((h - h0) / h0)),
+             "hamiltonian_drift_abs_max": float(np.max(np.abs(h - h0) / h0))}
+        if ref is not None:
+            e["moment_rel_err_vs_oracle"] = moment_rel_errors(r["mom"], ref[6])
+            hr = hamiltonian(der, ref[0], ref[1])
+            e["hamiltonian_drift_diff_vs_oracle_abs_max"] = float(np.max(np.abs(h - hr) / h0))
+        if dt != "f64":
+            e["moment_rel_err_vs_f64_gpu"] = moment_rel_errors(r["mom"], res["f64"]["mom"])
+            if ref is not None:
+                e["meets_1e-4"] = e["moment_rel_err_vs_oracle"]["max"] <= 1e-4
+        out[dt] = e
+    return out
+
+
+def default_extras(args):
+    """The rest of the headline metric, measured after the FP64 line: the FP32-compensated
+    batch of 64 uneven bunches, the precision sweep's moment accuracy after 1e6 turns against
+    the FP64 oracle, and the serving trace with its p50/p99 and the FP32C-served against
+    FP64-per-job comparison.  The oracle's 1e6-turn run of the precision subsample goes on a
+    background host thread (two cores left to the GPU work) while the batch runs."""
+    import numpy as np
+
+    out = {}
+    pw = dict(WORKLOADS["precision_sweep_4e6x1e6_lf"])
+    pw["subsample"] = args.precision_subsample
+    ring, dO, z, d = precision_setup(pw)
+    sub = pw["subsample"]
+    othr = OracleThread(dO, "leapfrog", np.ascontiguousarray(z[:sub]),
+                        np.ascontiguousarray(d[:sub]), pw["turns"], pw["stride"],
+                        max(1, (os.cpu_count() or 4) - 2))
+    othr.start()
+    try:
+        out["batched_f32c_64_bunches"] = measure_batched(
+            WORKLOADS["batched_64_bunches_f32c_lf"], steps=1, warmup=1)
+    except Exception as e:
+        out["batched_f32c_64_bunches"] = {"error": repr(e)}
+    try:
+        out["precision_sweep"] = measure_precision_subsample(pw, ring, z, d, othr)
+    except Exception as e:
+        out["precision_sweep"] = {"error": repr(e)}
+    try:
+        out["serving"] = measure_serving(args.serving_jobs)
+    except Exception as e:
+        out["serving"] = {"error": repr(e)}
+    return out
+
+
+def run_precision(args, wl_name, wl):
+    """Precision sweep: FP32C / CD / CS at full size (4e6 x 1e6 turns) for throughput, and the
+    subsample against the FP64 oracle (with --oracle) and the FP64 GPU path."""
+    import numpy as np
+    import torch
+
+    from paper_1610_05801_gb300 import build as _build
+    from paper_1610_05801_gb300 import phtl
+
+    _build.build()
+    dev = torch.device("cuda", 0)
+    wl = dict(wl, subsample=args.precision_subsample)
+    ring, dO, z, d = precision_setup(wl)
+    othr = None
+    if args.oracle:
+        sub = wl["subsample"]
+        othr = OracleThread(dO, "leapfrog", np.ascontiguousarray(z[:sub]),
+                            np.ascontiguousarray(d[:sub]), wl["turns"], wl["stride"],
+                            max(1, (os.cpu_count() or 4) - 2))
+        othr.start()
+    R = phtl.Ring(**ring)
+    full = {}
+    for dt in ("f32c", "f32cd", "f32cs"):
+        bz = torch.tensor(phtl.split_f32c(z), dtype=torch.float32, device=dev)
+        bd = torch.tensor(phtl.split_f32c(d), dtype=torch.float32, device=dev)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.track(bz, bd, turns=wl["turns"], integrator="leapfrog", dtype=dt)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        full[dt] = {"pts": wl["n"] * wl["turns"] / (ms / 1e3), "kernel_ms": ms}
+        del bz, bd
+    R.close()
+    out = {"metric": "moment relative error FP32C vs FP64 after 1e6 turns", "workload": wl_name,
+           "n": wl["n"], "turns": wl["turns"], "full_size_longitudinal": full}
+    out.update(measure_precision_subsample(wl, ring, z, d, othr))
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -942,8 +1159,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample", type=int, default=20_000,
-                    help="particles in the oracle's bounded CPU-baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PARTICLES,
+                    help="particles in the oracle's bounded CPU-baseline sample (both arms)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle", action="store_true",
                     help="precision sweep: also re-track the subsample with the FP64 oracle")
@@ -957,6 +1174,13 @@ def main(argv=None):
     ap.add_argument("--no-transverse", action="store_true")
     ap.add_argument("--perturn", action="store_true", help="one launch per turn (HBM-bound variant)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: print the FP64 line without the FP32C batch, "
+                         "precision-sweep and serving keys")
+    ap.add_argument("--serving-jobs", type=int, default=64,
+                    help="serving: the first N arrivals of the 2000-arrival trace")
+    ap.add_argument("--precision-subsample", type=int, default=10_000,
+                    help="precision sweep: particles compared with the FP64 oracle")
     ap.add_argument("--block", type=int, help="threads per block (default: the library's)")
     ap.add_argument("--turns-per-launch", type=int, help="turns per launch (default: automatic)")
     args = ap.parse_args(argv)

@@ -67,6 +67,8 @@ extern "C" {
 #define PHTL_E_BADHANDLE (-7) /* null, destroyed or foreign handle / unknown ticket   */
 #define PHTL_E_NODEVICE (-8)  /* no CUDA device, or not an sm_103 device              */
 #define PHTL_E_TOOBIG (-9)    /* more jobs than phtl_batch_run_noalloc's fixed table   */
+#define PHTL_E_CAPTURE (-10)  /* the stream is capturing a CUDA graph and the call      */
+                              /* cannot be recorded into one                          */
 
 /* ---- enums ------------------------------------------------------------------------- */
 /* PHTL_RK4: classic 4th-order Runge-Kutta on the smooth motion per turn, dz/dn = -eta(d) C d,
@@ -404,12 +406,16 @@ int phtl_batch_destroy(phtl_batch* b);
  * the library's default turns per launch; no autotuner probe and no CUDA graph.
  * jobs: as for phtl_batch_create (caller-owned device buffers, updated in place).
  * The call is stream-ordered on cuda_stream.  The first call on a device looks up the
- * array's device address (one-time set-up); make that first call before any stream
- * capture.  Every call shares the array and it keeps the last call's contents; each call
- * rewrites all entries it uses.  Calls that can overlap on the GPU (for example on two
- * streams with no ordering between them) race on the array: order them on one stream.
- * Errors: PHTL_E_TOOBIG (njobs > PHTL_NOALLOC_MAX_JOBS), PHTL_E_BADHANDLE,
- * PHTL_E_INVALID, PHTL_E_UNSTABLE, PHTL_E_NODEVICE, PHTL_E_CUDA.                        */
+ * array's device address (one-time set-up).  The table is copied from host memory that
+ * lives only during the call, so the call cannot be recorded into a CUDA graph: on a
+ * stream that is capturing it returns PHTL_E_CAPTURE and enqueues nothing.  Every call
+ * shares the array and it keeps the last call's contents; each call rewrites all entries
+ * it uses.  Calls that can overlap on the GPU (for example on two streams with no
+ * ordering between them) race on the array: order them on one stream.  Every check runs
+ * before the first enqueue, so a rejected call leaves the jobs untouched; only a CUDA
+ * error during the enqueue (PHTL_E_CUDA) can leave some arithmetic groups advanced.
+ * Errors: PHTL_E_TOOBIG (njobs > PHTL_NOALLOC_MAX_JOBS), PHTL_E_CAPTURE,
+ * PHTL_E_BADHANDLE, PHTL_E_INVALID, PHTL_E_UNSTABLE, PHTL_E_NODEVICE, PHTL_E_CUDA.      */
 int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int32_t njobs,
                            void* cuda_stream);
 

@@ -125,6 +125,8 @@ class Oracle:
         L.ref_track_collective.restype = C.c_int
         L.ref_num_threads.argtypes = []
         L.ref_num_threads.restype = C.c_int
+        L.ref_set_num_threads.argtypes = [C.c_int]
+        L.ref_set_num_threads.restype = C.c_int
         self.lib = L
         self.path = path
 
@@ -251,6 +253,11 @@ class Oracle:
 
     def num_threads(self) -> int:
         return int(self.lib.ref_num_threads())
+
+    def set_num_threads(self, n: int) -> int:
+        """Threads of this OS thread's later oracle calls (OpenMP); returns the count in
+        effect.  Used to time the oracle on one core and on all cores."""
+        return int(self.lib.ref_set_num_threads(int(n)))
 
 
 def load() -> Oracle:

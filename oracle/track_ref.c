@@ -701,3 +701,16 @@ int ref_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the calling thread's later parallel loops (n >= 1), for timing the oracle
+ * single-threaded and on all cores; returns the count now in effect.  Test
+ * infrastructure only: it changes no arithmetic. */
+int ref_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return ref_num_threads();
+}

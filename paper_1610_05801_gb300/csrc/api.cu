@@ -479,6 +479,7 @@ const char* phtl_strerror(int code)
         case PHTL_E_BADHANDLE: return "bad handle or ticket";
         case PHTL_E_NODEVICE: return "no sm_103 CUDA device";
         case PHTL_E_TOOBIG: return "more jobs than the fixed table of the no-allocation batch run";
+        case PHTL_E_CAPTURE: return "the stream is capturing a CUDA graph; this call cannot be captured";
         default: return "unknown error code";
     }
 }

@@ -84,39 +84,63 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
     }
     int rc = ensure_device(h);
     if (rc != PHTL_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // The table is copied from this call's stack frame: inside a stream capture that copy
+    // would become a graph node reading a dead frame at replay, so a capturing stream is
+    // refused before anything is enqueued.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return PHTL_E_CAPTURE;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return PHTL_E_CAPTURE;
     JobDesc* table = nullptr;
     rc = noalloc_table(h->device, &table);
     if (rc != PHTL_OK) return rc;
     if (njobs == 0) return PHTL_OK;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
-    // host copy of the table: on the stack, no allocation
+    // Pass 1 (host only): the table of every arithmetic group and its launch shape, with
+    // every check, so that a rejected call enqueues nothing.  On the stack, no allocation.
+    struct Group {
+        int32_t dtype, first, cnt;
+        int32_t block;
+        bool mon;
+        MapConsts mc;
+        int64_t T, tiles;
+    };
     JobDesc host[PHTL_NOALLOC_MAX_JOBS];
     int32_t order[PHTL_NOALLOC_MAX_JOBS];
-    int32_t used = 0;
+    Group groups[4];
+    int32_t ngroups = 0, used = 0;
     for (int dt = PHTL_F64; dt <= PHTL_F32CS; ++dt) {
         int32_t cnt = 0;
+        int32_t* ord = order + used;
         for (int32_t i = 0; i < njobs; ++i)
-            if (jobs[i].dtype == dt) order[cnt++] = i;
+            if (jobs[i].dtype == dt) ord[cnt++] = i;
         if (cnt == 0) continue;
-        std::stable_sort(order, order + cnt,
+        std::stable_sort(ord, ord + cnt,
                          [&](int32_t a, int32_t b) { return jobs[a].turns > jobs[b].turns; });
         int64_t active = 0;
         bool mon = false, rk4 = false;
         for (int32_t k = 0; k < cnt; ++k) {
-            active += jobs[order[k]].n;
-            mon = mon || jobs[order[k]].mon_rows != nullptr;
-            rk4 = rk4 || jobs[order[k]].integrator == PHTL_RK4;
+            active += jobs[ord[k]].n;
+            mon = mon || jobs[ord[k]].mon_rows != nullptr;
+            rk4 = rk4 || jobs[ord[k]].integrator == PHTL_RK4;
         }
-        const MapConsts mc = batch_consts(h, rk4);
-        const int block = h->block > 0 ? h->block : 128;
-        if (occupancy_batched(dt, mon, block, mc.general != 0) <= 0) return PHTL_E_INVALID;
-        const int64_t T = h->tpl > 0 ? h->tpl : auto_turns_per_launch(dt, jobs[order[0]].integrator, active);
-        const int64_t per_tile = static_cast<int64_t>(block) * particles_per_thread(dt);
+        Group& g = groups[ngroups++];
+        g.dtype = dt;
+        g.first = used;
+        g.cnt = cnt;
+        g.mon = mon;
+        g.mc = batch_consts(h, rk4);
+        g.block = h->block > 0 ? h->block : 128;
+        if (occupancy_batched(dt, mon, g.block, g.mc.general != 0) <= 0) return PHTL_E_INVALID;
+        g.T = h->tpl > 0 ? h->tpl : auto_turns_per_launch(dt, jobs[ord[0]].integrator, active);
+        const int64_t per_tile = static_cast<int64_t>(g.block) * particles_per_thread(dt);
         JobDesc* G = host + used;
         int64_t tiles = 0;
         for (int32_t k = 0; k < cnt; ++k) {
-            const phtl_job& U = jobs[order[k]];
+            const phtl_job& U = jobs[ord[k]];
             JobDesc& J = G[k];
             std::memset(&J, 0, sizeof(J));
             bool vec = true;
@@ -134,36 +158,44 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
             J.tile_begin = tiles;
             job_weights(h, U.integrator, U.voltage_V, J);
             tiles += (U.n + per_tile - 1) / per_tile;
-            if (U.mon_rows) {
-                rc = cuda_rc(cudaMemsetAsync(U.mon_rows, 0,
-                                             static_cast<size_t>(U.turns / U.mon_stride + 1) * PHTL_MON_FIELDS * 8, s));
-                if (rc != PHTL_OK) return rc;
-            }
         }
         if (tiles > (int64_t(1) << 31) - 1) return PHTL_E_INVALID;
-        // the table entries of this group, then its chunk launches (stream-ordered)
-        rc = cuda_rc(cudaMemcpyAsync(table + used, G, sizeof(JobDesc) * cnt, cudaMemcpyHostToDevice, s));
-        if (rc != PHTL_OK) return rc;
+        g.tiles = tiles;
+        used += cnt;
+    }
+
+    // Pass 2: the whole table in one copy, then per group its monitor clears and its chunk
+    // launches (all stream-ordered).  A CUDA error here can leave earlier groups enqueued.
+    rc = cuda_rc(cudaMemcpyAsync(table, host, sizeof(JobDesc) * used, cudaMemcpyHostToDevice, s));
+    if (rc != PHTL_OK) return rc;
+    for (int32_t gi = 0; gi < ngroups; ++gi) {
+        const Group& g = groups[gi];
+        const JobDesc* G = host + g.first;
+        for (int32_t k = 0; k < g.cnt; ++k) {
+            if (!G[k].mon) continue;
+            rc = cuda_rc(cudaMemsetAsync(G[k].mon, 0,
+                                         static_cast<size_t>(G[k].turns / G[k].stride + 1) * PHTL_MON_FIELDS * 8, s));
+            if (rc != PHTL_OK) return rc;
+        }
         const int64_t max_turns = G[0].turns;
         int64_t t0 = 0, nl = 0;
         do {
-            int32_t k = cnt;
+            int32_t k = g.cnt;
             if (t0 > 0) {
                 k = 0;
-                while (k < cnt && G[k].turns > t0) ++k;
+                while (k < g.cnt && G[k].turns > t0) ++k;
             }
-            const int64_t grid = k == cnt ? tiles : G[k].tile_begin;
-            const int32_t nt = static_cast<int32_t>(std::min<int64_t>(T, std::max<int64_t>(max_turns - t0, 0)));
+            const int64_t grid = k == g.cnt ? g.tiles : G[k].tile_begin;
+            const int32_t nt = static_cast<int32_t>(std::min<int64_t>(g.T, std::max<int64_t>(max_turns - t0, 0)));
             if (grid > 0) {
-                rc = cuda_rc(launch_batched(table + used, cnt, mc, dt, mon, t0, nt,
-                                            static_cast<int>(grid), block, s));
+                rc = cuda_rc(launch_batched(table + g.first, g.cnt, g.mc, g.dtype, g.mon, t0, nt,
+                                            static_cast<int>(grid), g.block, s));
                 if (rc != PHTL_OK) return rc;
                 ++nl;
             }
-            t0 += T;
+            t0 += g.T;
         } while (t0 < max_turns);
         h->stats.launches += nl;
-        used += cnt;
     }
     for (int32_t i = 0; i < njobs; ++i) h->stats.particle_turns += jobs[i].n * jobs[i].turns;
     ++h->stats.calls;

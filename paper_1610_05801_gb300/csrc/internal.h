@@ -171,6 +171,9 @@ struct JobDesc {
     int32_t vec;         // nonzero: 16-byte aligned buffers (128-bit loads)
     int32_t pad_;
 };
+// 6 + 1 pointers, 5 int64, 10 doubles, 20 floats, 3 int32: the no-allocation batch run's
+// fixed table is PHTL_NOALLOC_MAX_JOBS of these (69,632 bytes per GPU).
+static_assert(sizeof(JobDesc) == 272, "JobDesc layout changed: update the table sizes");
 
 // Split the job's FP64 drift / kick weights into FP32 hi + lo pairs.
 inline void fill_float_weights(JobDesc& J)

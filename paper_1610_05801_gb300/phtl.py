@@ -21,6 +21,7 @@ OK = 0
 E_INVALID, E_UNSTABLE, E_NOMEM, E_CUDA, E_TIMEOUT, E_CANCELLED, E_BADHANDLE, E_NODEVICE = (
     -1, -2, -3, -4, -5, -6, -7, -8)
 E_TOOBIG = -9
+E_CAPTURE = -10
 NOALLOC_MAX_JOBS = 256
 EULER_CROMER, LEAPFROG, RUTH4, RK4 = 0, 1, 2, 3
 F64, F32C, F32CD, F32CS = 0, 1, 2, 3

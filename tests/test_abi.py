@@ -38,8 +38,8 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_version_and_strerror():
     lib = phtl.load()
     assert b"sm_103a" in lib.phtl_version()
-    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8):
-        assert lib.phtl_strerror(code)
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10):
+        assert lib.phtl_strerror(code) != b"unknown error code", code
     assert lib.phtl_strerror(-99) == b"unknown error code"
 
 

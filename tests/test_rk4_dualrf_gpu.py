@@ -200,6 +200,11 @@ def test_rk4_serving_equals_alone():
         assert np.array_equal(u.cpu().numpy(), v)
     for u, v in zip(alone_b, host_b):
         assert np.array_equal(u.cpu().numpy(), v)
+    # and both served jobs against the oracle directly
+    ref_a, _ = run_ref(inp, "rk4", 400)
+    ref_b, _ = run_ref(inp, "ruth4", 250)
+    assert errors(inp, host_a, ref_a) < TOL["f64"][0], errors(inp, host_a, ref_a)
+    assert errors(inp, host_b, ref_b) < TOL["f64"][0], errors(inp, host_b, ref_b)
     R.close()
 
 

@@ -3,18 +3,23 @@
 Result independence: jobs of different sizes, turn counts, voltages, integrators and
 arithmetic submitted together (so they share scheduling rounds and launches) give, each,
 bitwise the same particles as the same job tracked alone with phtl_track, and monitor
-moments equal to FP64 rounding.  Also: resume from a resident state, cancellation at a
+moments equal to FP64 rounding.  Parity: every served job of the mix also agrees with the
+FP64 oracle on the same inputs, within the parity tolerances of the single-bunch path
+(FP64: per particle <= 1e-10, moments <= 1e-9; FP32C / FP32CD: per particle <= 1e-8 with
+median <= 1e-10, moments <= 1e-6).  Also: resume from a resident state, cancellation at a
 round boundary, latency statistics.
 """
 import numpy as np
 import pytest
 
 import helpers
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_1610_05801_gb300 import phtl, synth  # noqa: E402
+from test_parity_gpu import moment_errors  # noqa: E402
 
 DEV = "cuda:0"
 MIX = [  # n, turns, voltage, integrator, dtype, monitor stride, transverse
@@ -56,6 +61,29 @@ def alone(ring, arrays, turns, V, integ, dt, stride):
     return res, m
 
 
+def oracle_check(spec, seed, out, mon):
+    """A served job's particles and monitor moments against the FP64 oracle tracking the
+    same initial values (the FP32 layouts are compared through hi + comp)."""
+    n, turns, V, integ, dt, stride, tr = spec
+    inp = helpers.inputs(n, seed=seed, voltage=V, transverse=True)
+    keys = ("z", "dp", "x", "xp", "y", "yp") if tr else ("z", "dp")
+    args = [inp[k] for k in keys]
+    ref = oracle.track(inp["d"], integ, *args, turns=turns, moments=bool(stride),
+                       stride=stride or 1)
+    got = [None if a is None else (a if dt == "f64" else phtl.join_f32c(a)) for a in out]
+    refp = [ref[i] if i < len(keys) else None for i in range(6)]
+    err = helpers.rel_errors(inp["d"], refp, got, inp["z"], inp["dp"])
+    if dt == "f64":
+        assert np.max(err) < 1e-10, (spec, np.max(err))
+    else:
+        assert np.max(err) < 1e-8, (spec, np.max(err))
+        assert np.median(err) < 1e-10, (spec, np.median(err))
+    if stride and n > 1:
+        mg = phtl.moments_from_sums(mon)
+        tol = 1e-9 if dt == "f64" else 1e-6
+        assert moment_errors(inp["d"], mg, ref[6], with_emittance=n > 2) < tol, spec
+
+
 def test_results_identical_alone_and_in_the_mix():
     ring = synth.ring(2e6, transverse=True)
     R = phtl.Ring(**ring)
@@ -78,6 +106,10 @@ def test_results_identical_alone_and_in_the_mix():
         if stride:
             ma, mb = phtl.moments_from_sums(mon), phtl.moments_from_sums(mref)
             assert np.allclose(ma, mb, rtol=1e-11, atol=1e-300), (n, integ, dt)
+    # every served job against the oracle (the chain served == alone == oracle, checked
+    # directly rather than through the single-bunch parity tests)
+    for i, ((t, arrs, out, mon), spec) in enumerate(zip(subs, MIX)):
+        oracle_check(spec, 300 + i, out, mon)
     s = S.stats()
     assert s.completed == len(MIX) and s.failed == 0 and s.bytes_in_use == 0
     assert 0 < s.p50_latency_s <= s.p99_latency_s

@@ -170,4 +170,6 @@ def test_widened_serving_equals_alone():
         S.stop()
     for u, v in zip(alone, host):
         assert np.array_equal(u.cpu().numpy(), v)
+    ref, _ = run_ref(inp, "ruth4", 400)  # the served job against the oracle directly
+    assert errors(inp, host, ref) < TOL["f64"][0], errors(inp, host, ref)
     R.close()
