@@ -512,9 +512,9 @@ def run_ours(args, wl_name, wl):
     achieved = flops / dur_s / 1e12
 
     if args.no_e2e or wl.get("perturn") or wl.get("ramp") or wl.get("wake"):
-        e2e_value, h2d, d2h, e2e_steps = None, 0, 0, 0
+        e2e_value, h2d, d2h, e2e_steps, phases = None, 0, 0, 0, None
     else:
-        e2e_value, h2d, d2h, e2e_steps = e2e_host(R, host, wl, args, dist, dev, ws)
+        e2e_value, h2d, d2h, e2e_steps, phases = e2e_host(R, host, wl, args, dist, dev, ws)
     roof = per_turn_roofline(wl, per_scheme_ms, n, turns, dt) if wl.get("perturn") else None
     kname = (f"k_track_{'f64' if dt == 'f64' else 'f32c'}<{dom}"
              f"{', transverse' if wl['transverse'] else ''}{', monitor' if wl['stride'] else ''}"
@@ -541,21 +541,13 @@ def run_ours(args, wl_name, wl):
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
         "roofline": roof or (issue_roofline(
             kname, (dt, dom, bool(wl["transverse"]), bool(wl["stride"]), False),
-            n * tpl / dur_s, clk.get("sm_mhz")) if dt != "f64" else None) or {
-            "bound": "alu", "kernel": kname,
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": kernel_traffic(dt, dom, wl, n),
-            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
-                           "counts and max clock); DFMA rate confirmed by a microbenchmark",
-            "alg_flops_per_particle_turn": flops_pt,
-            "moment_flops_per_particle_turn_fp32_pipe": MONITOR_FLOPS if wl["stride"] else 0,
-            "launch_ms": dur_s * 1e3, "turns_per_launch": tpl,
-            **executed_flops(dt, dom, wl, n * tpl / dur_s)},
+            n * tpl / dur_s, clk.get("sm_mhz")) if dt != "f64" else None) or fp64_roofline(
+            kname, dt, dom, wl, n, tpl, dur_s, flops_pt, achieved),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "api": "phtl_track_host (pinned host buffers; alloc, H2D, kernels, D2H, free)"},
+                "api": "phtl_track_host (pinned host buffers; alloc, H2D, kernels, D2H, free)",
+                "last_call_phases_ms": phases},
         "clocks": clk,
         "per_scheme_ms": per_scheme_ms,
         "wall_s_timed_region": wall,
@@ -590,6 +582,40 @@ def executed_flops(dt, scheme, wl, particle_turns_per_s):
     tf = f * particle_turns_per_s / 1e12
     return {"executed_flops_per_particle_turn_ncu": f, "executed_tflops": tf,
             "executed_frac": tf / FP64_PEAK_TFLOPS}
+
+
+def fp64_roofline(kname, dt, dom, wl, n, tpl, dur_s, flops_pt, achieved_alg):
+    """FP64-pipe roofline of the dominant persistent kernel.  The cost of an FP64 sine is
+    implementation-defined, so the fraction of the FP64 peak is taken from the FP64 flops the
+    kernel executes (ncu: 2 x DFMA + DMUL + DADD per particle-turn, stored per kernel variant)
+    at the live launch duration; where no capture of the variant exists, from the
+    algorithmic count with each sine costed at SINE_FLOPS.  Both counts are reported, and
+    the sine-free count of the method's drifts, kick multiply-adds and transverse push."""
+    exe = executed_flops(dt, dom, wl, n * tpl / dur_s)
+    base = {"bound": "alu", "kernel": kname, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "traffic": kernel_traffic(dt, dom, wl, n),
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe unit "
+                           "counts and max clock); DFMA rate confirmed by a microbenchmark",
+            "launch_ms": dur_s * 1e3, "turns_per_launch": tpl,
+            "alg_flops_per_particle_turn": flops_pt,
+            "alg_sine_flops": SINE_FLOPS, "alg_achieved": achieved_alg,
+            "alg_frac": achieved_alg / FP64_PEAK_TFLOPS,
+            "moment_flops_per_particle_turn_fp32_pipe": MONITOR_FLOPS if wl["stride"] else 0}
+    nosine = flops_pt - SINE_FLOPS * KICKS.get(dom, 0) * (
+        1 + (1 if (wl.get("ring") or {}).get("voltage2_V") else 0))
+    base["alg_flops_per_particle_turn_without_sines"] = nosine
+    base["alg_frac_without_sines"] = nosine * n * tpl / dur_s / 1e12 / FP64_PEAK_TFLOPS
+    if exe:
+        base.update(exe)
+        base.update(achieved=exe["executed_tflops"], frac=exe["executed_frac"],
+                    basis="ncu-executed FP64 flops per particle-turn (2 DFMA + DMUL + DADD) "
+                          "x live particle-turns/s; alg_frac counts each sine as "
+                          f"{SINE_FLOPS} flops")
+    else:
+        base.update(achieved=achieved_alg, frac=achieved_alg / FP64_PEAK_TFLOPS,
+                    basis=f"algorithmic FP64 flops, each sine costed at {SINE_FLOPS} flops "
+                          "(no ncu count of this kernel variant stored)")
+    return base
 
 
 def kernel_traffic(dt, scheme, wl, n):
@@ -653,7 +679,8 @@ def e2e_host(R, host, wl, args, dist, dev, ws):
     nb = sum(h.numel() * h.element_size() for h in hbufs if h is not None)
     h2d = nb * len(wl["schemes"])
     d2h = (nb + (hmon.numel() * 8 if wl["stride"] else 0)) * len(wl["schemes"])
-    return n * turns * len(wl["schemes"]) * e2e_steps * ws / e2e_t, h2d, d2h, e2e_steps
+    return (n * turns * len(wl["schemes"]) * e2e_steps * ws / e2e_t, h2d, d2h, e2e_steps,
+            R.phase_times())
 
 
 def finish_line(line, args, wl, rank, R, dist, ws=1):
@@ -682,9 +709,18 @@ def _clocked(fn):
 
 
 # Executed warp-instructions per particle-turn of the FP32-compensated persistent kernels
-# (smsp__inst_executed.sum / particle-turns), from one ncu capture per kernel (launch list
-# and summaries in profiles/); keyed by (dtype, scheme, transverse, monitor, batched).
-NCU_WARP_INST_PER_PARTICLE_TURN = {}
+# (sm__inst_executed.sum / particle-turns of the launch), from one ncu capture per kernel:
+# 2e6 particles x 200 turns per launch, transverse planes, stride-1 monitor (summary:
+# profiles/k_track_f32c_instruction_counts_2e6x200.md); keyed by (dtype, scheme,
+# transverse, monitor, batched).
+NCU_WARP_INST_PER_PARTICLE_TURN = {
+    ("f32c", "leapfrog", True, True, False): 4790748955 / (2e6 * 200),
+    ("f32c", "ruth4", True, True, False): 10788660484 / (2e6 * 200),
+    ("f32cd", "leapfrog", True, True, False): 3924877111 / (2e6 * 200),
+    ("f32cd", "ruth4", True, True, False): 8228979485 / (2e6 * 200),
+    ("f32cs", "leapfrog", True, True, False): 2326276064 / (2e6 * 200),
+    ("f32cs", "ruth4", True, True, False): 3477286084 / (2e6 * 200),
+}
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 
 
@@ -1177,6 +1213,10 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: print the FP64 line without the FP32C batch, "
                          "precision-sweep and serving keys")
+    ap.add_argument("--batch-total", type=float,
+                    help="batched workload: total particles (profiling captures; default 6e7)")
+    ap.add_argument("--turn-scale", type=float,
+                    help="batched workload: scale of every bunch's turns (profiling captures)")
     ap.add_argument("--serving-jobs", type=int, default=64,
                     help="serving: the first N arrivals of the 2000-arrival trace")
     ap.add_argument("--precision-subsample", type=int, default=10_000,
@@ -1197,6 +1237,11 @@ def main(argv=None):
         wl["perturn"] = args.perturn
         wl["block"] = args.block or 0
         wl["tpl"] = args.turns_per_launch or 0
+    if kind == "batched":
+        if args.batch_total:
+            wl["total"] = args.batch_total
+        if args.turn_scale:
+            wl["turn_scale"] = args.turn_scale
     if args.impl == "reference":
         if kind != "single":
             print(json.dumps({"impl": "reference", "unavailable":

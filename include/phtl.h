@@ -29,6 +29,10 @@
  * (phtl_set_programme) and a collective step of slicing, wake and space-charge kick
  * (phtl_set_wake), each stated where it is declared.
  *
+ * Logging: with the environment variable PHTL_LOG set to 1 (or higher) when the library is
+ * first used, each tracking call, batch and serving event prints one line to stderr
+ * ("phtl: ..."): the entry point, sizes, integrator, arithmetic and launch shape.
+ *
  * Conventions for every entry point:
  *   - Return value: PHTL_OK (0) or a negative PHTL_E_* code.  No C++ exception
  *     crosses this boundary.  phtl_strerror() names a code.
@@ -204,6 +208,25 @@ int phtl_set_tuning(phtl_handle* h, int32_t block_threads, int64_t turns_per_lau
 int phtl_track(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
                int64_t n, int64_t turns, int integrator, int dtype, void* cuda_stream);
 
+/* Stop the persistent tracking calls already enqueued on this handle (phtl_track,
+ * phtl_track_programme and the kernels of phtl_track_host), from any host thread, at the
+ * next boundary between their launches.  Each launch is preceded on the stream by a
+ * one-thread gate kernel that reads the handle's cancel word (host-mapped memory) and lets
+ * the launch run whole or skip it, so the particles are left exactly as after the last
+ * launch that ran: bitwise the state of the same call with fewer turns, its later monitor
+ * rows zero.  Calls enqueued after phtl_track_cancel returns run normally.  The first
+ * device call of a handle allocates the cancel and gate words (8 pinned host words, one
+ * device word); a handle's calls share them, so calls that can overlap on the GPU must not
+ * be cancelled independently.  Errors: PHTL_E_BADHANDLE.                               */
+int phtl_track_cancel(phtl_handle* h);
+
+/* Outcome of the handle's last phtl_track / phtl_track_programme / phtl_track_host call,
+ * to be read after that call's stream work has completed: PHTL_OK with *turns_done = its
+ * turns, or PHTL_E_CANCELLED with *turns_done = the turns of the launches that ran before
+ * phtl_track_cancel took effect (a multiple of the turns per launch).  Host only.
+ * Errors: PHTL_E_BADHANDLE, PHTL_E_INVALID (turns_done NULL).                          */
+int phtl_track_status(const phtl_handle* h, int64_t* turns_done);
+
 /* Same arguments and results as phtl_track, but one kernel launch per turn, so the
  * state makes a round trip through HBM every turn (Sec. 2.3's host-side turn loop):
  * the memory-bound reference point.                                               */
@@ -219,6 +242,25 @@ int phtl_track_perturn(phtl_handle* h, void* z, void* dp, void* x, void* xp, voi
 int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, void* yp,
                     int64_t n, int64_t turns, int integrator, int dtype, double* mon_rows,
                     int64_t mon_stride);
+
+/* Phase times of the last phtl_track_host call on a handle: the phases of the paper's CUDA
+ * profile (Sec. 2.4.2, Fig. cuprof: allocate, copy in, kernel, copy out, free), each
+ * measured with CUDA events recorded on the call's stream between the phases (device
+ * time, ms), plus the call's host wall time from entry to return.  Zeros before the first
+ * call.  Host only.  Errors: PHTL_E_BADHANDLE, PHTL_E_INVALID (out NULL).               */
+typedef struct phtl_phase_times {
+    double alloc_ms;   /* stream-ordered device allocations                            */
+    double h2d_ms;     /* host -> device copies of the coordinates                      */
+    double kernel_ms;  /* monitor clear and the tracking launches                       */
+    double d2h_ms;     /* device -> host copies of the coordinates and monitor rows     */
+    double free_ms;    /* stream-ordered frees                                          */
+    double total_ms;   /* first event to last                                           */
+    double wall_ms;    /* host wall time of the call                                    */
+    int64_t h2d_bytes, d2h_bytes;
+    int64_t launches;  /* tracking kernels of the call                                  */
+} phtl_phase_times;
+
+int phtl_get_phase_times(const phtl_handle* h, phtl_phase_times* out);
 
 /* ---- ramp programme (accelerating bucket) ---------------------------------------------- */
 
@@ -526,6 +568,8 @@ typedef struct phtl_stats {
     int64_t launches;       /* tracking kernels enqueued by this handle          */
     int64_t particle_turns; /* sum over tracking calls of n * turns              */
     int64_t calls;          /* tracking calls that enqueued work                 */
+    int64_t gate_launches;  /* one-thread cancellation gates in front of the     */
+                            /* persistent launches (phtl_track_cancel)           */
 } phtl_stats;
 
 int phtl_get_stats(const phtl_handle* h, phtl_stats* out);
@@ -547,7 +591,7 @@ int phtl_eval_sin(const double* x, double* y, int64_t n, int which, void* cuda_s
 /* Diagnostic: y[i] = sin(k * z[i]) for n device doubles, stream-ordered, through the
  * form the FP64 kick takes for phi_s = 0 (Sec. 1.1.2's kick with a stationary bucket):
  * the product k z is folded into the sine's argument reduction, so it is never rounded
- * on its own.  |k z| beyond ~6000, Inf and NaN use which = 0 of phtl_eval_sin on the
+ * on its own.  |k z| beyond ~1e5, Inf and NaN use which = 0 of phtl_eval_sin on the
  * rounded product.  Errors: PHTL_E_INVALID (n < 0, null pointer with n > 0, k not
  * finite), PHTL_E_NODEVICE, PHTL_E_CUDA.                                           */
 int phtl_eval_sin_kz(double k, const double* z, double* y, int64_t n, void* cuda_stream);

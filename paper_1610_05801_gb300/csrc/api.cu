@@ -3,8 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdarg>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -14,6 +18,31 @@
 #include "handle.h"
 
 namespace phtl {
+
+namespace {
+
+// One thread: the launch runs (go = 1) unless phtl_track_cancel raised the cancel epoch to
+// this call's epoch or beyond; the turns of the launches that run are counted.  The epoch
+// is read with a system-scope load, so a host store is seen by the next gate.
+__global__ void k_track_gate(const long long* cancel_epoch, long long epoch, int* go,
+                             long long* done, int nturns, int first)
+{
+    long long ce;
+    asm volatile("ld.relaxed.sys.global.s64 %0, [%1];" : "=l"(ce) : "l"(cancel_epoch) : "memory");
+    const int g = ce < epoch ? 1 : 0;
+    *go = g;
+    const long long d0 = first ? 0 : *done;
+    *done = d0 + (g ? nturns : 0);
+}
+
+}  // namespace
+
+cudaError_t launch_gate(const long long* cancel_epoch, long long epoch, int* go, long long* done,
+                        int nturns, bool first, cudaStream_t s)
+{
+    k_track_gate<<<1, 1, 0, s>>>(cancel_epoch, epoch, go, done, nturns, first ? 1 : 0);
+    return cudaGetLastError();
+}
 
 namespace {
 
@@ -237,7 +266,39 @@ void release_handle_resources(phtl_handle* h)
         cudaStreamDestroy(h->stream);
         h->stream = nullptr;
     }
+    for (cudaEvent_t& e : h->phase_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (h->ctl_host || h->gate_go) cudaDeviceSynchronize();  // no gate may still be reading them
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
+    if (h->gate_go) cudaFree(h->gate_go);
+    h->ctl_host = nullptr;
+    h->ctl_dev = nullptr;
+    h->gate_go = nullptr;
     cudaGetLastError();
+}
+
+int log_level()
+{
+    static const int level = [] {
+        const char* v = std::getenv("PHTL_LOG");
+        return v ? std::atoi(v) : 0;
+    }();
+    return level;
+}
+
+void log_line(const char* fmt, ...)
+{
+    if (log_level() <= 0) return;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    std::fputs("phtl: ", stderr);
+    va_list ap;
+    va_start(ap, fmt);
+    std::vfprintf(stderr, fmt, ap);
+    va_end(ap);
+    std::fputc('\n', stderr);
 }
 
 bool handle_valid(const phtl_handle* h)
@@ -262,6 +323,30 @@ int ensure_device(phtl_handle* h)
     }
     // the library is compiled for sm_103a only
     if (prop.major != 10 || prop.minor != 3) return PHTL_E_NODEVICE;
+    // the cancellation words of persistent calls (host-mapped) and the launch gate (device)
+    if (h->ctl_host) {
+        cudaFreeHost(h->ctl_host);
+        h->ctl_host = nullptr;
+        h->ctl_dev = nullptr;
+    }
+    if (h->gate_go) {
+        cudaFree(h->gate_go);
+        h->gate_go = nullptr;
+    }
+    void* hp = nullptr;
+    void* dp = nullptr;
+    if (cudaHostAlloc(&hp, 4 * sizeof(long long), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&h->gate_go), sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (hp) cudaFreeHost(hp);
+        if (h->gate_go) cudaFree(h->gate_go);
+        h->gate_go = nullptr;
+        return PHTL_E_NOMEM;
+    }
+    h->ctl_host = static_cast<long long*>(hp);
+    h->ctl_dev = static_cast<long long*>(dp);
+    std::memset(h->ctl_host, 0, 4 * sizeof(long long));
     h->device = dev;
     h->nsm = prop.multiProcessorCount;
     h->dev_ready = true;
@@ -324,6 +409,8 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
 {
     int rc = ensure_device(h);
     if (rc != PHTL_OK) return rc;
+    h->last_turns = turns;
+    h->last_gated = false;
     if (mon_rows) {
         const int64_t nrows = turns / mon_stride + 1;
         if (nrows > mon_cap) return PHTL_E_INVALID;
@@ -372,12 +459,25 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     L.grid = std::max(grid, 1);
     L.vec = vec ? 1 : 0;
     const MapConsts& mc = h->mc[integrator];
+    // persistent calls: a cancellation gate in front of every launch (phtl_track_cancel)
+    const bool gated = !perturn && h->ctl_dev && h->gate_go;
+    const long long epoch = gated ? ++h->epoch : 0;
+    h->last_gated = gated;
+    L.go = gated ? h->gate_go : nullptr;
 
     int64_t t0 = 0;
     bool first = true;
     do {
         const int64_t nt = std::min<int64_t>(tpl, turns - t0);
         L.nturns = static_cast<int32_t>(nt);
+        if (gated) {
+            if (launch_gate(h->ctl_dev, epoch, h->gate_go, h->ctl_dev + 1, static_cast<int>(nt), first,
+                            s) != cudaSuccess) {
+                cudaGetLastError();
+                return PHTL_E_CUDA;
+            }
+            ++h->stats.gate_launches;
+        }
         MonitorArgs m;
         std::memset(&m, 0, sizeof(m));
         if (mon) {
@@ -404,6 +504,12 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     } while (t0 < turns);
     h->stats.particle_turns += n * turns;
     ++h->stats.calls;
+    if (log_level() > 0)
+        log_line("%s n=%lld turns=%lld integrator=%d dtype=%d launches=%lld grid=%d block=%d "
+                 "turns_per_launch=%lld monitor=%s transverse=%d", perturn ? "track_perturn" : "track",
+                 static_cast<long long>(n), static_cast<long long>(turns), integrator, dtype,
+                 static_cast<long long>((turns + tpl - 1) / std::max<int64_t>(tpl, 1)), L.grid,
+                 block, static_cast<long long>(tpl), mon ? "on" : "off", trans ? 1 : 0);
     return PHTL_OK;
 }
 
@@ -528,6 +634,7 @@ int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* 
                     int64_t n, int64_t turns, int integrator, int dtype, double* mon_rows,
                     int64_t mon_stride)
 {
+    const auto wall0 = std::chrono::steady_clock::now();
     void* hc[6] = {z, dp, x, xp, y, yp};
     int rc = check_track_args(h, hc, n, turns, integrator, dtype);
     if (rc != PHTL_OK) return rc;
@@ -537,49 +644,116 @@ int phtl_track_host(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* 
     cudaStream_t s = nullptr;
     rc = handle_stream(h, &s);
     if (rc != PHTL_OK) return rc;
-    const size_t per = (dtype == PHTL_F64 ? 8u : 8u) * static_cast<size_t>(n);  // n doubles or 2n floats
+    for (cudaEvent_t& e : h->phase_ev) {
+        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+            return PHTL_E_CUDA;
+        }
+    }
+    cudaEvent_t* ev = h->phase_ev;
+    const size_t per = 8u * static_cast<size_t>(n);  // n doubles or 2n floats
     const int64_t nrows = mon_rows ? turns / mon_stride + 1 : 0;
     const size_t mon_bytes = static_cast<size_t>(nrows) * PHTL_MON_FIELDS * sizeof(double);
     void* dc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double* dmon = nullptr;
-    auto cleanup = [&]() {
+    int nplanes = 0;
+    for (int i = 0; i < 6; ++i)
+        if (hc[i]) ++nplanes;
+    auto release = [&]() {
         for (int i = 0; i < 6; ++i)
             if (dc[i]) cudaFreeAsync(dc[i], s);
         if (dmon) cudaFreeAsync(dmon, s);
-        cudaStreamSynchronize(s);
     };
+    auto fail = [&](int code) {
+        cudaGetLastError();
+        release();
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        return code;
+    };
+    // allocate
+    cudaEventRecord(ev[0], s);
     for (int i = 0; i < 6 && n > 0; ++i) {
         if (!hc[i]) continue;
-        if (cudaMallocAsync(&dc[i], per, s) != cudaSuccess) {
-            cudaGetLastError();
-            cleanup();
-            return PHTL_E_NOMEM;
-        }
-        if (cudaMemcpyAsync(dc[i], hc[i], per, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-            cudaGetLastError();
-            cleanup();
-            return PHTL_E_CUDA;
-        }
+        if (cudaMallocAsync(&dc[i], per, s) != cudaSuccess) return fail(PHTL_E_NOMEM);
     }
-    if (mon_rows && cudaMallocAsync(reinterpret_cast<void**>(&dmon), mon_bytes, s) != cudaSuccess) {
-        cudaGetLastError();
-        cleanup();
-        return PHTL_E_NOMEM;
-    }
+    if (mon_rows && cudaMallocAsync(reinterpret_cast<void**>(&dmon), mon_bytes, s) != cudaSuccess)
+        return fail(PHTL_E_NOMEM);
+    // copy in
+    cudaEventRecord(ev[1], s);
+    for (int i = 0; i < 6 && n > 0; ++i)
+        if (hc[i] && cudaMemcpyAsync(dc[i], hc[i], per, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(PHTL_E_CUDA);
+    // kernels
+    cudaEventRecord(ev[2], s);
+    const int64_t l0 = h->stats.launches;
     rc = enqueue_track(h, dc, n, turns, integrator, dtype, s, false, dmon, nrows,
                        mon_rows ? mon_stride : 1);
-    if (rc == PHTL_OK) {
-        for (int i = 0; i < 6 && n > 0; ++i)
-            if (hc[i] && cudaMemcpyAsync(hc[i], dc[i], per, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                rc = PHTL_E_CUDA;
-        if (mon_rows && cudaMemcpyAsync(mon_rows, dmon, mon_bytes, cudaMemcpyDeviceToHost, s) !=
-                            cudaSuccess)
-            rc = PHTL_E_CUDA;
+    if (rc != PHTL_OK) return fail(rc);
+    // copy out
+    cudaEventRecord(ev[3], s);
+    for (int i = 0; i < 6 && n > 0; ++i)
+        if (hc[i] && cudaMemcpyAsync(hc[i], dc[i], per, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return fail(PHTL_E_CUDA);
+    if (mon_rows && cudaMemcpyAsync(mon_rows, dmon, mon_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return fail(PHTL_E_CUDA);
+    // free
+    cudaEventRecord(ev[4], s);
+    release();
+    cudaEventRecord(ev[5], s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return PHTL_E_CUDA;
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = PHTL_E_CUDA;
+    phtl_phase_times& P = h->phases;
+    float ms[5] = {0, 0, 0, 0, 0}, tot = 0.0f;
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+    cudaEventElapsedTime(&tot, ev[0], ev[5]);
     cudaGetLastError();
-    cleanup();
-    return rc;
+    P.alloc_ms = ms[0];
+    P.h2d_ms = ms[1];
+    P.kernel_ms = ms[2];
+    P.d2h_ms = ms[3];
+    P.free_ms = ms[4];
+    P.total_ms = tot;
+    P.h2d_bytes = n > 0 ? static_cast<int64_t>(per) * nplanes : 0;
+    P.d2h_bytes = P.h2d_bytes + static_cast<int64_t>(mon_bytes);
+    P.launches = h->stats.launches - l0;
+    P.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    if (log_level() > 0)
+        log_line("track_host alloc=%.3f h2d=%.3f kernel=%.3f d2h=%.3f free=%.3f total=%.3f wall=%.3f ms",
+                 P.alloc_ms, P.h2d_ms, P.kernel_ms, P.d2h_ms, P.free_ms, P.total_ms, P.wall_ms);
+    return PHTL_OK;
+}
+
+int phtl_get_phase_times(const phtl_handle* h, phtl_phase_times* out)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (!out) return PHTL_E_INVALID;
+    *out = h->phases;
+    return PHTL_OK;
+}
+
+int phtl_track_cancel(phtl_handle* h)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (!h->ctl_host) return PHTL_OK;  // nothing was ever enqueued
+    __atomic_store_n(&h->ctl_host[0], h->epoch, __ATOMIC_SEQ_CST);
+    return PHTL_OK;
+}
+
+int phtl_track_status(const phtl_handle* h, int64_t* turns_done)
+{
+    if (!handle_valid(h)) return PHTL_E_BADHANDLE;
+    if (!turns_done) return PHTL_E_INVALID;
+    if (!h->last_gated) {
+        *turns_done = h->last_turns;
+        return PHTL_OK;
+    }
+    const long long done = __atomic_load_n(&h->ctl_host[1], __ATOMIC_SEQ_CST);
+    *turns_done = done;
+    return done < h->last_turns ? PHTL_E_CANCELLED : PHTL_OK;
 }
 
 int phtl_get_stats(const phtl_handle* h, phtl_stats* out)

@@ -332,6 +332,10 @@ int phtl_batch_create(phtl_handle* h, const phtl_job* jobs, int32_t njobs, int32
         b->info.probe_particle_turns_per_s[slot] = G.rate;
         b->info.particle_turns_per_run += pt;
         b->info.tiles_first_launch += tiles;
+        if (log_level() > 0)
+            log_line("batch_create dtype=%d jobs=%zu block=%d turns_per_launch=%lld probe=%.3e "
+                     "particle_turns=%.3e graph=%d", dt, G.jobs.size(), G.block,
+                     static_cast<long long>(G.T), G.rate, static_cast<double>(pt), use_graph ? 1 : 0);
         b->groups.push_back(std::move(G));
     }
     {

@@ -199,5 +199,6 @@ extern "C" int phtl_batch_run_noalloc(phtl_handle* h, const phtl_job* jobs, int3
     }
     for (int32_t i = 0; i < njobs; ++i) h->stats.particle_turns += jobs[i].n * jobs[i].turns;
     ++h->stats.calls;
+    log_line("batch_run_noalloc jobs=%d groups=%d", njobs, ngroups);
     return PHTL_OK;
 }

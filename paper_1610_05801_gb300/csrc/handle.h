@@ -55,6 +55,18 @@ struct phtl_handle {
     uint16_t* coll_slot = nullptr;
     int64_t coll_slot_cap = 0;
     phtl_stats stats{};
+    // cancellation of persistent tracking calls (phtl_track_cancel): host-mapped words
+    // [0] cancel epoch, [1] turns done by the last call's launches that ran; the device
+    // gate word of the launch that follows; the epoch and turns of the last call
+    long long* ctl_host = nullptr;   // host address (cudaHostAlloc, mapped)
+    long long* ctl_dev = nullptr;    // its device address
+    int* gate_go = nullptr;          // device word
+    long long epoch = 0;
+    int64_t last_turns = 0;
+    bool last_gated = false;
+    // phase times of the last phtl_track_host call, and its events (created on first use)
+    phtl_phase_times phases{};
+    cudaEvent_t phase_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace phtl {
@@ -83,5 +95,8 @@ MapConsts batch_consts(const phtl_handle* h, bool has_rk4);
 // PHTL_OK if a job's own voltage gives a stable bucket with the ring's second RF system
 // (the rule of phtl_create), else PHTL_E_UNSTABLE.
 int voltage_check(const phtl_handle* h, double voltage_V);
+// PHTL_LOG level (environment, read once; 0 = silent) and a printf-style line to stderr.
+int log_level();
+void log_line(const char* fmt, ...);
 
 }  // namespace phtl

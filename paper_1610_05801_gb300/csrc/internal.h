@@ -143,7 +143,16 @@ struct LaunchDesc {
     int32_t grid;      // blocks
     int32_t vec;       // nonzero: all pointers 16-byte aligned (128-bit loads)
     int32_t pad_;
+    const int* go;     // non-null: the launch runs only if *go != 0 (the call's cancellation
+                       // gate, written by the gate kernel launched just before it)
 };
+
+// The cancellation gate in front of each persistent launch of a call (api.cu): one thread
+// reads the handle's cancel epoch from host-mapped memory, writes the launch's decision to
+// *go (device memory, read by every block of the launch that follows on the stream) and
+// counts the turns that run into *done (host-mapped).
+cudaError_t launch_gate(const long long* cancel_epoch, long long epoch, int* go, long long* done,
+                        int nturns, bool first, cudaStream_t s);
 
 // One bunch of a batched launch, as the batched kernels read it from the device job
 // table.  Jobs are sorted by turns (descending), so the jobs still running at any turn

@@ -75,8 +75,9 @@ __device__ __forceinline__ void turns(DF (&z)[P], DF (&d)[P], DF (&x)[P], DF (&x
 // true; planes and monitor are checked at run time); DUAL (GEN only): with the second RF
 // system.
 template <int SCHEME, int DT, bool TRANS, bool MON, bool GEN, bool DUAL = false>
-__global__ void PHTL_F32C_BOUNDS k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
+__global__ void PHTL_F32C_TRACK_BOUNDS(SCHEME, DT, GEN) k_track_f32c(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
+    if (L.go && *L.go == 0) return;  // the call was cancelled before this launch
     extern __shared__ double smem[];
     float* g[6];
 #pragma unroll

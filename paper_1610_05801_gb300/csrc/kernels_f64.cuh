@@ -76,6 +76,7 @@ template <int SCHEME, bool TRANS, bool MON, bool GEN, bool DUAL = false>
 __global__ void PHTL_F64_BOUNDS(SCHEME, GEN)
     k_track_f64(LaunchDesc L, MapConsts c, MonitorArgs m)
 {
+    if (L.go && *L.go == 0) return;  // the call was cancelled before this launch
     extern __shared__ double smem[];
     double* gz = static_cast<double*>(L.c[0]);
     double* gd = static_cast<double*>(L.c[1]);

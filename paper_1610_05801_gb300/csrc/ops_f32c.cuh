@@ -15,12 +15,26 @@ namespace f32c {
 
 constexpr int P = 4;
 
-// Register cap of the FP32-compensated kernels: a build option (the default is the compiler's
-// choice under a 256-thread launch bound).
+// Register budgets of the FP32-compensated kernels, as resident 256-thread blocks per SM asked
+// of the compiler.  The kernels are issue-bound with few resident warps (116-128 registers:
+// 16 warps per SM at 128-thread blocks), so 3 blocks (at most 85 registers: 24 warps, some
+// spill) pays where it was measured to: the single-bunch FP32C and FP32CS kernels, the Ruth4
+// FP32CD kernel and the batched kernels; the single-bunch FP32CD Euler-Cromer and leap-frog
+// kernels ran slower at that budget and keep 1, as do the widened map's kernels (not
+// measured at 3).  Build option PHTL_F32C_MAXNREG: one register cap for all of them.
+constexpr int f32c_track_min_blocks(int scheme, int dtype, bool general)
+{
+    return general ? 1 : (dtype == PHTL_F32CD && scheme != PHTL_RUTH4 ? 1 : 3);
+}
+constexpr int f32c_batched_min_blocks(bool general) { return general ? 1 : 3; }
 #ifdef PHTL_F32C_MAXNREG
 #define PHTL_F32C_BOUNDS __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_BATCHED_BOUNDS(G) __maxnreg__(PHTL_F32C_MAXNREG)
 #else
 #define PHTL_F32C_BOUNDS __launch_bounds__(256)
+#define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __launch_bounds__(256, f32c::f32c_track_min_blocks(S, DT, G))
+#define PHTL_F32C_BATCHED_BOUNDS(G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(G))
 #endif
 constexpr float kTwoPiHi = 6.28318548202514648438f;     // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
@@ -111,6 +125,14 @@ __device__ __forceinline__ DF2 phase_df(const MapConsts& c, const DF& z)
         return split_bits(ZS ? c.k * zd : fma(c.k, zd, c.phis));
     }
     const DF2 kz = df_mul(DF2{c.k_hi, c.k_lo}, as2(z));
+#ifdef PHTL_F32CD_PHASE_F32
+    // build option, for the accuracy comparison of the FP32 variants: the PHTL_F32CD phase
+    // rounded to one float (double-float state, increments and sine otherwise)
+    if (DT == PHTL_F32CD) {
+        const DF2 ph = ZS ? kz : df_add(kz, DF2{c.phis_hi, c.phis_lo});
+        return DF2{__fadd_rn(ph.h, ph.l), 0.0f};
+    }
+#endif
     return ZS ? kz : df_add(kz, DF2{c.phis_hi, c.phis_lo});
 }
 
@@ -167,18 +189,34 @@ __device__ __forceinline__ DF2 sin_df(DF2 x)
 // ---------------------------------------------------------------------------------------
 // Arithmetic of PHTL_F32CS: FP32 increments and the SFU sine (fast, less accurate).
 
-// Phase argument rounded to FP32 (double-float formation, then rounded).
+// Phase argument rounded to FP32 (double-float formation, then rounded).  Build option
+// PHTL_F32CS_PHASE_FP64: formed in FP64 from hi + comp instead (the same value after the
+// rounding to FP32, up to ties), for the accuracy comparison of the FP32CS variants.
 template <bool ZS>
 __device__ __forceinline__ float phase_f(const MapConsts& c, const DF& z)
 {
+#ifdef PHTL_F32CS_PHASE_FP64
+    const double zd = widen_bits(z.hi) + widen_bits(z.c);
+    const double ph = ZS ? c.k * zd : fma(c.k, zd, c.phis);
+    const DF2 p2 = split_bits(ph);
+    return __fadd_rn(p2.h, p2.l);
+#else
     const DF2 ph = phase_df<PHTL_F32CD, ZS>(c, z);
     return __fadd_rn(ph.h, ph.l);
+#endif
 }
 
+// Build option PHTL_F32CS_SINE_DF: the double-float sine of the FP32 phase instead of the
+// SFU (rounded to FP32), for the accuracy comparison of the FP32CS variants.
 __device__ __forceinline__ float sin_sfu(float x)
 {
+#ifdef PHTL_F32CS_SINE_DF
+    const DF2 s = sin_df(DF2{x, 0.0f});
+    return __fadd_rn(s.h, s.l);
+#else
     const float nq = rintf(x * kInvTwoPi);
     return __sinf(__fmaf_rn(-nq, kTwoPiLo, __fmaf_rn(-nq, kTwoPiHi, x)));
+#endif
 }
 
 // ---------------------------------------------------------------------------------------

@@ -84,6 +84,7 @@ public:
             if (rc != PHTL_OK) return rc;
             block_[g] = cfg_.block_threads > 0 ? cfg_.block_threads : t.block_threads;
             rate_[g] = t.particle_turns_per_s;
+            log_line("server dtype=%d block=%d probe=%.3e particle-turns/s", g, block_[g], rate_[g]);
         }
         if (cfg_.target_round_ms > 0) target_ms_ = cfg_.target_round_ms;
         return PHTL_OK;

@@ -14,11 +14,11 @@
 // tests through phtl_eval_sin).
 //
 // sin_kz(k, z) = sin(k z) is the kick's phase for phi_s = 0 with the product folded into
-// the reduction: r = (k z - q H) - q L with H = 3217/2048 (12 significant bits, so q H
-// is exact in FP32 for |q| < 4096) and L = pi/2 - H rounded to FP64.  The first step is
-// one FMA on the exact k z, the second one FMA, so the phase costs no separate FP64
-// operation and r is rounded relative to itself rather than to k z: 11 FP64 operations
-// for sin(k z), against 12 for the phase product followed by sin_f64.
+// the reduction: r = (k z - q H) - q L with H = 3217/2048 (12 significant bits, so q H is
+// an integer times 2^-11, formed exactly for |q| < 2^16) and L = pi/2 - H rounded to FP64.
+// The first step is one FMA on the exact k z, the second one FMA, so the phase costs no
+// separate FP64 operation and r is rounded relative to itself rather than to k z: 11 FP64
+// operations for sin(k z), against 12 for the phase product followed by sin_f64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -88,17 +88,38 @@ __device__ __forceinline__ double sin_f64(double x)
     return sin_quadrant(r, qi);
 }
 
-// sin(k z); k2opi = k * 2/pi rounded to FP32.  |k z| >= ~6000 (lost particles far outside
-// the bucket), Inf and NaN take sin_f64(k * z).
+namespace detail {
+
+// -q H = -q 3217 / 2048 as a double, exactly, for |q| < 2^16: the integer product m = q 3217
+// (|m| < 2^28) placed into the significand with integer operations (no FP64 or conversion
+// instruction).  Within |q| < 4096 it equals the FP32 product q H, which is exact there.
+__device__ __forceinline__ double neg_q_h(int q)
+{
+    const int m = -q * 3217;
+    const unsigned a = static_cast<unsigned>(m < 0 ? -m : m);
+    const int p = 31 - __clz(static_cast<int>(a | 1u));            // leading bit of |m|
+    const unsigned long long mant = (static_cast<unsigned long long>(a) << (52 - p)) &
+                                    0x000FFFFFFFFFFFFFull;
+    const unsigned long long bits = (static_cast<unsigned long long>(m < 0 ? 1u : 0u) << 63) |
+                                    (static_cast<unsigned long long>(1023 - 11 + p) << 52) | mant;
+    return a == 0u ? -0.0 : __longlong_as_double(static_cast<long long>(bits));  // q = 0: -0 * H
+}
+
+}  // namespace detail
+
+// sin(k z); k2opi = k * 2/pi rounded to FP32.  The fused form holds for |k z| up to ~1e5
+// (the quadrant q below 2^16): it covers the bucket and the particles that leave it for
+// ~1e6 turns, so a warp does not split between two sine paths when one of its particles
+// drifts away.  Beyond, and for Inf and NaN: sin_f64(k * z).
 __device__ __forceinline__ double sin_kz(double k, float k2opi, double z)
 {
     using namespace detail;
     const float xq = __fmul_rn(split_bits(z).h, k2opi);   // ~ k z * 2/pi
-    if (!(fabsf(xq) < 4000.0f)) return sin_f64(k * z);
+    if (!(fabsf(xq) < 65536.0f)) return sin_f64(k * z);
     const float tf = __fadd_rn(xq, kMagic);
     const int qi = __float_as_int(tf);
     const float qf = __fsub_rn(tf, kMagic);
-    const double mqh = widen_float_bits(__fmul_rn(qf, -kPio2H12));  // -q H, exact
+    const double mqh = neg_q_h(qi - __float_as_int(kMagic));         // -q H, exact
     double r = fma(k, z, mqh);
     r = fma(widen_float_bits(qf), -kPio2L12, r);
     return sin_quadrant(r, qi);

@@ -87,6 +87,7 @@ template <int S>
 __global__ void __launch_bounds__(256, 2)
     k_ramp_f64(LaunchDesc L, MapConsts c, MonitorArgs m, const RampTurn* __restrict__ prog, int64_t turn0)
 {
+    if (L.go && *L.go == 0) return;  // the call was cancelled before this launch
     extern __shared__ double smem[];
     double* g[6];
 #pragma unroll
@@ -259,6 +260,7 @@ template <int S, int DT>
 __global__ void PHTL_F32C_BOUNDS
     k_ramp_f32c(LaunchDesc L, MapConsts c, MonitorArgs m, const RampTurn* __restrict__ prog, int64_t turn0)
 {
+    if (L.go && *L.go == 0) return;  // the call was cancelled before this launch
     extern __shared__ double smem[];
     float* g[6];
 #pragma unroll

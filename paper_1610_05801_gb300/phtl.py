@@ -69,7 +69,14 @@ MAX_SLICES = 4096
 
 
 class Stats(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("particle_turns", C.c_int64), ("calls", C.c_int64)]
+    _fields_ = [("launches", C.c_int64), ("particle_turns", C.c_int64), ("calls", C.c_int64),
+                ("gate_launches", C.c_int64)]
+
+
+class PhaseTimes(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("alloc_ms", "h2d_ms", "kernel_ms", "d2h_ms", "free_ms",
+                                          "total_ms", "wall_ms")] + \
+               [("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("launches", C.c_int64)]
 
 
 class Job(C.Structure):
@@ -138,6 +145,9 @@ SIGNATURES = {
     "phtl_track_host": (_int, [_vp] + [_vp] * 6 + [_i64, _i64, _int, _int, _vp, _i64]),
     "phtl_moments_from_sums": (_int, [_vp, _vp]),
     "phtl_get_stats": (_int, [_vp, C.POINTER(Stats)]),
+    "phtl_get_phase_times": (_int, [_vp, C.POINTER(PhaseTimes)]),
+    "phtl_track_cancel": (_int, [_vp]),
+    "phtl_track_status": (_int, [_vp, C.POINTER(C.c_int64)]),
     "phtl_eval_sin": (_int, [_vp, _vp, _i64, _int, _vp]),
     "phtl_eval_sin_kz": (_int, [C.c_double, _vp, _vp, _i64, _vp]),
     "phtl_set_programme": (_int, [_vp, _vp, _vp, _i64]),
@@ -269,6 +279,27 @@ class Ring:
         st = Stats()
         _check(self._lib.phtl_get_stats(self._h, C.byref(st)), "phtl_get_stats")
         return st
+
+    def cancel(self):
+        """Stop the persistent tracking calls already enqueued on this ring at their next
+        launch boundary (phtl_track_cancel); callable from any thread."""
+        _check(self._lib.phtl_track_cancel(self._h), "phtl_track_cancel")
+
+    def status(self):
+        """(rc, turns_done) of the last tracking call once its stream work has completed:
+        rc is OK, or E_CANCELLED when it was cut short (phtl_track_status)."""
+        t = C.c_int64()
+        rc = self._lib.phtl_track_status(self._h, C.byref(t))
+        if rc not in (OK, E_CANCELLED):
+            raise PhtlError(rc, "phtl_track_status")
+        return rc, t.value
+
+    def phase_times(self) -> dict:
+        """Phase times (ms) of the last track_host call: alloc, h2d, kernel, d2h, free,
+        total (CUDA events) and wall (host), with the bytes copied and the launches."""
+        p = PhaseTimes()
+        _check(self._lib.phtl_get_phase_times(self._h, C.byref(p)), "phtl_get_phase_times")
+        return {name: getattr(p, name) for name, _ in PhaseTimes._fields_}
 
     def autotune(self, dtype="f32c", integrator="leapfrog", active_particles=1_000_000,
                  target_launch_ms=20.0) -> Tuning:

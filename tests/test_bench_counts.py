@@ -41,3 +41,37 @@ def test_executed_flops_only_where_the_capture_applies():
     assert bench.executed_flops("f64", "leapfrog", wl, 1e10) == {}
     assert bench.executed_flops("f64", "ruth4", dict(wl, ramp={"p0_end": 3e10}), 1e10) == {}
     assert bench.executed_flops("f32cd", "ruth4", wl, 1e10) == {}
+
+
+def test_fp64_roofline_leads_with_the_executed_count():
+    wl = dict(bench.WORKLOADS[bench.DEFAULT_WORKLOAD])
+    n, tpl, dur = 1_000_000, 264, 0.023
+    alg = bench.alg_flops("ruth4", True, True) * n * tpl / dur / 1e12
+    r = bench.fp64_roofline("k", "f64", "ruth4", wl, n, tpl, dur, bench.alg_flops("ruth4", True, True), alg)
+    assert r["frac"] == r["executed_frac"] and r["achieved"] == r["executed_tflops"]
+    assert abs(r["executed_tflops"] - 86.08 * n * tpl / dur / 1e12) < 1e-3
+    assert r["alg_frac"] == alg / bench.FP64_PEAK_TFLOPS
+    # the sine-free count: 4 drifts (2 each), 3 kicks (phase FMA, subtract, FMA), transverse 12
+    assert r["alg_flops_per_particle_turn_without_sines"] == 4 * 2 + 3 * 5 + 12
+    # a variant without a stored ncu count falls back to the algorithmic count
+    w2 = dict(bench.WORKLOADS["widened_map_1e6x1e4_f64"])
+    f2 = bench.alg_flops("ruth4", True, True, w2["ring"])
+    r2 = bench.fp64_roofline("k", "f64", "ruth4", w2, n, tpl, dur, f2, 0.9)
+    assert r2["frac"] == r2["alg_frac"] == 0.9 / bench.FP64_PEAK_TFLOPS
+    assert "executed_frac" not in r2
+
+
+def test_issue_roofline_uses_the_stored_instruction_count():
+    key = ("f32cd", "leapfrog", True, True, False)
+    saved = dict(bench.NCU_WARP_INST_PER_PARTICLE_TURN)
+    try:
+        bench.NCU_WARP_INST_PER_PARTICLE_TURN[key] = 10.0
+        r = bench.issue_roofline("k", key, 5e10, 2000.0)
+        assert abs(r["achieved"] - 500.0) < 1e-9
+        assert abs(r["peak"] - 152 * 4 * 2.0) < 1e-9
+        assert abs(r["frac"] - 500.0 / (152 * 4 * 2.0)) < 1e-12
+        r = bench.issue_roofline("k", ("f32cd", "ruth4", True, True, False), 5e10, 2000.0)
+        assert r["frac"] is None
+    finally:
+        bench.NCU_WARP_INST_PER_PARTICLE_TURN.clear()
+        bench.NCU_WARP_INST_PER_PARTICLE_TURN.update(saved)

@@ -85,9 +85,16 @@ def test_fused_sin_kz_of_the_phi_s_zero_kick():
     assert np.max(np.abs(own[big] / ref[big] - 1)) < 4e-15
     tiny = (np.abs(p) < 1e-3) & (np.abs(p) > 1e-290)
     assert np.max(np.abs(own[tiny] / ref[tiny] - 1)) < 3e-16
-    # far outside any bucket (|k z| beyond the fused range) the kick uses the plain sine
-    # of the rounded product: bitwise what phtl_eval_sin gives for k * z
-    far = np.array([7e3, -1e4, 5e4, -1e5, 3e7, 1e300]) / k
+    # particles that have left the bucket: the fused form holds to |k z| ~ 1e5 (quadrant
+    # below 2^16); the reduction's q L term then carries L's own rounding times q, a few
+    # ulp more
+    out = rng.uniform(-1, 1, 200000) * 1.0e5 / k
+    own_out = phtl.eval_sin_kz(k, torch.tensor(out, dtype=torch.float64, device="cuda:0")).cpu().numpy()
+    ref_out, _ = _sin_kz_reference(k, out)
+    assert np.max(np.abs(own_out - ref_out)) <= 8 * 2.0 ** -53, np.max(np.abs(own_out - ref_out))
+    # beyond the fused range the kick uses the plain sine of the rounded product: bitwise
+    # what phtl_eval_sin gives for k * z
+    far = np.array([1.1e5, -2e5, 5e5, -1e6, 3e7, 1e300]) / k
     own_far = phtl.eval_sin_kz(k, torch.tensor(far, dtype=torch.float64, device="cuda:0")).cpu().numpy()
     ref_far = phtl.eval_sin(torch.tensor(k * far, dtype=torch.float64, device="cuda:0"), 0).cpu().numpy()
     assert np.array_equal(own_far, ref_far)
