@@ -556,20 +556,20 @@ def run_ours(args, wl_name, wl):
 
 
 # DRAM bytes per particle per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# persistent FP64 kernel, from one ncu capture of the current kernel on a 3e6-particle case
-# (state larger than L2); the launch's traffic grows in proportion to its particles.
-# Summary: profiles/k_track_f64_ruth4_transverse_monitor_3e6x100.md.
-NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.354816e6 + 82.915840e6) / 3e6}
+# persistent FP64 kernel, from one ncu capture (--set full) of the current kernel on a
+# 3e6-particle case (state larger than L2); the launch's traffic grows in proportion to its
+# particles.  Summary: profiles/k_track_f64_ruth4_transverse_monitor_3e6x100.md.
+NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.729600e6 + 83.410688e6) / 3e6}
 
 
 # FP64 flops the kernel executes per particle-turn, from the same ncu capture:
 # (2 x DFMA + DMUL + DADD thread instructions per cycle) x cycles / particle-turns, i.e.
-# (2 x 225.610532 + 33.841580 + 0.475363) x 22.909184 ms x 2.043125 GHz / (3e6 x 88).
+# (2 x 225.068198 + 33.760230 + 0.474220) x 22.946400 ms x 2.044726 GHz / (3e6 x 88).
 # Fewer than the algorithmic count: for phi_s = 0 the kernel skips the phase addition and the
 # sin(phi_s) subtraction of the general kick and flips the sine's sign with an integer XOR.
 NCU_EXEC_FLOPS_PER_PARTICLE_TURN = {("f64", "ruth4", True, True):
-                                    (2 * 225.610532 + 33.841580 + 0.475363) * 22.909184e-3
-                                    * 2.043125e9 / (3e6 * 88)}
+                                    (2 * 225.068198 + 33.760230 + 0.474220) * 22.946400e-3
+                                    * 2.044726e9 / (3e6 * 88)}
 
 
 def executed_flops(dt, scheme, wl, particle_turns_per_s):
@@ -720,6 +720,10 @@ NCU_WARP_INST_PER_PARTICLE_TURN = {
     ("f32cd", "ruth4", True, True, False): 8228979485 / (2e6 * 200),
     ("f32cs", "leapfrog", True, True, False): 2326276064 / (2e6 * 200),
     ("f32cs", "ruth4", True, True, False): 3477286084 / (2e6 * 200),
+    # the batched FP32C kernel (leap-frog bunches, stride-1 monitors, no transverse planes): the
+    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 588 turns for every bunch
+    # (profiles/k_batched_f32c_leapfrog_monitor_4e6x588.md)
+    ("f32c", "leapfrog", False, True, True): 21721822992 / (4005158 * 588),
 }
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 

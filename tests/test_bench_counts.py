@@ -36,7 +36,7 @@ def test_algorithmic_flops_of_the_extensions():
 def test_executed_flops_only_where_the_capture_applies():
     wl = {"transverse": True, "stride": 1}
     e = bench.executed_flops("f64", "ruth4", wl, 1e10)
-    assert abs(e["executed_flops_per_particle_turn_ncu"] - 86.08) < 0.01
+    assert abs(e["executed_flops_per_particle_turn_ncu"] - 86.09) < 0.02
     assert abs(e["executed_tflops"] - 0.8608) < 1e-3
     assert bench.executed_flops("f64", "leapfrog", wl, 1e10) == {}
     assert bench.executed_flops("f64", "ruth4", dict(wl, ramp={"p0_end": 3e10}), 1e10) == {}
@@ -49,7 +49,7 @@ def test_fp64_roofline_leads_with_the_executed_count():
     alg = bench.alg_flops("ruth4", True, True) * n * tpl / dur / 1e12
     r = bench.fp64_roofline("k", "f64", "ruth4", wl, n, tpl, dur, bench.alg_flops("ruth4", True, True), alg)
     assert r["frac"] == r["executed_frac"] and r["achieved"] == r["executed_tflops"]
-    assert abs(r["executed_tflops"] - 86.08 * n * tpl / dur / 1e12) < 1e-3
+    assert abs(r["executed_tflops"] - 86.09 * n * tpl / dur / 1e12) < 2e-3
     assert r["alg_frac"] == alg / bench.FP64_PEAK_TFLOPS
     # the sine-free count: 4 drifts (2 each), 3 kicks (phase FMA, subtract, FMA), transverse 12
     assert r["alg_flops_per_particle_turn_without_sines"] == 4 * 2 + 3 * 5 + 12
@@ -70,7 +70,7 @@ def test_issue_roofline_uses_the_stored_instruction_count():
         assert abs(r["achieved"] - 500.0) < 1e-9
         assert abs(r["peak"] - 152 * 4 * 2.0) < 1e-9
         assert abs(r["frac"] - 500.0 / (152 * 4 * 2.0)) < 1e-12
-        r = bench.issue_roofline("k", ("f32cd", "ruth4", True, True, False), 5e10, 2000.0)
+        r = bench.issue_roofline("k", ("f32cd", "euler_cromer", False, False, False), 5e10, 2000.0)
         assert r["frac"] is None
     finally:
         bench.NCU_WARP_INST_PER_PARTICLE_TURN.clear()
