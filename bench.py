@@ -878,7 +878,7 @@ def _play(S, trace, hosts, times, dtype_override=None):
     return time.perf_counter() - t0
 
 
-def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=False):
+def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=False, waves=0):
     """Serving: the first `count` arrivals of the 2000-arrival Poisson trace (seed 4), through
     the continuous-batching loop with their own arithmetic (FP64 or FP32C); then the same
     jobs every one FP32C through the loop (the batched FP32-compensated serving path), and
@@ -906,7 +906,7 @@ def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=Fal
     work = sum(j["n"] * j["turns"] for j in trace)
 
     def served(hosts, times, dtype_override=None):
-        S = phtl.Server(R, memory_budget_bytes=int(budget), max_active=64)
+        S = phtl.Server(R, memory_budget_bytes=int(budget), max_active=64, waves=waves)
         mk, clk = _clocked(lambda: _play(S, trace, hosts, times, dtype_override))
         st = S.stats()
         S.stop()

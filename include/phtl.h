@@ -476,12 +476,13 @@ typedef struct phtl_server_config {
     int64_t chunk_turns_f32;     /* the same for the FP32-compensated jobs                 */
     double target_round_ms;      /* 0 = 20 ms                                              */
     int32_t policy;              /* PHTL_POLICY_SRPT (0, default) or PHTL_POLICY_SHARE     */
-    int32_t pad_;
+    int32_t waves;               /* SRPT: particles of one arithmetic a round carries, in
+                                    resident waves of its batched kernel; 0 = 2            */
 } phtl_server_config;
 
 /* Which admitted jobs a scheduling round advances.
  *  PHTL_POLICY_SRPT : per arithmetic, the jobs with the least remaining work
- *                     (n x turns left) first, up to enough particles to keep the GPU busy,
+ *                     (n x turns left) first, up to `waves` resident waves of particles,
  *                     plus always the longest-admitted one (no starvation): short jobs
  *                     finish early, lowering the median latency.
  *  PHTL_POLICY_SHARE: every admitted job advances every round (processor sharing).    */

@@ -132,12 +132,14 @@ public:
         return cuda_rc(cudaStreamSynchronize(s));
     }
 
-    // Two resident waves of the batched kernel of this arithmetic.
+    // The configured number of resident waves (default 2) of the batched kernel of this
+    // arithmetic, in particles.
     int64_t saturation(int dtype) const
     {
         const int g = dtype < 0 || dtype >= kNumDtypes ? 0 : dtype;
         const int occ = std::max(1, occupancy_batched(g, true, block_[g], h_->mc[0].general != 0));
-        return 2ll * occ * h_->nsm * block_[g] * particles_per_thread(g);
+        const int64_t waves = cfg_.waves > 0 ? cfg_.waves : 2;
+        return waves * occ * h_->nsm * block_[g] * particles_per_thread(g);
     }
 
     void adopt(sched::Job& to, sched::Job& from)
@@ -326,7 +328,7 @@ int phtl_server_start(phtl_handle* h, const phtl_server_config* cfg)
     if (cfg) c = *cfg;
     if (c.policy != PHTL_POLICY_SRPT && c.policy != PHTL_POLICY_SHARE) return PHTL_E_INVALID;
     if (c.memory_budget_bytes < 0 || c.max_active < 0 || c.chunk_turns_f64 < 0 || c.chunk_turns_f32 < 0 ||
-        c.target_round_ms < 0 || (c.block_threads != 0 && (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32)))
+        c.target_round_ms < 0 || c.waves < 0 || (c.block_threads != 0 && (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32)))
         return PHTL_E_INVALID;
     if (c.memory_budget_bytes == 0) c.memory_budget_bytes = 150000000000ll;
     if (c.max_active == 0) c.max_active = 64;

@@ -101,7 +101,7 @@ class ServerConfig(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_int64), ("max_active", C.c_int32),
                 ("block_threads", C.c_int32), ("chunk_turns_f64", C.c_int64),
                 ("chunk_turns_f32", C.c_int64), ("target_round_ms", C.c_double),
-                ("policy", C.c_int32), ("pad_", C.c_int32)]
+                ("policy", C.c_int32), ("waves", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -576,12 +576,14 @@ class Server:
     default the inputs, in place) before the job turns DONE."""
 
     def __init__(self, ring: Ring, memory_budget_bytes=0, max_active=0, block_threads=0,
-                 chunk_turns_f64=0, chunk_turns_f32=0, target_round_ms=0.0, policy="srpt"):
+                 chunk_turns_f64=0, chunk_turns_f32=0, target_round_ms=0.0, policy="srpt",
+                 waves=0):
         self._lib = load()
         self._ring = ring
         pol = {"srpt": POLICY_SRPT, "share": POLICY_SHARE}[policy] if isinstance(policy, str) else int(policy)
         cfg = ServerConfig(int(memory_budget_bytes), int(max_active), int(block_threads),
-                           int(chunk_turns_f64), int(chunk_turns_f32), float(target_round_ms), pol, 0)
+                           int(chunk_turns_f64), int(chunk_turns_f32), float(target_round_ms), pol,
+                           int(waves))
         _check(self._lib.phtl_server_start(ring.handle, C.byref(cfg)), "phtl_server_start")
         self._keep = {}
         self._running = True
