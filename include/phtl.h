@@ -477,7 +477,7 @@ typedef struct phtl_server_config {
     double target_round_ms;      /* 0 = 20 ms                                              */
     int32_t policy;              /* PHTL_POLICY_SRPT (0, default) or PHTL_POLICY_SHARE     */
     int32_t waves;               /* SRPT: particles of one arithmetic a round carries, in
-                                    resident waves of its batched kernel; 0 = 2            */
+                                    resident waves of its batched kernel; 0 = 8            */
 } phtl_server_config;
 
 /* Which admitted jobs a scheduling round advances.

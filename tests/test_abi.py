@@ -301,3 +301,19 @@ def test_batch_validation_needs_no_gpu():
     assert lib.phtl_batch_run(None, None) == phtl.E_BADHANDLE
     assert lib.phtl_batch_destroy(None) == phtl.E_BADHANDLE
     R.close()
+
+
+def test_server_config_validation_without_a_gpu():
+    """A bad serving configuration is refused before any device work: negative budget, slots,
+    chunk turns, round target or SRPT wave cap, an unknown policy, an odd block size."""
+    lib = phtl.load()
+    rc, h = _create(**dict(synth.ring(2e6)))
+    assert rc == phtl.OK
+    good = dict(memory_budget_bytes=0, max_active=0, block_threads=0, chunk_turns_f64=0,
+                chunk_turns_f32=0, target_round_ms=0.0, policy=0, waves=0)
+    for field, bad in (("memory_budget_bytes", -1), ("max_active", -1), ("chunk_turns_f64", -5),
+                       ("chunk_turns_f32", -5), ("target_round_ms", -1.0), ("waves", -1),
+                       ("policy", 7), ("block_threads", 100)):
+        cfg = phtl.ServerConfig(**dict(good, **{field: bad}))
+        assert lib.phtl_server_start(h, C.byref(cfg)) == phtl.E_INVALID, field
+    assert lib.phtl_destroy(h) == phtl.OK
