@@ -59,11 +59,13 @@ WORKLOADS = {
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
         voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5,
         ring=dict(harmonic2=2 * 4620, voltage2_V=0.3 * 4.5e6, phi2_rad=0.0)),
-    # accelerating bucket: a linear momentum ramp 26 -> 30 GeV/c over the 1e4 turns at
-    # 4.5 MV (phi_s ~ 0.09 rad), per-turn constants from the programme table
+    # accelerating bucket: a linear momentum ramp from 26 GeV/c gaining 0.4 MeV/c per turn
+    # (26 -> 30 GeV/c over 1e4 turns) at 4.5 MV (phi_s ~ 0.09 rad), per-turn constants from
+    # the programme table; the gain per turn, not the end momentum, is fixed, so a shorter
+    # run (--turns) keeps the same bucket
     "ramp_1e6x1e4_ec_lf_ruth4_f64": dict(
         n=1_000_000, turns=10_000, schemes=("euler_cromer", "leapfrog", "ruth4"), dtype="f64",
-        voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5, ramp=dict(p0_end=30e9)),
+        voltage=4.5e6, transverse=True, stride=1, sep_frac=0.5, ramp=dict(gain_eVc_per_turn=4e5)),
     # collective step after every turn: 512 uniform slices on [-0.75, 0.75) m, a decaying
     # oscillating (resonator-like) wake table, kick -5e-11 x V plus space charge 1e-9 x the
     # line-density slope; leap-frog, 1e6 x 1e4 turns
@@ -253,15 +255,14 @@ def make_inputs(wl, derived, seed):
 
 def ramp_programme(wl):
     """(V[turns], p0[turns + 1]) of a ramp workload: a linear momentum ramp from the ring's
-    p0 to wl['ramp']['p0_end'] at the workload's voltage."""
+    p0 gaining wl['ramp']['gain_eVc_per_turn'] per turn, at the workload's voltage."""
     import numpy as np
 
     from paper_1610_05801_gb300 import synth
 
     turns = wl["turns"]
     pa = synth.ring(wl["voltage"])["p0_eVc"]
-    pb = wl["ramp"]["p0_end"]
-    return np.full(turns, wl["voltage"]), pa + (pb - pa) * np.arange(turns + 1) / turns
+    return np.full(turns, wl["voltage"]), pa + wl["ramp"]["gain_eVc_per_turn"] * np.arange(turns + 1)
 
 
 def wake_table(wl):
@@ -483,7 +484,9 @@ def run_ours(args, wl_name, wl):
     torch.cuda.synchronize()
     clk = clocks.stop()
     st1 = R.stats()
-    launches = st1.launches - st0.launches
+    # every kernel of the library in the timed region: the tracking launches and the
+    # one-thread cancellation gate in front of each persistent launch
+    launches = (st1.launches - st0.launches) + (st1.gate_launches - st0.gate_launches)
     step_ms = [a.elapsed_time(b) for a, b in step_events]
     t_local = sum(step_ms) / 1e3
     t_max = max_over_ranks(t_local, dist, dev)
@@ -534,8 +537,8 @@ def run_ours(args, wl_name, wl):
                    "monitor_stride": wl["stride"], "ring": "C=6911.5 m h=4620 p0=26 GeV/c "
                    "gamma_t=22.77 V=4.5 MV phi_s=0" + "".join(
                        f" {k}={v}" for k, v in (wl.get("ring") or {}).items()) + (
-                       f" ramp p0 26 -> {wl['ramp']['p0_end'] / 1e9:g} GeV/c linear over the "
-                       f"turns" if wl.get("ramp") else ""),
+                       f" ramp p0 26 GeV/c + {wl['ramp']['gain_eVc_per_turn'] / 1e6:g} MeV/c "
+                       f"per turn" if wl.get("ramp") else ""),
                    "l2": "flushed between timed steps (256 MiB write); state 48 MB resident",
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
@@ -567,17 +570,42 @@ NCU_TRAFFIC_BYTES_PER_PARTICLE = {("f64", "ruth4", True, True): (144.729600e6 + 
 # (2 x 225.068198 + 33.760230 + 0.474220) x 22.946400 ms x 2.044726 GHz / (3e6 x 88).
 # Fewer than the algorithmic count: for phi_s = 0 the kernel skips the phase addition and the
 # sin(phi_s) subtraction of the general kick and flips the sine's sign with an integer XOR.
-NCU_EXEC_FLOPS_PER_PARTICLE_TURN = {("f64", "ruth4", True, True):
+NCU_EXEC_FLOPS_PER_PARTICLE_TURN = {("f64", "ruth4", True, True, "plain"):
                                     (2 * 225.068198 + 33.760230 + 0.474220) * 22.946400e-3
                                     * 2.044726e9 / (3e6 * 88)}
+# The map variants, from thread-instruction totals of one launch each
+# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on.sum; 3e6 particles, the automatic
+# turns per launch: 88 for Ruth4, 66 for RK4): (DFMA, DMUL, DADD, particle-turns).
+NCU_EXEC_COUNTS = {
+    # chromaticity and amplitude detuning: a sine and cosine of each plane's phase per turn
+    ("f64", "ruth4", True, True, "widened"): (19_536_000_000, 5_814_000_000, 550_250_000, 3e6 * 88),
+    # second RF system: a second sine per kick
+    ("f64", "ruth4", True, True, "double_rf"): (21_384_000_000, 3_174_000_000, 814_250_000, 3e6 * 88),
+    ("f64", "rk4", True, True, "double_rf"): (20_196_000_000, 4_752_000_000, 1_996_750_000, 3e6 * 66),
+}
+for _k, (_fma, _mul, _add, _pt) in NCU_EXEC_COUNTS.items():
+    NCU_EXEC_FLOPS_PER_PARTICLE_TURN[_k] = (2 * _fma + _mul + _add) / _pt
+
+
+def map_variant(wl):
+    """The kernel variant a workload runs: 'plain', 'widened' (second-order slippage,
+    chromaticity), 'double_rf', 'ramp', or None for the per-turn and collective paths."""
+    if wl.get("perturn") or wl.get("wake"):
+        return None
+    if wl.get("ramp"):
+        return "ramp"
+    ring = wl.get("ring") or {}
+    if ring.get("voltage2_V"):
+        return "double_rf"
+    return "widened" if ring else "plain"
 
 
 def executed_flops(dt, scheme, wl, particle_turns_per_s):
     """ncu's executed DP FLOP/s rescaled to the live launch duration, where a capture of
     this kernel exists: the fraction of the FP64 peak the pipe's own flop count gives."""
-    key = (dt, scheme, bool(wl["transverse"]), bool(wl["stride"]))
+    key = (dt, scheme, bool(wl["transverse"]), bool(wl["stride"]), map_variant(wl))
     f = NCU_EXEC_FLOPS_PER_PARTICLE_TURN.get(key)
-    if f is None or wl.get("perturn") or wl.get("ring") or wl.get("ramp") or wl.get("wake"):
+    if f is None:
         return {}
     tf = f * particle_turns_per_s / 1e12
     return {"executed_flops_per_particle_turn_ncu": f, "executed_tflops": tf,

@@ -151,6 +151,8 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
     rc = ensure_device(h);
     if (rc != PHTL_OK) return rc;
     if (!h->ramp || h->ramp_device != h->device) return PHTL_E_INVALID;
+    h->last_turns = turns;
+    h->last_gated = false;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     double* mon_rows = h->mon_rows;
     if (mon_rows) {
@@ -186,11 +188,24 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
     L.block = block;
     L.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nchunks, cap)));
     L.vec = vec ? 1 : 0;
+    // a cancellation gate in front of every launch (phtl_track_cancel), as in phtl_track
+    const bool gated = h->ctl_dev && h->gate_go;
+    const long long epoch = gated ? ++h->epoch : 0;
+    h->last_gated = gated;
+    L.go = gated ? h->gate_go : nullptr;
     int64_t t0 = 0;
     bool first = true;
     do {
         const int64_t nt = std::min<int64_t>(tpl, turns - t0);
         L.nturns = static_cast<int32_t>(nt);
+        if (gated) {
+            if (launch_gate(h->ctl_dev, epoch, h->gate_go, h->ctl_dev + 1, static_cast<int>(nt), first,
+                            s) != cudaSuccess) {
+                cudaGetLastError();
+                return PHTL_E_CUDA;
+            }
+            ++h->stats.gate_launches;
+        }
         MonitorArgs m;
         std::memset(&m, 0, sizeof(m));
         if (mon_rows) {

@@ -17,24 +17,31 @@ constexpr int P = 4;
 
 // Register budgets of the FP32-compensated kernels, as resident 256-thread blocks per SM asked
 // of the compiler.  The kernels are issue-bound with few resident warps (116-128 registers:
-// 16 warps per SM at 128-thread blocks), so 3 blocks (at most 85 registers: 24 warps, some
-// spill) pays where it was measured to: the single-bunch FP32C and FP32CS kernels, the Ruth4
-// FP32CD kernel and the batched kernels; the single-bunch FP32CD Euler-Cromer and leap-frog
-// kernels ran slower at that budget and keep 1, as do the widened map's kernels (not
-// measured at 3).  Build option PHTL_F32C_MAXNREG: one register cap for all of them.
+// 16 warps per SM at 128-thread blocks), so more blocks per SM (fewer registers, some spill)
+// pays where it was measured to: 4 blocks (at most 64 registers: 32 warps) for the
+// single-bunch FP32C kernels (+3.8 % over 3 blocks, all three schemes); 3 blocks (at most 85
+// registers) for FP32CS (-2.5 % at 4), the Ruth4 FP32CD kernel (-7 % at 4) and the batched
+// kernels (the batched FP32C kernel spills 2 KB a thread at 64 registers for +1.2 %); the
+// single-bunch FP32CD Euler-Cromer and leap-frog kernels ran slower at 3 and keep 1, as do the
+// widened map's kernels (not measured).  Build option PHTL_F32C_MAXNREG: one register cap for
+// all of them.
 constexpr int f32c_track_min_blocks(int scheme, int dtype, bool general)
 {
-    return general ? 1 : (dtype == PHTL_F32CD && scheme != PHTL_RUTH4 ? 1 : 3);
+    return general ? 1
+                   : dtype == PHTL_F32C ? 4 : (dtype == PHTL_F32CD && scheme != PHTL_RUTH4 ? 1 : 3);
 }
-constexpr int f32c_batched_min_blocks(bool general) { return general ? 1 : 3; }
+constexpr int f32c_batched_min_blocks(int dtype, bool general)
+{
+    return (void)dtype, general ? 1 : 3;
+}
 #ifdef PHTL_F32C_MAXNREG
 #define PHTL_F32C_BOUNDS __maxnreg__(PHTL_F32C_MAXNREG)
 #define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
-#define PHTL_F32C_BATCHED_BOUNDS(G) __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_BATCHED_BOUNDS(DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
 #else
 #define PHTL_F32C_BOUNDS __launch_bounds__(256)
 #define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __launch_bounds__(256, f32c::f32c_track_min_blocks(S, DT, G))
-#define PHTL_F32C_BATCHED_BOUNDS(G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(G))
+#define PHTL_F32C_BATCHED_BOUNDS(DT, G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(DT, G))
 #endif
 constexpr float kTwoPiHi = 6.28318548202514648438f;     // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi

@@ -39,8 +39,20 @@ def test_executed_flops_only_where_the_capture_applies():
     assert abs(e["executed_flops_per_particle_turn_ncu"] - 86.09) < 0.02
     assert abs(e["executed_tflops"] - 0.8608) < 1e-3
     assert bench.executed_flops("f64", "leapfrog", wl, 1e10) == {}
-    assert bench.executed_flops("f64", "ruth4", dict(wl, ramp={"p0_end": 3e10}), 1e10) == {}
+    assert bench.executed_flops("f64", "ruth4", dict(wl, wake={"nslices": 512}), 1e10) == {}
+    assert bench.executed_flops("f64", "ruth4", dict(wl, perturn=True), 1e10) == {}
     assert bench.executed_flops("f32cd", "ruth4", wl, 1e10) == {}
+    # each map variant takes its own capture: the widened map's per-plane phase sine and
+    # cosine, the double-RF kick's second sine
+    for name, scheme, lo, hi in (("widened_map_1e6x1e4_f64", "ruth4", 150, 200),
+                                 ("double_rf_1e6x1e4_ec_lf_ruth4_f64", "ruth4", 150, 200),
+                                 ("rk4_double_rf_1e6x1e4_f64", "rk4", 200, 260)):
+        w = bench.WORKLOADS[name]
+        f = bench.executed_flops("f64", scheme, w, 1e10)["executed_flops_per_particle_turn_ncu"]
+        assert lo < f < hi, (name, f)
+        assert f > bench.NCU_EXEC_FLOPS_PER_PARTICLE_TURN[("f64", "ruth4", True, True, "plain")]
+    assert bench.map_variant(bench.WORKLOADS["ramp_1e6x1e4_ec_lf_ruth4_f64"]) == "ramp"
+    assert bench.map_variant(bench.WORKLOADS[bench.DEFAULT_WORKLOAD]) == "plain"
 
 
 def test_fp64_roofline_leads_with_the_executed_count():
@@ -55,8 +67,8 @@ def test_fp64_roofline_leads_with_the_executed_count():
     assert r["alg_flops_per_particle_turn_without_sines"] == 4 * 2 + 3 * 5 + 12
     # a variant without a stored ncu count falls back to the algorithmic count
     w2 = dict(bench.WORKLOADS["widened_map_1e6x1e4_f64"])
-    f2 = bench.alg_flops("ruth4", True, True, w2["ring"])
-    r2 = bench.fp64_roofline("k", "f64", "ruth4", w2, n, tpl, dur, f2, 0.9)
+    f2 = bench.alg_flops("leapfrog", True, True, w2["ring"])
+    r2 = bench.fp64_roofline("k", "f64", "leapfrog", w2, n, tpl, dur, f2, 0.9)
     assert r2["frac"] == r2["alg_frac"] == 0.9 / bench.FP64_PEAK_TFLOPS
     assert "executed_frac" not in r2
 

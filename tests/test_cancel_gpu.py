@@ -94,3 +94,34 @@ def test_cancel_before_a_call_and_from_another_thread():
     torch.cuda.synchronize()
     assert R.status() == (phtl.OK, 300)
     R.close()
+
+
+def test_cancel_a_programme_call():
+    import test_ramp_gpu as tr
+
+    n, tpl, turns = 500_000, 1000, 200_000
+    # a flat programme (constant momentum and voltage): long, and the bunch stays bunched
+    inp = tr.ramp_inputs(n, seed=29, pb=26e9, N=turns)
+    R = phtl.Ring(**inp["ring"])
+    R.set_programme(inp["V"], inp["p0"])
+    R.set_tuning(turns_per_launch=tpl)
+    bufs = _bufs(inp, "f64")
+    stream = torch.cuda.Stream()
+    R.track_programme(*bufs, turn0=0, turns=turns, integrator="ruth4", stream=stream)
+    time.sleep(0.5)
+    R.cancel()
+    stream.synchronize()
+    rc, done = R.status()
+    assert rc == phtl.E_CANCELLED and 0 < done < turns and done % tpl == 0, (rc, done)
+    got = [b.cpu() for b in bufs]
+    R.close()
+    R2 = phtl.Ring(**inp["ring"])
+    R2.set_programme(inp["V"], inp["p0"])
+    R2.set_tuning(turns_per_launch=tpl)
+    ref = _bufs(inp, "f64")
+    R2.track_programme(*ref, turn0=0, turns=done, integrator="ruth4")
+    torch.cuda.synchronize()
+    assert R2.status() == (phtl.OK, done)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b.cpu())
+    R2.close()
