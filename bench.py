@@ -582,6 +582,8 @@ NCU_EXEC_COUNTS = {
     # second RF system: a second sine per kick
     ("f64", "ruth4", True, True, "double_rf"): (21_384_000_000, 3_174_000_000, 814_250_000, 3e6 * 88),
     ("f64", "rk4", True, True, "double_rf"): (20_196_000_000, 4_752_000_000, 1_996_750_000, 3e6 * 66),
+    # ramp programme: the general kick (phi_s != 0), delta, x' and y' rescaled every turn
+    ("f64", "ruth4", True, True, "ramp"): (11_352_000_000, 2_376_000_000, 814_250_000, 3e6 * 88),
 }
 for _k, (_fma, _mul, _add, _pt) in NCU_EXEC_COUNTS.items():
     NCU_EXEC_FLOPS_PER_PARTICLE_TURN[_k] = (2 * _fma + _mul + _add) / _pt
@@ -742,8 +744,9 @@ def _clocked(fn):
 # profiles/k_track_f32c_instruction_counts_2e6x200.md); keyed by (dtype, scheme,
 # transverse, monitor, batched).
 NCU_WARP_INST_PER_PARTICLE_TURN = {
-    ("f32c", "leapfrog", True, True, False): 4790748955 / (2e6 * 200),
-    ("f32c", "ruth4", True, True, False): 10788660484 / (2e6 * 200),
+    # FP32C at its 64-register budget (4 resident 256-thread blocks)
+    ("f32c", "leapfrog", True, True, False): 4916360742 / (2e6 * 200),
+    ("f32c", "ruth4", True, True, False): 10993311206 / (2e6 * 200),
     ("f32cd", "leapfrog", True, True, False): 3924877111 / (2e6 * 200),
     ("f32cd", "ruth4", True, True, False): 8228979485 / (2e6 * 200),
     ("f32cs", "leapfrog", True, True, False): 2326276064 / (2e6 * 200),

@@ -46,11 +46,14 @@ def test_executed_flops_only_where_the_capture_applies():
     # cosine, the double-RF kick's second sine
     for name, scheme, lo, hi in (("widened_map_1e6x1e4_f64", "ruth4", 150, 200),
                                  ("double_rf_1e6x1e4_ec_lf_ruth4_f64", "ruth4", 150, 200),
-                                 ("rk4_double_rf_1e6x1e4_f64", "rk4", 200, 260)):
+                                 ("rk4_double_rf_1e6x1e4_f64", "rk4", 200, 260),
+                                 ("ramp_1e6x1e4_ec_lf_ruth4_f64", "ruth4", 90, 110)):
         w = bench.WORKLOADS[name]
         f = bench.executed_flops("f64", scheme, w, 1e10)["executed_flops_per_particle_turn_ncu"]
         assert lo < f < hi, (name, f)
         assert f > bench.NCU_EXEC_FLOPS_PER_PARTICLE_TURN[("f64", "ruth4", True, True, "plain")]
+    assert bench.executed_flops("f64", "leapfrog", bench.WORKLOADS["ramp_1e6x1e4_ec_lf_ruth4_f64"],
+                                1e10) == {}
     assert bench.map_variant(bench.WORKLOADS["ramp_1e6x1e4_ec_lf_ruth4_f64"]) == "ramp"
     assert bench.map_variant(bench.WORKLOADS[bench.DEFAULT_WORKLOAD]) == "plain"
 
