@@ -744,17 +744,18 @@ def _clocked(fn):
 # profiles/k_track_f32c_instruction_counts_2e6x200.md); keyed by (dtype, scheme,
 # transverse, monitor, batched).
 NCU_WARP_INST_PER_PARTICLE_TURN = {
-    # FP32C at its 64-register budget (4 resident 256-thread blocks)
-    ("f32c", "leapfrog", True, True, False): 4916360742 / (2e6 * 200),
-    ("f32c", "ruth4", True, True, False): 10993311206 / (2e6 * 200),
+    # FP32C at its 64-register budget (4 resident 256-thread blocks), the phase split with
+    # the phase forms of the integer widening and split
+    ("f32c", "leapfrog", True, True, False): 4410069242 / (2e6 * 200),
+    ("f32c", "ruth4", True, True, False): 9480594061 / (2e6 * 200),
     ("f32cd", "leapfrog", True, True, False): 3924877111 / (2e6 * 200),
     ("f32cd", "ruth4", True, True, False): 8228979485 / (2e6 * 200),
     ("f32cs", "leapfrog", True, True, False): 2326276064 / (2e6 * 200),
     ("f32cs", "ruth4", True, True, False): 3477286084 / (2e6 * 200),
     # the batched FP32C kernel (leap-frog bunches, stride-1 monitors, no transverse planes): the
-    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 588 turns for every bunch
-    # (profiles/k_batched_f32c_leapfrog_monitor_4e6x588.md)
-    ("f32c", "leapfrog", False, True, True): 21721822992 / (4005158 * 588),
+    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 722 turns for every bunch
+    # (profiles/k_batched_f32c_leapfrog_monitor_4e6.md)
+    ("f32c", "leapfrog", False, True, True): 22834113924 / (4005158 * 722),
 }
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 

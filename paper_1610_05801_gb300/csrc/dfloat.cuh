@@ -71,6 +71,39 @@ __device__ __forceinline__ double widen_float_bits(float f)
                             static_cast<int>(m << 29));
 }
 
+// Cheaper forms of the two for the RF phase argument of the FP32C kernels (k z + phi_s
+// formed in FP64 from a coordinate's two floats), where a term below 2^-126 in magnitude
+// changes nothing.
+//
+// widen_float_phase: exact for normal floats; +-0 and subnormals become values of magnitude
+// in [2^-127, 2^-126); Inf / NaN become finite values of magnitude >= 2^128 (a lost
+// particle's phase, which the sine's wide-range path takes).
+__device__ __forceinline__ double widen_float_phase(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return __hiloint2double(static_cast<int>((u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20))),
+                            static_cast<int>(u << 29));
+}
+
+// split_phase: split_bits's high part; the low part is the remaining 29 bits rounded to
+// nearest (one integer-to-float conversion) instead of truncated, so
+// |x - (h + l)| <= 2^-48 |x|.  For 2^-74 <= |x| < 2^128 (both parts normal or zero);
+// other magnitudes, Inf and NaN take split_bits.
+__device__ __forceinline__ DF2 split_phase(double x)
+{
+    const unsigned hi32 = static_cast<unsigned>(__double2hiint(x));
+    const unsigned lo32 = static_cast<unsigned>(__double2loint(x));
+    const unsigned e = (hi32 >> 20) & 0x7ffu;
+    if (e - 949u > 201u) return split_bits(x);
+    const unsigned sign = hi32 & 0x80000000u;
+    const unsigned t = (hi32 & 0x7fffffffu) - (896u << 20);  // FP32 biased exponent at bit 20
+    DF2 r;
+    r.h = __uint_as_float(sign | __funnelshift_l(lo32, t, 3));
+    const float m = __uint2float_rn(lo32 & 0x1fffffffu);      // the remaining bits, rounded
+    r.l = __uint_as_float(sign | __float_as_uint(__fmul_rn(m, __uint_as_float((e - 948u) << 23))));
+    return r;
+}
+
 __device__ __forceinline__ DF2 df_two_sum(float a, float b)
 {
     const float s = __fadd_rn(a, b);

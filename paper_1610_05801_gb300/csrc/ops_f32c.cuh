@@ -122,14 +122,15 @@ __device__ __forceinline__ void acc2(DF& a, DF2 inc)
 __device__ __forceinline__ double widen_bits(float f) { return widen_float_bits(f); }
 
 // Phase argument phi = phi_s + k z as a double-float pair.  PHTL_F32C forms it in FP64 from
-// hi + comp (exact in double) with one DFMA; PHTL_F32CD in double-float arithmetic.
+// hi + comp (exact in double) with one DFMA and splits it with the phase forms of the
+// integer widening and split; PHTL_F32CD in double-float arithmetic.
 // ZS: phi_s == 0, so the phase is k z alone (chosen once, outside the turn loop).
 template <int DT, bool ZS>
 __device__ __forceinline__ DF2 phase_df(const MapConsts& c, const DF& z)
 {
     if (DT == PHTL_F32C) {
-        const double zd = widen_bits(z.hi) + widen_bits(z.c);
-        return split_bits(ZS ? c.k * zd : fma(c.k, zd, c.phis));
+        const double zd = widen_float_phase(z.hi) + widen_float_phase(z.c);
+        return split_phase(ZS ? c.k * zd : fma(c.k, zd, c.phis));
     }
     const DF2 kz = df_mul(DF2{c.k_hi, c.k_lo}, as2(z));
 #ifdef PHTL_F32CD_PHASE_F32
@@ -332,8 +333,8 @@ __device__ __forceinline__ DF2 force2_df(const MapConsts& c, DF2 z)
     if (c.linear) return df_mul(DF2{c.lin2_hi, c.lin2_lo}, z);
     DF2 ph;
     if (DT == PHTL_F32C) {
-        const double zd = widen_bits(z.h) + widen_bits(z.l);
-        ph = split_bits(fma(c.k2, zd, c.phi2));
+        const double zd = widen_float_phase(z.h) + widen_float_phase(z.l);
+        ph = split_phase(fma(c.k2, zd, c.phi2));
     } else {
         ph = df_add(df_mul(DF2{c.k2_hi, c.k2_lo}, z), DF2{c.phi2_hi, c.phi2_lo});
     }

@@ -207,8 +207,8 @@ __device__ __forceinline__ void kick(const DF (&z)[P], DF (&d)[P], double w, con
             } else {
                 DF2 ph;
                 if (DT == PHTL_F32C) {
-                    const double zd = widen_bits(z[p].hi) + widen_bits(z[p].c);
-                    ph = split_bits(fma(c.k, zd, T.phis64));
+                    const double zd = widen_float_phase(z[p].hi) + widen_float_phase(z[p].c);
+                    ph = split_phase(fma(c.k, zd, T.phis64));
                 } else {
                     ph = df_add(df_mul(DF2{c.k_hi, c.k_lo}, as2(z[p])), T.phis);
                 }
