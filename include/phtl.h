@@ -217,7 +217,10 @@ int phtl_track(phtl_handle* h, void* z, void* dp, void* x, void* xp, void* y, vo
  * rows zero.  Calls enqueued after phtl_track_cancel returns run normally.  The first
  * device call of a handle allocates the cancel and gate words (8 pinned host words, one
  * device word); a handle's calls share them, so calls that can overlap on the GPU must not
- * be cancelled independently.  Errors: PHTL_E_BADHANDLE.                               */
+ * be cancelled independently.  A call enqueued on a stream that is capturing a CUDA graph
+ * gets no gates (a replay would reuse its epoch): phtl_track_cancel does not stop the
+ * graph's replays, and phtl_track_status reports such a call as complete.
+ * Errors: PHTL_E_BADHANDLE.                                                            */
 int phtl_track_cancel(phtl_handle* h);
 
 /* Outcome of the handle's last phtl_track / phtl_track_programme / phtl_track_host call,

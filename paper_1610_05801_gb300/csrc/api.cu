@@ -37,6 +37,16 @@ __global__ void k_track_gate(const long long* cancel_epoch, long long epoch, int
 
 }  // namespace
 
+bool stream_capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cap != cudaStreamCaptureStatusNone;
+}
+
 cudaError_t launch_gate(const long long* cancel_epoch, long long epoch, int* go, long long* done,
                         int nturns, bool first, cudaStream_t s)
 {
@@ -460,7 +470,7 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     L.vec = vec ? 1 : 0;
     const MapConsts& mc = h->mc[integrator];
     // persistent calls: a cancellation gate in front of every launch (phtl_track_cancel)
-    const bool gated = !perturn && h->ctl_dev && h->gate_go;
+    const bool gated = !perturn && h->ctl_dev && h->gate_go && !stream_capturing(s);
     const long long epoch = gated ? ++h->epoch : 0;
     h->last_gated = gated;
     L.go = gated ? h->gate_go : nullptr;

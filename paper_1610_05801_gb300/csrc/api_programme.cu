@@ -189,7 +189,7 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
     L.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nchunks, cap)));
     L.vec = vec ? 1 : 0;
     // a cancellation gate in front of every launch (phtl_track_cancel), as in phtl_track
-    const bool gated = h->ctl_dev && h->gate_go;
+    const bool gated = h->ctl_dev && h->gate_go && !stream_capturing(s);
     const long long epoch = gated ? ++h->epoch : 0;
     h->last_gated = gated;
     L.go = gated ? h->gate_go : nullptr;

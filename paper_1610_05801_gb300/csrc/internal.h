@@ -151,6 +151,9 @@ struct LaunchDesc {
 // reads the handle's cancel epoch from host-mapped memory, writes the launch's decision to
 // *go (device memory, read by every block of the launch that follows on the stream) and
 // counts the turns that run into *done (host-mapped).
+// True when the stream is capturing a CUDA graph (or the query fails): a captured call is
+// enqueued without cancellation gates, because a replay would reuse the call's epoch.
+bool stream_capturing(cudaStream_t s);
 cudaError_t launch_gate(const long long* cancel_epoch, long long epoch, int* go, long long* done,
                         int nturns, bool first, cudaStream_t s);
 

@@ -125,3 +125,34 @@ def test_cancel_a_programme_call():
     for a, b in zip(got, ref):
         assert torch.equal(a, b.cpu())
     R2.close()
+
+
+def test_a_call_captured_in_a_graph_has_no_gates():
+    inp = helpers.inputs(50_000, seed=31, transverse=True)
+    R = phtl.Ring(**inp["ring"])
+    R.set_tuning(turns_per_launch=100)
+    bufs = _bufs(inp, "f64")
+    ref = _bufs(inp, "f64")
+    R.track(*ref, turns=1, integrator="leapfrog")  # first device call: control words allocated
+    torch.cuda.synchronize()
+    R.track(*ref, turns=399, integrator="leapfrog")
+    R.track(*ref, turns=400, integrator="leapfrog")
+    torch.cuda.synchronize()
+    R.track(*bufs, turns=1, integrator="leapfrog")
+    torch.cuda.synchronize()
+    gates0 = R.stats().gate_launches
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+        R.track(*bufs, turns=399, integrator="leapfrog", stream=side)
+    assert R.stats().gate_launches == gates0  # captured without gates
+    g.replay()
+    R.cancel()  # a cancel does not reach the captured launches
+    g.replay()
+    torch.cuda.synchronize()
+    # 1 + 399 + 399 turns against 1 + 399 + 400: compare with one more turn on the graph side
+    R.track(*bufs, turns=1, integrator="leapfrog")
+    torch.cuda.synchronize()
+    for a, b in zip(bufs, ref):
+        assert torch.equal(a, b)
+    R.close()
