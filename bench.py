@@ -910,12 +910,14 @@ def _play(S, trace, hosts, times, dtype_override=None):
     return time.perf_counter() - t0
 
 
-def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=False, waves=0):
+def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=False, waves=0,
+                    f32c_leg=True, f64_leg=True):
     """Serving: the first `count` arrivals of the 2000-arrival Poisson trace (seed 4), through
     the continuous-batching loop with their own arithmetic (FP64 or FP32C); then the same
     jobs every one FP32C through the loop (the batched FP32-compensated serving path), and
     every one FP64 through the plain per-job path (one phtl_track_host call per job, in
-    arrival order) -- the comparison the throughput claim rests on."""
+    arrival order) -- the comparison the throughput claim rests on.  f32c_leg / f64_leg False
+    skip those two legs (long traces)."""
     import numpy as np
 
     from paper_1610_05801_gb300 import phtl, synth
@@ -967,6 +969,9 @@ def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=Fal
         out["at_70pct_load"] = {"rate_hz": len(trace) / float(np.sum(gaps * scale)),
                                 "throughput_pts": s2.throughput_pts, "p50_s": s2.p50_latency_s,
                                 "p99_s": s2.p99_latency_s, "makespan_s": mk2}
+    if not f32c_leg:
+        R.close()
+        return out
     mk3, s3, clk3 = served(host(lambda j: 1), arrivals, "f32c")
     out["all_jobs_f32c_serving"] = {
         "throughput_pts": s3.throughput_pts, "p50_s": s3.p50_latency_s,
@@ -992,6 +997,9 @@ def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=Fal
             lat.append(time.perf_counter() - t0 - j["t_arrive_s"])
         return time.perf_counter() - t0, np.sort(np.array(lat))
 
+    if not f64_leg:
+        R.close()
+        return out
     (mk4, lat), clk4 = _clocked(per_job)
     out["all_jobs_f64_plain_per_job"] = {
         "throughput_pts": work / mk4, "p50_s": float(np.percentile(lat, 50)),
@@ -1006,8 +1014,10 @@ def run_serving(args, wl_name, wl):
     from paper_1610_05801_gb300 import build as _build
 
     _build.build()
+    legs = set(args.serving_legs.split(","))
     m = measure_serving(args.serving_jobs or wl["count"], wl["rate_hz"], wl["budget"],
-                        load70=True, cd_leg=True)
+                        load70="load70" in legs, cd_leg="f32cd" in legs,
+                        f32c_leg="f32c" in legs, f64_leg="f64" in legs)
     line = {"metric": METRIC, "value": m["mixed"]["throughput_pts"], "unit": UNIT, "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": m["mixed"]["makespan_s"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1253,6 +1263,8 @@ def main(argv=None):
                     help="batched workload: total particles (profiling captures; default 6e7)")
     ap.add_argument("--turn-scale", type=float,
                     help="batched workload: scale of every bunch's turns (profiling captures)")
+    ap.add_argument("--serving-legs", default="mixed,load70,f32c,f32cd,f64",
+                    help="serving workload: the legs to run (the mixed trace always runs)")
     ap.add_argument("--serving-jobs", type=int, default=64,
                     help="serving: the first N arrivals of the 2000-arrival trace")
     ap.add_argument("--precision-subsample", type=int, default=10_000,
