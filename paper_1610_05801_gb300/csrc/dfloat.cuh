@@ -75,14 +75,16 @@ __device__ __forceinline__ double widen_float_bits(float f)
 // formed in FP64 from a coordinate's two floats), where a term below 2^-126 in magnitude
 // changes nothing.
 //
-// widen_float_phase: exact for normal floats; +-0 and subnormals become values of magnitude
-// in [2^-127, 2^-126); Inf / NaN become finite values of magnitude >= 2^128 (a lost
-// particle's phase, which the sine's wide-range path takes).
+// widen_float_phase: exact for normal floats and +-0 (a particle at z = 0 keeps the phase 0
+// exactly); subnormals become values of magnitude in [2^-127, 2^-126); Inf / NaN become
+// finite values of magnitude >= 2^128 (a lost particle's phase, which the sine's
+// wide-range path takes).
 __device__ __forceinline__ double widen_float_phase(float f)
 {
     const unsigned u = __float_as_uint(f);
-    return __hiloint2double(static_cast<int>((u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20))),
-                            static_cast<int>(u << 29));
+    const unsigned mag = u & 0x7fffffffu;
+    const unsigned hi = mag != 0u ? (mag >> 3) + (896u << 20) : 0u;
+    return __hiloint2double(static_cast<int>((u & 0x80000000u) | hi), static_cast<int>(u << 29));
 }
 
 // split_phase: split_bits's high part; the low part is the remaining 29 bits rounded to
