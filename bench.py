@@ -969,6 +969,7 @@ def measure_serving(count, rate_hz=200.0, budget=150e9, load70=False, cd_leg=Fal
         out["at_70pct_load"] = {"rate_hz": len(trace) / float(np.sum(gaps * scale)),
                                 "throughput_pts": s2.throughput_pts, "p50_s": s2.p50_latency_s,
                                 "p99_s": s2.p99_latency_s, "makespan_s": mk2}
+    del mixed  # a long trace holds tens of GB of host state per copy
     if not f32c_leg:
         R.close()
         return out
