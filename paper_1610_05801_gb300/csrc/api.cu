@@ -471,7 +471,7 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
     const MapConsts& mc = h->mc[integrator];
     // persistent calls: a cancellation gate in front of every launch (phtl_track_cancel)
     const bool gated = !perturn && h->ctl_dev && h->gate_go && !stream_capturing(s);
-    const long long epoch = gated ? ++h->epoch : 0;
+    const long long epoch = gated ? __atomic_add_fetch(&h->epoch, 1LL, __ATOMIC_SEQ_CST) : 0;
     h->last_gated = gated;
     L.go = gated ? h->gate_go : nullptr;
 
@@ -749,7 +749,7 @@ int phtl_track_cancel(phtl_handle* h)
 {
     if (!handle_valid(h)) return PHTL_E_BADHANDLE;
     if (!h->ctl_host) return PHTL_OK;  // nothing was ever enqueued
-    __atomic_store_n(&h->ctl_host[0], h->epoch, __ATOMIC_SEQ_CST);
+    __atomic_store_n(&h->ctl_host[0], __atomic_load_n(&h->epoch, __ATOMIC_SEQ_CST), __ATOMIC_SEQ_CST);
     return PHTL_OK;
 }
 

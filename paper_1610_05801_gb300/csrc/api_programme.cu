@@ -190,7 +190,7 @@ int phtl_track_programme(phtl_handle* h, void* z, void* dp, void* x, void* xp, v
     L.vec = vec ? 1 : 0;
     // a cancellation gate in front of every launch (phtl_track_cancel), as in phtl_track
     const bool gated = h->ctl_dev && h->gate_go && !stream_capturing(s);
-    const long long epoch = gated ? ++h->epoch : 0;
+    const long long epoch = gated ? __atomic_add_fetch(&h->epoch, 1LL, __ATOMIC_SEQ_CST) : 0;
     h->last_gated = gated;
     L.go = gated ? h->gate_go : nullptr;
     int64_t t0 = 0;
