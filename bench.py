@@ -584,6 +584,11 @@ NCU_EXEC_COUNTS = {
     ("f64", "rk4", True, True, "double_rf"): (20_196_000_000, 4_752_000_000, 1_996_750_000, 3e6 * 66),
     # ramp programme: the general kick (phi_s != 0), delta, x' and y' rescaled every turn
     ("f64", "ruth4", True, True, "ramp"): (11_352_000_000, 2_376_000_000, 814_250_000, 3e6 * 88),
+    # the batched FP64 kernel, leap-frog bunches with monitors: the first launch of the 64-bunch
+    # batch scaled to 4.0e6 particles at full turns, 190 turns for every bunch
+    # (profiles/k_batched_f64_leapfrog_monitor_4e6.md)
+    ("f64", "leapfrog", False, True, "batched"): (8_995_244_544, 1_499_207_424, 94_201_536,
+                                                  4005158 * 190),
 }
 for _k, (_fma, _mul, _add, _pt) in NCU_EXEC_COUNTS.items():
     NCU_EXEC_FLOPS_PER_PARTICLE_TURN[_k] = (2 * _fma + _mul + _add) / _pt
@@ -594,6 +599,8 @@ def map_variant(wl):
     chromaticity), 'double_rf', 'ramp', or None for the per-turn and collective paths."""
     if wl.get("perturn") or wl.get("wake"):
         return None
+    if wl.get("kind") == "batched":
+        return "batched"
     if wl.get("ramp"):
         return "ramp"
     ring = wl.get("ring") or {}
@@ -756,6 +763,8 @@ NCU_WARP_INST_PER_PARTICLE_TURN = {
     # first launch of the 64-bunch batch scaled to 4.0e6 particles, 722 turns for every bunch
     # (profiles/k_batched_f32c_leapfrog_monitor_4e6.md)
     ("f32c", "leapfrog", False, True, True): 22834113924 / (4005158 * 722),
+    # the batched FP32CD kernel, the same batch: 846 turns for every bunch
+    ("f32cd", "leapfrog", False, True, True): 23875961875 / (4005158 * 846),
 }
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 
@@ -869,6 +878,16 @@ def measure_batched(wl, steps, warmup):
         out["roofline"] = issue_roofline(f"k_batched_f32c<{dt}, {wl['scheme']}, monitor>",
                                          (dt, wl["scheme"], False, True, True), value,
                                          clk.get("sm_mhz"))
+    else:
+        # FP64-pipe roofline at the rate over whole batch runs (many launches per run)
+        wlb = dict(wl, transverse=False)
+        fpt = alg_flops(wl["scheme"], False, bool(wl["stride"]))
+        r = fp64_roofline(f"k_batched_f64<{wl['scheme']}, monitor>", "f64", wl["scheme"], wlb,
+                          pt * steps, 1, t, fpt, fpt * value / 1e12)
+        r.pop("launch_ms", None)
+        r.pop("turns_per_launch", None)
+        r["basis"] += "; rate over whole batch runs (CUDA events)"
+        out["roofline"] = r
     B.close()
     R.close()
     del keep
