@@ -543,7 +543,8 @@ def run_ours(args, wl_name, wl):
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
         "roofline": roof or (issue_roofline(
-            kname, (dt, dom, bool(wl["transverse"]), bool(wl["stride"]), False),
+            kname, None if map_variant(wl) != "plain" else (dt, dom, bool(wl["transverse"]),
+                                                            bool(wl["stride"]), False),
             n * tpl / dur_s, clk.get("sm_mhz")) if dt != "f64" else None) or fp64_roofline(
             kname, dt, dom, wl, n, tpl, dur_s, flops_pt, achieved),
         "gpu_launches": launches,
@@ -555,6 +556,9 @@ def run_ours(args, wl_name, wl):
         "per_scheme_ms": per_scheme_ms,
         "wall_s_timed_region": wall,
     }
+    if wl.get("wake") and line["roofline"].get("basis"):
+        line["roofline"]["basis"] += ("; the time per turn includes the potential kernel and "
+                                      "the launch gaps, so the fraction is a lower bound")
     return finish_line(line, args, wl, rank, R, dist, ws)
 
 
@@ -589,6 +593,9 @@ NCU_EXEC_COUNTS = {
     # (profiles/k_batched_f64_leapfrog_monitor_4e6.md)
     ("f64", "leapfrog", False, True, "batched"): (8_995_244_544, 1_499_207_424, 94_201_536,
                                                   4005158 * 190),
+    # the collective step's turn kernel (k_coll_turn, leap-frog, transverse, monitor): one turn
+    # of 3e6 particles (profiles/k_coll_turn_leapfrog_collective_3e6x20.md)
+    ("f64", "leapfrog", True, True, "collective"): (54_001_152, 9_000_128, 6_187_504, 3e6),
 }
 for _k, (_fma, _mul, _add, _pt) in NCU_EXEC_COUNTS.items():
     NCU_EXEC_FLOPS_PER_PARTICLE_TURN[_k] = (2 * _fma + _mul + _add) / _pt
@@ -596,9 +603,12 @@ for _k, (_fma, _mul, _add, _pt) in NCU_EXEC_COUNTS.items():
 
 def map_variant(wl):
     """The kernel variant a workload runs: 'plain', 'widened' (second-order slippage,
-    chromaticity), 'double_rf', 'ramp', or None for the per-turn and collective paths."""
-    if wl.get("perturn") or wl.get("wake"):
+    chromaticity), 'double_rf', 'ramp', 'batched', 'collective', or None for the per-turn
+    path."""
+    if wl.get("perturn"):
         return None
+    if wl.get("wake"):
+        return "collective"
     if wl.get("kind") == "batched":
         return "batched"
     if wl.get("ramp"):

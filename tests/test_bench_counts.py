@@ -105,3 +105,13 @@ def test_batched_lines_have_a_roofline():
     r2 = bench.issue_roofline("k", ("f32cd", "leapfrog", False, True, True), 1.4e11, 2070.0)
     assert abs(r2["warp_inst_per_particle_turn_ncu"] - 7.046) < 1e-3
     assert 0.7 < r2["frac"] < 0.9
+
+
+def test_collective_and_variant_keys():
+    wl = dict(bench.WORKLOADS["collective_wake_1e6x1e4_lf_f64"])
+    assert bench.map_variant(wl) == "collective"
+    e = bench.executed_flops("f64", "leapfrog", wl, 1.7e10)
+    # 18 DFMA, 3 DMUL, 2.06 DADD per particle-turn: the leap-frog map, the three-shear planes,
+    # the slice index and the kick's add
+    assert abs(e["executed_flops_per_particle_turn_ncu"] - 41.06) < 0.01
+    assert bench.map_variant(dict(wl, perturn=True)) is None
