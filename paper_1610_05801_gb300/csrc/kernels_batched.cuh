@@ -191,7 +191,11 @@ __device__ __forceinline__ void run_f32c_zs(f32c::DF (&z)[f32c::P], f32c::DF (&d
         }
         if (MON && J.mon) {
             if (--until == 0) {
-                record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
+                // a longitudinal job reduces its 6 fields only (8 lanes' worth of butterfly)
+                if (hx || hy)
+                    record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
+                else
+                    record<false>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
                 parity ^= 1;
                 ++row;
                 until = J.stride;
@@ -250,7 +254,10 @@ __global__ void PHTL_F32C_BATCHED_BOUNDS(DT, GEN) k_batched_f32c(const JobDesc* 
     const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
     int parity = 0;
     if (mon && first) {
-        record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);
+        if (hx || hy)
+            record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);
+        else
+            record<false>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);
         parity ^= 1;
     }
     if (GEN || mon) {
