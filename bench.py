@@ -770,11 +770,11 @@ NCU_WARP_INST_PER_PARTICLE_TURN = {
     ("f32cs", "leapfrog", True, True, False): 2326276064 / (2e6 * 200),
     ("f32cs", "ruth4", True, True, False): 3477286084 / (2e6 * 200),
     # the batched FP32C kernel (leap-frog bunches, stride-1 monitors, no transverse planes): the
-    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 722 turns for every bunch
+    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 719 turns for every bunch
     # (profiles/k_batched_f32c_leapfrog_monitor_4e6.md)
-    ("f32c", "leapfrog", False, True, True): 22834113924 / (4005158 * 722),
-    # the batched FP32CD kernel, the same batch: 846 turns for every bunch
-    ("f32cd", "leapfrog", False, True, True): 23875961875 / (4005158 * 846),
+    ("f32c", "leapfrog", False, True, True): 22110333139 / (4005158 * 719),
+    # the batched FP32CD kernel, the same batch: 849 turns for every bunch
+    ("f32cd", "leapfrog", False, True, True): 23027263805 / (4005158 * 849),
 }
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 

@@ -103,7 +103,7 @@ def test_batched_lines_have_a_roofline():
     assert abs(r["achieved"] - 25.74 * pts / t / 1e12) < 1e-3
     # FP32CD batch: an issue roofline
     r2 = bench.issue_roofline("k", ("f32cd", "leapfrog", False, True, True), 1.4e11, 2070.0)
-    assert abs(r2["warp_inst_per_particle_turn_ncu"] - 7.046) < 1e-3
+    assert abs(r2["warp_inst_per_particle_turn_ncu"] - 6.772) < 1e-3
     assert 0.7 < r2["frac"] < 0.9
 
 
