@@ -61,7 +61,11 @@ __device__ __forceinline__ void run_f64_zs(double (&z)[f64::P], double (&d)[f64:
         }
         if (MON && J.mon) {
             if (--until == 0) {
-                f64::record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
+                // a longitudinal job reduces its 6 fields only (8 lanes' worth of butterfly)
+                if (hx || hy)
+                    f64::record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
+                else
+                    f64::record<false>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, row);
                 parity ^= 1;
                 ++row;
                 until = J.stride;
@@ -124,7 +128,10 @@ __global__ void __launch_bounds__(256, f64::kBatchedMinBlocks256) k_batched_f64(
     const float cnt = left >= P ? static_cast<float>(P) : (left > 0 ? static_cast<float>(left) : 0.0f);
     int parity = 0;
     if (mon && first) {
-        record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);
+        if (hx || hy)
+            record<true>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);
+        else
+            record<false>(z, d, x, xp, y, yp, cnt, hx, hy, smem, parity, J.mon, 0);
         parity ^= 1;
     }
     if (GEN || mon) {
