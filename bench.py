@@ -588,11 +588,11 @@ NCU_EXEC_COUNTS = {
     ("f64", "rk4", True, True, "double_rf"): (20_196_000_000, 4_752_000_000, 1_996_750_000, 3e6 * 66),
     # ramp programme: the general kick (phi_s != 0), delta, x' and y' rescaled every turn
     ("f64", "ruth4", True, True, "ramp"): (11_352_000_000, 2_376_000_000, 814_250_000, 3e6 * 88),
-    # the batched FP64 kernel, leap-frog bunches with monitors: the first launch of the 64-bunch
-    # batch scaled to 4.0e6 particles at full turns, 190 turns for every bunch
+    # the batched FP64 kernel, leap-frog bunches with monitors: one launch of the 64-bunch batch
+    # scaled to 4.0e6 particles at full turns, 200 turns for every bunch, 256-thread blocks
     # (profiles/k_batched_f64_leapfrog_monitor_4e6.md)
-    ("f64", "leapfrog", False, True, "batched"): (8_995_244_544, 1_499_207_424, 94_201_536,
-                                                  4005158 * 190),
+    ("f64", "leapfrog", False, True, "batched"): (9_646_080_000, 1_607_680_000, 9_467_100,
+                                                  4005158 * 200),
     # the collective step's turn kernel (k_coll_turn, leap-frog, transverse, monitor): one turn
     # of 3e6 particles (profiles/k_coll_turn_leapfrog_collective_3e6x20.md)
     ("f64", "leapfrog", True, True, "collective"): (54_001_152, 9_000_128, 6_187_504, 3e6),
@@ -770,11 +770,11 @@ NCU_WARP_INST_PER_PARTICLE_TURN = {
     ("f32cs", "leapfrog", True, True, False): 2326276064 / (2e6 * 200),
     ("f32cs", "ruth4", True, True, False): 3477286084 / (2e6 * 200),
     # the batched FP32C kernel (leap-frog bunches, stride-1 monitors, no transverse planes): the
-    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 719 turns for every bunch
-    # (profiles/k_batched_f32c_leapfrog_monitor_4e6.md)
-    ("f32c", "leapfrog", False, True, True): 22110333139 / (4005158 * 719),
-    # the batched FP32CD kernel, the same batch: 849 turns for every bunch
-    ("f32cd", "leapfrog", False, True, True): 23027263805 / (4005158 * 849),
+    # first launch of the 64-bunch batch scaled to 4.0e6 particles, 200 turns for every bunch,
+    # 256-thread blocks (profiles/k_batched_f32c_leapfrog_monitor_4e6.md)
+    ("f32c", "leapfrog", False, True, True): 6160999306 / (4005158 * 200),
+    # the batched FP32CD kernel, the same batch and shape
+    ("f32cd", "leapfrog", False, True, True): 5468097246 / (4005158 * 200),
 }
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 
@@ -841,6 +841,8 @@ def measure_batched(wl, steps, warmup):
     torch.cuda.set_device(dev)
     specs, ring, jobs, keep = batch_jobs(wl, dev)
     R = phtl.Ring(**ring)
+    if wl.get("block") or wl.get("tpl"):  # a fixed launch shape instead of the autotuner's
+        R.set_tuning(block_threads=wl.get("block", 0), turns_per_launch=wl.get("tpl", 0))
     dt = wl["dtype"]
     t_create = time.perf_counter()
     B = phtl.Batch(R, jobs, use_graph=True)
@@ -1316,6 +1318,8 @@ def main(argv=None):
         wl["block"] = args.block or 0
         wl["tpl"] = args.turns_per_launch or 0
     if kind == "batched":
+        wl["block"] = args.block or 0
+        wl["tpl"] = args.turns_per_launch or 0
         if args.batch_total:
             wl["total"] = args.batch_total
         if args.turn_scale:
