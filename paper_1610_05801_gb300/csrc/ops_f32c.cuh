@@ -30,18 +30,15 @@ constexpr int f32c_track_min_blocks(int scheme, int dtype, bool general)
     return general ? 1
                    : dtype == PHTL_F32C ? 4 : (dtype == PHTL_F32CD && scheme != PHTL_RUTH4 ? 1 : 3);
 }
-constexpr int f32c_batched_min_blocks(int dtype, bool general)
-{
-    return (void)dtype, general ? 1 : 3;
-}
+constexpr int f32c_batched_min_blocks(bool general) { return general ? 1 : 3; }
 #ifdef PHTL_F32C_MAXNREG
 #define PHTL_F32C_BOUNDS __maxnreg__(PHTL_F32C_MAXNREG)
 #define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
-#define PHTL_F32C_BATCHED_BOUNDS(DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_BATCHED_BOUNDS(G) __maxnreg__(PHTL_F32C_MAXNREG)
 #else
 #define PHTL_F32C_BOUNDS __launch_bounds__(256)
 #define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __launch_bounds__(256, f32c::f32c_track_min_blocks(S, DT, G))
-#define PHTL_F32C_BATCHED_BOUNDS(DT, G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(DT, G))
+#define PHTL_F32C_BATCHED_BOUNDS(G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(G))
 #endif
 constexpr float kTwoPiHi = 6.28318548202514648438f;     // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
