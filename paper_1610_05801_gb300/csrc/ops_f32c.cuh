@@ -16,18 +16,32 @@ namespace f32c {
 constexpr int P = 4;
 
 // Register budgets of the FP32-compensated kernels, as resident 256-thread blocks per SM asked
-// of the compiler.  The kernels are issue-bound with few resident warps (116-128 registers:
-// 16 warps per SM at 128-thread blocks), so more blocks per SM (fewer registers, some spill)
-// pays where it was measured to: 4 blocks (at most 64 registers: 32 warps) for the
-// single-bunch FP32C kernels (+3.8 % over 3 blocks, all three schemes); 3 blocks (at most 85
-// registers) for FP32CS (-2.5 % at 4), the Ruth4 FP32CD kernel (-7 % at 4) and the batched
-// kernels (the batched FP32C kernel spills 2 KB a thread at 64 registers for +1.2 %); the
-// single-bunch FP32CD Euler-Cromer and leap-frog kernels ran slower at 3 and keep 1, as do the
-// widened map's kernels (not measured).  Build option PHTL_F32C_MAXNREG: one register cap for
-// all of them.
+// of the compiler.  The kernels are issue-bound with few resident warps (116-160 registers:
+// 12-16 warps per SM), so more blocks per SM (fewer registers, some spill) pays where it was
+// measured to (1e6 particles, transverse planes, a monitor row every turn):
+//   - linear map: 4 blocks (at most 64 registers: 32 warps) for FP32C (+3.8 % over 3 blocks,
+//     all three schemes); 3 blocks (at most 85 registers) for FP32CS (-2.5 % at 4) and the Ruth4
+//     FP32CD kernel (-7 % at 4); the FP32CD Euler-Cromer and leap-frog kernels ran slower at 3
+//     and keep the compiler's choice (1);
+//   - widened map and RK4 / double RF (general kernels): 3 blocks for FP32C (-4 % time over the
+//     three symplectic schemes, -34 % for RK4 on the double-RF ring), FP32CS (-29 %) and FP32CD
+//     RK4 (-24 %); 2 blocks (at most 128 registers) for the FP32CD symplectic schemes (-2 %;
+//     3 blocks was 1 % slower than the compiler's choice);
+//   - batched kernels: 3 blocks (the batched FP32C kernel spills 2 KB a thread at 64 registers
+//     for +1.2 %).
+// Build options PHTL_F32C_GEN_MIN_BLOCKS (general kernels) and PHTL_F32C_MAXNREG (one register
+// cap for all of them) override these, for measuring.
+constexpr int f32c_general_min_blocks(int scheme, int dtype)
+{
+#ifdef PHTL_F32C_GEN_MIN_BLOCKS
+    return (void)scheme, (void)dtype, PHTL_F32C_GEN_MIN_BLOCKS;
+#else
+    return dtype == PHTL_F32CD && scheme != PHTL_RK4 ? 2 : 3;
+#endif
+}
 constexpr int f32c_track_min_blocks(int scheme, int dtype, bool general)
 {
-    return general ? 1
+    return general ? f32c_general_min_blocks(scheme, dtype)
                    : dtype == PHTL_F32C ? 4 : (dtype == PHTL_F32CD && scheme != PHTL_RUTH4 ? 1 : 3);
 }
 constexpr int f32c_batched_min_blocks(bool general) { return general ? 1 : 3; }
