@@ -226,7 +226,7 @@ __device__ __forceinline__ void run_f32c(f32c::DF (&z)[f32c::P], f32c::DF (&d)[f
 }
 
 template <int DT, bool MON, bool GEN>
-__global__ void PHTL_F32C_BATCHED_BOUNDS(GEN) k_batched_f32c(const JobDesc* __restrict__ jobs, int njobs,
+__global__ void PHTL_F32C_BATCHED_BOUNDS(DT, GEN) k_batched_f32c(const JobDesc* __restrict__ jobs, int njobs,
                                                       MapConsts c, int64_t t0, int T)
 {
     using namespace f32c;

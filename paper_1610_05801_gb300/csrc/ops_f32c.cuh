@@ -28,9 +28,13 @@ constexpr int P = 4;
 //     RK4 (-24 %); 2 blocks (at most 128 registers) for the FP32CD symplectic schemes (-2 %;
 //     3 blocks was 1 % slower than the compiler's choice);
 //   - batched kernels: 3 blocks (the batched FP32C kernel spills 2 KB a thread at 64 registers
-//     for +1.2 %).
-// Build options PHTL_F32C_GEN_MIN_BLOCKS (general kernels) and PHTL_F32C_MAXNREG (one register
-// cap for all of them) override these, for measuring.
+//     for +1.2 %); the widened map's batched kernels (16 bunches of 2.5e5 particles, 500
+//     turns): 2 blocks for FP32C and FP32CD (FP32CD leap-frog -17 %, Ruth4 -47 %), 3 for FP32CS
+//     (-37 %);
+//   - ramp programme: 3 blocks for FP32C (-6.6 %), the compiler's choice for FP32CD and FP32CS
+//     (track_ramp.cu).
+// Build options PHTL_F32C_GEN_MIN_BLOCKS, PHTL_F32C_GEN_BATCHED_MIN_BLOCKS (general kernels) and
+// PHTL_F32C_MAXNREG (one register cap for all of them) override these, for measuring.
 constexpr int f32c_general_min_blocks(int scheme, int dtype)
 {
 #ifdef PHTL_F32C_GEN_MIN_BLOCKS
@@ -44,15 +48,24 @@ constexpr int f32c_track_min_blocks(int scheme, int dtype, bool general)
     return general ? f32c_general_min_blocks(scheme, dtype)
                    : dtype == PHTL_F32C ? 4 : (dtype == PHTL_F32CD && scheme != PHTL_RUTH4 ? 1 : 3);
 }
-constexpr int f32c_batched_min_blocks(bool general) { return general ? 1 : 3; }
-#ifdef PHTL_F32C_MAXNREG
-#define PHTL_F32C_BOUNDS __maxnreg__(PHTL_F32C_MAXNREG)
-#define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
-#define PHTL_F32C_BATCHED_BOUNDS(G) __maxnreg__(PHTL_F32C_MAXNREG)
+constexpr int f32c_batched_min_blocks(int dtype, bool general)
+{
+#ifdef PHTL_F32C_GEN_BATCHED_MIN_BLOCKS
+    return general ? ((void)dtype, PHTL_F32C_GEN_BATCHED_MIN_BLOCKS) : 3;
 #else
-#define PHTL_F32C_BOUNDS __launch_bounds__(256)
+    return general ? (dtype == PHTL_F32CS ? 3 : 2) : 3;
+#endif
+}
+#ifdef PHTL_F32C_MAXNREG
+#define PHTL_F32C_RAMP_BOUNDS(S, DT) __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_RAMP_BOUNDS_C __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
+#define PHTL_F32C_BATCHED_BOUNDS(DT, G) __maxnreg__(PHTL_F32C_MAXNREG)
+#else
+#define PHTL_F32C_RAMP_BOUNDS(S, DT) __launch_bounds__(256)
+#define PHTL_F32C_RAMP_BOUNDS_C __launch_bounds__(256, 3)
 #define PHTL_F32C_TRACK_BOUNDS(S, DT, G) __launch_bounds__(256, f32c::f32c_track_min_blocks(S, DT, G))
-#define PHTL_F32C_BATCHED_BOUNDS(G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(G))
+#define PHTL_F32C_BATCHED_BOUNDS(DT, G) __launch_bounds__(256, f32c::f32c_batched_min_blocks(DT, G))
 #endif
 constexpr float kTwoPiHi = 6.28318548202514648438f;     // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
