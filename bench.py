@@ -543,8 +543,8 @@ def run_ours(args, wl_name, wl):
                    "parallelism": f"replica per GPU x{ws}",
                    "launch": "per-turn" if wl.get("perturn") else "persistent"},
         "roofline": roof or (issue_roofline(
-            kname, None if map_variant(wl) != "plain" else (dt, dom, bool(wl["transverse"]),
-                                                            bool(wl["stride"]), False),
+            kname, (dt, dom, bool(wl["transverse"]), bool(wl["stride"]),
+                    False if map_variant(wl) == "plain" else map_variant(wl)),
             n * tpl / dur_s, clk.get("sm_mhz")) if dt != "f64" else None) or fp64_roofline(
             kname, dt, dom, wl, n, tpl, dur_s, flops_pt, achieved),
         "gpu_launches": launches,
@@ -776,6 +776,14 @@ NCU_WARP_INST_PER_PARTICLE_TURN = {
     # the batched FP32CD kernel, the same batch and shape
     ("f32cd", "leapfrog", False, True, True): 5468097246 / (4005158 * 200),
 }
+# the general (widened-map and double-RF) FP32 kernels: one 2e6 x 200-turn launch each, transverse,
+# stride-1 monitor (profiles/k_track_f32c_general_instruction_counts_2e6x200.md)
+for _dt, _counts in (("f32c", (10580001894, 16535668547, 24935241314)),
+                     ("f32cd", (10161272287, 15357883224, 22700504514)),
+                     ("f32cs", (2700933979, 3972666386, 4572386973))):
+    NCU_WARP_INST_PER_PARTICLE_TURN[(_dt, "leapfrog", True, True, "widened")] = _counts[0] / 4e8
+    NCU_WARP_INST_PER_PARTICLE_TURN[(_dt, "ruth4", True, True, "widened")] = _counts[1] / 4e8
+    NCU_WARP_INST_PER_PARTICLE_TURN[(_dt, "rk4", True, True, "double_rf")] = _counts[2] / 4e8
 ISSUE_PER_SM_PER_CLK = 4  # one warp-instruction per clock per SM sub-partition
 
 

@@ -115,3 +115,13 @@ def test_collective_and_variant_keys():
     # the slice index and the kick's add
     assert abs(e["executed_flops_per_particle_turn_ncu"] - 41.06) < 0.01
     assert bench.map_variant(dict(wl, perturn=True)) is None
+
+
+def test_general_fp32_kernels_have_issue_counts():
+    for dt in ("f32c", "f32cd", "f32cs"):
+        for scheme, variant in (("leapfrog", "widened"), ("ruth4", "widened"), ("rk4", "double_rf")):
+            per = bench.NCU_WARP_INST_PER_PARTICLE_TURN[(dt, scheme, True, True, variant)]
+            plain = bench.NCU_WARP_INST_PER_PARTICLE_TURN.get((dt, "leapfrog", True, True, False))
+            assert per > plain  # the general map does more than the linear one
+    r = bench.issue_roofline("k", ("f32cd", "rk4", True, True, "double_rf"), 1.2e10, 2070.0)
+    assert abs(r["warp_inst_per_particle_turn_ncu"] - 56.75) < 0.01 and 0.4 < r["frac"] < 0.7
