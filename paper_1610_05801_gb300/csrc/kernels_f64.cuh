@@ -70,7 +70,10 @@ __device__ __forceinline__ void turns(double (&z)[P], double (&d)[P], double (&x
 #define PHTL_F64_BOUNDS(S, G) \
     __launch_bounds__(256) __maxnreg__((S) == PHTL_RUTH4 && !(G) ? PHTL_F64_RUTH4_MAXNREG : ((G) ? 128 : 80))
 #else
-#define PHTL_F64_BOUNDS(S, G) __launch_bounds__(256, (G) ? 2 : min_blocks_256<S>())
+#ifndef PHTL_F64_GEN_MIN_BLOCKS
+#define PHTL_F64_GEN_MIN_BLOCKS 2
+#endif
+#define PHTL_F64_BOUNDS(S, G) __launch_bounds__(256, (G) ? PHTL_F64_GEN_MIN_BLOCKS : min_blocks_256<S>())
 #endif
 template <int SCHEME, bool TRANS, bool MON, bool GEN, bool DUAL = false>
 __global__ void PHTL_F64_BOUNDS(SCHEME, GEN)
