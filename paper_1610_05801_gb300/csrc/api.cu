@@ -435,10 +435,13 @@ int enqueue_track(phtl_handle* h, void* const* c, int64_t n, int64_t turns, int 
 
     const bool trans = c[2] != nullptr || c[4] != nullptr;
     const bool mon = mon_rows != nullptr;
-    // default block: 96 threads for the FP64 persistent kernels (measured fastest for all three
-    // schemes on 1e6 particles: 2.6 % over 128, 10 % over 256), 128 for the FP32 ones, 256 for
-    // the per-turn launches
-    const int block = h->block > 0 ? h->block : (perturn ? 256 : (dtype == PHTL_F64 ? 96 : 128));
+    // default block: for the FP64 persistent kernels 96 threads with a monitor (measured fastest
+    // for all three schemes on 1e6 particles: 2.6 % over 128, 10 % over 256) and 32 without one
+    // (EC + LF + Ruth4, transverse: 8.3 / 6.5 / 3.7 / 0.9 % over 96 at 1e5 / 3.3e5 / 1e6 / 4e6
+    // particles: the last round of chunks is finer); 128 for the FP32 ones (block size made no
+    // difference without a monitor), 256 for the per-turn launches
+    const int block = h->block > 0 ? h->block
+                                   : (perturn ? 256 : (dtype == PHTL_F64 ? (mon ? 96 : 32) : 128));
     const int es = dtype == PHTL_F64 ? 8 : 4;
     const int ppt = particles_per_thread(dtype);
     int64_t tpl = perturn ? 1 : (h->tpl > 0 ? h->tpl : auto_turns_per_launch(dtype, integrator, n));
